@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark: depth-based selective blurring of a 4096x2304 stereo video batch.
+
+Workload (the batched-video configuration): 250 synthetic rectified stereo
+pairs of 4096x2304 RGB, 12 textured layers drifting in disparity within
+[8, 240] (seed 2), max disparity 256, K = 8, SAD block 41x41, blur sigma 8 on
+disparities outside [120, 256].  A step is one pass of the whole pipeline
+(lightness, K-means, boundary refinement, CCA, SAD at the boundary pixels,
+reconstruction, selective blur) over the 250 pairs.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``value`` is pairs/s with inputs resident in
+HBM (batched form replayed from a CUDA graph); ``e2e`` is the same metric
+through sb_run with pinned HOST buffers (copies inside the timed region);
+``per_pair_plain`` is the per-pair launch form on the same GPU;
+``sad_gcell_s`` counts N_b (D+1) B^2 cells over the SAD kernel time;
+``roofline`` is for the box-sum SAD kernel (integer ALU bound);
+``cpu_baseline`` is the CPU oracle timed on a bounded sample of one pair.
+Under torchrun each rank processes its own 250 frames (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W_C3, H_C3, P_C3 = 4096, 2304, 250
+D_C3, B_C3, K_C3, SIGMA_C3 = 256, 41, 8, 8.0
+INTEREST_C3 = [(120, 256)]
+# algorithmic integer operations of the box-sum SAD per (domain pixel, disparity):
+# one |L - R|, two vertical running-sum updates, two horizontal, one compare
+BOX_OPS_PER_PXD = 6
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU side
+def cpu_oracle_sample(frame: int = 0, n_sad: int = 1500, n_blur: int = 400, seed: int = 5):
+    """Time the CPU oracle on a bounded sample of one 4096x2304 pair and scale
+    to one whole pair: the O(N) stages run in full; SAD runs at n_sad randomly
+    chosen anchors (scaled by the anchor count); reconstruction runs in full on
+    a synthetic sparse map of the same anchor set; blur runs at n_blur
+    randomly chosen blurred pixels (scaled by the blurred-pixel count)."""
+    import numpy as np
+    import oracle
+    import synth
+    sc = synth.scene_c3()
+    p = synth.PARAMS_C3
+    left, right, _ = sc.render(frame=frame, want_gt=False)
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    fr = oracle.run_front(left, right, p)
+    t_front = time.perf_counter() - t0
+    ys, xs = np.nonzero(fr.anchor)
+    nb = len(ys)
+    pick = rng.choice(nb, size=min(n_sad, nb), replace=False)
+    t0 = time.perf_counter()
+    for i in pick:
+        oracle.sad_argmin(fr.L_left, fr.L_right, int(xs[i]), int(ys[i]), p.max_disp, p.block)
+    t_sad = (time.perf_counter() - t0) * nb / len(pick)
+    sparse = np.full(fr.anchor.shape, oracle.UNDET, np.uint16)
+    sparse[fr.anchor == 1] = rng.integers(8, 240, nb).astype(np.uint16)
+    t0 = time.perf_counter()
+    filled = oracle.recon_fill(sparse, fr.anchor)
+    disp = oracle.recon_peek(filled, p.max_disp, p.block, p.disp_threshold)
+    t_recon = time.perf_counter() - t0
+    blur_mask = ~(((disp >= 120) & (disp <= 256)))
+    by, bx = np.nonzero(blur_mask)
+    nbl = len(by)
+    pk = rng.choice(nbl, size=min(n_blur, nbl), replace=False)
+    t0 = time.perf_counter()
+    for i in pk:
+        oracle.blur_at(left, int(bx[i]), int(by[i]), p.sigma)
+    t_blur = (time.perf_counter() - t0) * nbl / len(pk)
+    total = t_front + t_sad + t_recon + t_blur
+    sample = ("one 4096x2304 pair (frame %d): lightness/K-means/refinement/CCA/anchors and reconstruction in full; "
+              "SAD at %d of %d anchors and blur at %d of %d blurred pixels, each scaled to the full count"
+              % (frame, len(pick), nb, len(pk), nbl))
+    return {"seconds_per_pair": total, "stages_s": {"front": t_front, "sad": t_sad, "recon": t_recon, "blur": t_blur},
+            "sample": sample}
+
+
+def run_reference(args):
+    """The CPU oracle as it stands, as the reference arm: each step times the
+    oracle on a bounded sample of one pair of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    times = []
+    sample = None
+    for s in range(args.steps):
+        r = cpu_oracle_sample(frame=s % P_C3, n_sad=600, n_blur=200, seed=s)
+        times.append(r["seconds_per_pair"])
+        sample = r["sample"]
+    sec = statistics.mean(times)
+    value = 1.0 / sec
+    line = {
+        "impl": "reference", "metric": "stereo pairs/s at 4096x2304 (batched, CPU oracle)", "value": value,
+        "unit": "pairs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec * 1000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u8/int32/f64", "data": "synthetic",
+        "config": {"workload": "batched video: 250 pairs 4096x2304, D=256, block 41, K=8, sigma 8, interest [120,256]",
+                   "sample": "each step: one pair, sampled and scaled"},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU side
+def anchor_counts(ctx, sb, torch, lefts, rights, params):
+    """Anchors per pair (refined boundary pixels in the domain plus its border
+    columns), from the library's own stages; bookkeeping for the cell rate."""
+    H, W = lefts.shape[1], lefts.shape[2]
+    r = (B_C3 - 1) // 2
+    x0, x1, y0, y1 = D_C3 + r, W - 1 - r, r, H - 1 - r
+    L = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+    lab = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+    bnd = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+    out = []
+    for i in range(lefts.shape[0]):
+        sb.sb_rgb_to_lightness(ctx, lefts[i], L)
+        sb.sb_kmeans_segment(ctx, L, K_C3, 100, labels=lab)
+        sb.sb_refine_boundaries(ctx, lab, bnd, sb.SB_MORPH_FILL_REMOVE, 0.04)
+        m = bnd[y0:y1 + 1, x0:x1 + 1].clone()
+        m[:, 0] = 1
+        m[:, -1] = 1
+        out.append(m.sum())
+    return [int(v) for v in torch.stack(out).cpu()]
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import synth
+    import paper_2001_07809_b300 as sb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    P, H, W = args.pairs, H_C3, W_C3
+    scene = synth.scene_c3()
+    lefts = torch.empty((P, H, W, 3), dtype=torch.uint8, device="cuda")
+    rights = torch.empty((P, H, W, 3), dtype=torch.uint8, device="cuda")
+    outs = torch.empty((P, H, W, 3), dtype=torch.uint8, device="cuda")
+    disps = torch.empty((P, H, W), dtype=torch.int16, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for i in range(P):  # each rank renders its own frames of the video
+        synth.render_device(scene, rank * P + i, lefts[i], rights[i], None, stream)
+    torch.cuda.synchronize()
+
+    params = sb.make_params(k=K_C3, max_disp=D_C3, block=B_C3, disp_threshold=1, sigma=SIGMA_C3,
+                            ranges=INTEREST_C3, sad_variant=sb.SB_SAD_AUTO)
+    ctx = sb.Context(local)
+    pairs = [sb.Pair(lefts[i], rights[i], params, outs[i], disps[i]) for i in range(P)]
+    flags = sb.SB_RUN_BATCHED | sb.SB_RUN_GRAPH
+
+    # untimed warm-up (captures the graph)
+    for _ in range(args.warmup):
+        sb.sb_run(ctx, pairs, flags)
+    ctx.synchronize()
+
+    # timed region: device-resident inputs (250 x 56.6 MB, far above the 126 MB L2)
+    ctx.profile_enable(True)
+    sb.sb_run(ctx, pairs, flags)   # re-capture with stage marks (untimed)
+    ctx.synchronize()
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    l0 = ctx.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage_ms = []
+    ev0.record()
+    for _ in range(args.steps):
+        sb.sb_run(ctx, pairs, flags)
+        stage_ms.append(ctx.profile_read())   # waits for this step's last stage mark
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = ctx.launch_count() - l0
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms_max = max_over_ranks(ms)
+    value = P * world / (ms_max / 1000.0)
+    stage_avg = [statistics.mean(s[i] for s in stage_ms) for i in range(len(sb.STAGES))]
+    ctx.profile_enable(False)
+
+    # plain per-pair form on the same pairs
+    plain_steps = 1
+    sb.sb_run(ctx, pairs[:4], sb.SB_RUN_PLAIN)
+    ctx.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(plain_steps):
+        sb.sb_run(ctx, pairs, sb.SB_RUN_PLAIN)
+    e1.record()
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / plain_steps
+    plain_value = P * world / (max_over_ranks(plain_ms) / 1000.0)
+    # identical outputs batched vs plain (spot check of one pair)
+    ref_out, ref_disp = outs[7].clone(), disps[7].clone()
+    sb.sb_run(ctx, pairs, flags)
+    ctx.synchronize()
+    same = bool(torch.equal(ref_out, outs[7]) and torch.equal(ref_disp, disps[7]))
+
+    # anchors -> SAD cell rate and roofline of the box-sum kernel
+    nb = anchor_counts(ctx, sb, torch, lefts, rights, params)
+    cells = sum(nb) * (D_C3 + 1) * B_C3 * B_C3
+    sad_ms = stage_avg[sb.STAGES.index("sad")]
+    r = (B_C3 - 1) // 2
+    omega = (W - D_C3 - 2 * r) * (H - 2 * r)
+    ops = P * omega * (D_C3 + 1) * BOX_OPS_PER_PXD
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    alu_peak = 148 * 128 * sm_max * 1e6 / 1e12          # Tops/s: 148 SMs x 128 lanes x max clock
+    achieved = ops / (sad_ms / 1000.0) / 1e12
+
+    # end to end through sb_run with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hl = torch.empty((P, H, W, 3), dtype=torch.uint8).pin_memory()
+        hr = torch.empty((P, H, W, 3), dtype=torch.uint8).pin_memory()
+        ho = torch.empty((P, H, W, 3), dtype=torch.uint8).pin_memory()
+        hd = torch.empty((P, H, W), dtype=torch.int16).pin_memory()
+        hl.copy_(lefts)
+        hr.copy_(rights)
+        hpairs = [sb.Pair(hl[i], hr[i], params, ho[i], hd[i]) for i in range(P)]
+        hflags = sb.SB_RUN_BATCHED | sb.SB_RUN_HOST_IO
+        sb.sb_run(ctx, hpairs, hflags)
+        ctx.synchronize()
+        e2e_steps = max(1, min(args.steps, 3))
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            sb.sb_run(ctx, hpairs, hflags)
+            ctx.synchronize()
+        t1 = time.perf_counter()
+        barrier()
+        e2e_s = max_over_ranks((t1 - t0) / e2e_steps)
+        same = same and bool(torch.equal(ho[7].cuda(), outs[7]))
+        e2e = {"value": P * world / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": P * H * W * 6,
+               "d2h_bytes_per_step": P * H * W * 5, "ms_per_step": e2e_s * 1000.0}
+        del hl, hr, ho, hd
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        c = cpu_oracle_sample()
+        cpu = {"value": 1.0 / c["seconds_per_pair"], "unit": "pairs/s", "cores": 1, "kind": "oracle",
+               "sample": c["sample"], "stages_s": c["stages_s"]}
+
+    if rank == 0:
+        line = {
+            "metric": "stereo pairs/s at 4096x2304 (batched vs per-pair), SAD Gcell/s, p99 latency",
+            "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8/int32 (SAD), fp32 (blur)", "data": "synthetic",
+            "config": {"workload": "batched video: %d pairs 4096x2304 RGB per GPU, 12 drifting layers (seed 2), "
+                                   "D=256, block 41, K=8, sigma 8, interest [120,256]" % P,
+                       "form": "batched, CUDA graph replay", "l2": "inputs 56.6 MB per pair x %d, larger than L2" % P},
+            "per_pair_plain": {"value": plain_value, "unit": "pairs/s", "ms_per_step": plain_ms},
+            "batched_equals_plain": same,
+            "sad_gcell_s": cells / (sad_ms / 1000.0) / 1e9,
+            "stage_ms": dict(zip(sb.STAGES, stage_avg)),
+            "anchors_per_pair": sum(nb) / len(nb),
+            "roofline": {"bound": "alu", "kernel": "k_sad_boxsum", "achieved": achieved, "peak": alu_peak,
+                         "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": None,
+                         "peak_note": "148 SMs x 128 INT32 lanes x %.0f MHz (max SM clock)" % sm_max,
+                         "ops_per_launch": ops},
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--pairs", type=int, default=P_C3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

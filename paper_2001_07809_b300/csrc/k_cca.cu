@@ -1,0 +1,326 @@
+// Connected components analysis and small-component removal (Section III).
+//
+// Labelling (8-connectivity) is union-find: each 32x32 tile first unites its
+// pixels in shared memory, then pixels on tile borders unite across tiles in
+// global memory, then every pixel jumps to its root.  Unions always hang the
+// larger root under the smaller (atomicMin), so a component's final root is
+// its smallest linear index: the same label a raster-order flood fill gives.
+//
+// Removal: the components are ordered by (size, label) and the longest
+// prefix holding at most floor(frac * N_b) pixels is removed.  On the device
+// that prefix is "every component smaller than s*, plus the m size-s*
+// components with the smallest labels", with s* and m found from a histogram
+// of component sizes, and the cut label T found from per-row counts.  No
+// host round-trip, so the whole sequence can be captured in a CUDA graph.
+#include "sb_common.cuh"
+
+namespace sb {
+
+namespace {
+constexpr int CT = 32;                 // CCA tile side
+constexpr int kUnionLimit = 1 << 22;   // retries of one union before flagging an error
+
+__device__ __forceinline__ int find_root(const int* P, int x) {
+  int guard = 0;
+  while (true) {
+    int p = P[x];
+    if (p == x || ++guard > kUnionLimit) return x;
+    x = p;
+  }
+}
+
+// Lock-free union (both roots hang the larger index under the smaller).
+__device__ __forceinline__ bool unite(int* P, int a, int b) {
+  for (int it = 0; it < kUnionLimit; ++it) {
+    a = find_root(P, a);
+    b = find_root(P, b);
+    if (a == b) return true;
+    if (a < b) {
+      int old = atomicMin(&P[b], a);
+      if (old == b) return true;
+      b = old;
+    } else {
+      int old = atomicMin(&P[a], b);
+      if (old == a) return true;
+      a = old;
+    }
+  }
+  return false;
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_cca_local(const CcaJob* __restrict__ jobs, uint32_t* dev_err) {
+  __shared__ int s_p[CT * CT];
+  const CcaJob J = jobs[blockIdx.z];
+  const int tx0 = blockIdx.x * CT, ty0 = blockIdx.y * CT;
+  if (tx0 >= J.w || ty0 >= J.h) return;
+  const int w = J.w, h = J.h;
+  for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) {
+    const int x = tx0 + (i & (CT - 1)), y = ty0 + (i >> 5);
+    s_p[i] = (x < w && y < h && J.b[(int64_t)y * w + x]) ? i : -1;
+  }
+  __syncthreads();
+  bool ok = true;
+  for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) {
+    if (s_p[i] < 0) continue;
+    const int lx = i & (CT - 1), ly = i >> 5;
+    // previous neighbours inside the tile: W, NW, N, NE
+    if (lx > 0 && s_p[i - 1] >= 0) ok &= unite(s_p, i, i - 1);
+    if (ly > 0) {
+      if (lx > 0 && s_p[i - CT - 1] >= 0) ok &= unite(s_p, i, i - CT - 1);
+      if (s_p[i - CT] >= 0) ok &= unite(s_p, i, i - CT);
+      if (lx < CT - 1 && s_p[i - CT + 1] >= 0) ok &= unite(s_p, i, i - CT + 1);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) {
+    const int x = tx0 + (i & (CT - 1)), y = ty0 + (i >> 5);
+    if (x >= w || y >= h) continue;
+    int v = -1;
+    if (s_p[i] >= 0) {
+      const int root = find_root(s_p, i);
+      v = (ty0 + (root >> 5)) * w + tx0 + (root & (CT - 1));
+    }
+    J.lab[(int64_t)y * w + x] = v;
+  }
+  if (!ok) atomicOr(dev_err, DEV_ERR_CCA_ITER);
+}
+
+__global__ void __launch_bounds__(256) k_cca_merge(const CcaJob* __restrict__ jobs, uint32_t* dev_err) {
+  const CcaJob J = jobs[blockIdx.z];
+  const int tx0 = blockIdx.x * CT, ty0 = blockIdx.y * CT;
+  if (tx0 >= J.w || ty0 >= J.h) return;
+  const int w = J.w, h = J.h;
+  bool ok = true;
+  // tile border pixels: top row (32), left column (31 more), right column (31 more)
+  for (int t = threadIdx.x; t < 3 * CT; t += blockDim.x) {
+    int lx, ly;
+    if (t < CT) { lx = t; ly = 0; }
+    else if (t < 2 * CT - 1) { lx = 0; ly = t - CT + 1; }
+    else if (t < 3 * CT - 2) { lx = CT - 1; ly = t - 2 * CT + 2; }
+    else continue;
+    const int x = tx0 + lx, y = ty0 + ly;
+    if (x >= w || y >= h) continue;
+    const int p = y * w + x;
+    if (!J.b[p]) continue;
+    const int nx[4] = {x - 1, x - 1, x, x + 1}, ny[4] = {y, y - 1, y - 1, y - 1};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int qx = nx[k], qy = ny[k];
+      if (qx < 0 || qy < 0 || qx >= w) continue;
+      if (qx >= tx0 && qx < tx0 + CT && qy >= ty0) continue;  // same tile: done locally
+      const int q = qy * w + qx;
+      if (J.b[q]) ok &= unite(J.lab, p, q);
+    }
+  }
+  if (!ok) atomicOr(dev_err, DEV_ERR_CCA_ITER);
+}
+
+// Flatten to roots, then count component sizes and the boundary pixels.
+__global__ void __launch_bounds__(256) k_cca_flatten(const CcaJob* __restrict__ jobs) {
+  const CcaJob J = jobs[blockIdx.y];
+  const int64_t n = (int64_t)J.w * J.h;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    int v = J.lab[p];
+    if (v >= 0 && v != (int)p) J.lab[p] = find_root(J.lab, v);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_cc_count(const CcaJob* __restrict__ jobs) {
+  const CcaJob J = jobs[blockIdx.y];
+  const int64_t n = (int64_t)J.w * J.h;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned cnt = 0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    const int v = J.lab[p];
+    if (v >= 0) { atomicAdd(&J.size[v], 1u); ++cnt; }
+  }
+  for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(reinterpret_cast<unsigned long long*>(&J.cut[0]), (unsigned long long)cnt);
+}
+
+__device__ __forceinline__ int64_t removal_limit(const CcaJob& J) {
+  return (int64_t)floor(__dmul_rn(J.frac, (double)J.cut[0]));
+}
+
+__global__ void __launch_bounds__(256) k_cc_hist(const CcaJob* __restrict__ jobs) {
+  const CcaJob J = jobs[blockIdx.y];
+  const int64_t n = (int64_t)J.w * J.h;
+  const int64_t limit = removal_limit(J);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    if (J.lab[p] == (int)p) {
+      const uint32_t s = J.size[p];
+      if ((int64_t)s <= limit && (int64_t)s < J.shist_len) atomicAdd(&J.shist[s], 1u);
+    }
+  }
+}
+
+// One CTA per job: s* = smallest size whose cumulative pixel count exceeds the
+// limit, m = how many size-s* components still fit.
+__global__ void __launch_bounds__(1024) k_cc_cut(const CcaJob* __restrict__ jobs) {
+  __shared__ long long s_part[1024];
+  __shared__ long long s_first;
+  const CcaJob J = jobs[blockIdx.x];
+  const int64_t limit = removal_limit(J);
+  const int64_t len = limit < (int64_t)J.shist_len - 1 ? limit : (int64_t)J.shist_len - 1;  // sizes 1..len
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t per = (len + nt - 1) / nt;
+  const int64_t a = 1 + tid * per, b = a + per < len + 1 ? a + per : len + 1;
+  long long loc = 0;
+  for (int64_t s = a; s < b; ++s) loc += (long long)s * J.shist[s];
+  s_part[tid] = loc;
+  if (tid == 0) s_first = LLONG_MAX;
+  __syncthreads();
+  // inclusive scan over threads (Hillis-Steele, 1024 entries)
+  for (int o = 1; o < nt; o <<= 1) {
+    long long v = tid >= o ? s_part[tid - o] : 0;
+    __syncthreads();
+    s_part[tid] += v;
+    __syncthreads();
+  }
+  long long run = tid ? s_part[tid - 1] : 0;
+  long long found = LLONG_MAX, found_before = 0;
+  for (int64_t s = a; s < b; ++s) {
+    long long nxt = run + (long long)s * J.shist[s];
+    if (nxt > limit) { found = s; found_before = run; atomicMin(&s_first, found); break; }
+    run = nxt;
+  }
+  __syncthreads();
+  if (found != LLONG_MAX && found == s_first) {
+    // the unique thread holding the first crossing: m size-s* components still fit
+    J.cut[2] = found;
+    J.cut[3] = (limit - found_before) / found;
+  }
+  if (tid == 0) {
+    if (s_first == LLONG_MAX) {  // every component of size <= limit goes
+      J.cut[2] = limit + 1;
+      J.cut[3] = 0;
+    }
+    J.cut[1] = limit;
+    J.cut[4] = -1;
+  }
+}
+
+// Per row: how many roots have size s* (only when m > 0).
+__global__ void __launch_bounds__(256) k_cc_rowcount(const CcaJob* __restrict__ jobs) {
+  const CcaJob J = jobs[blockIdx.y];
+  if (J.cut[3] <= 0) return;
+  const uint32_t sstar = (uint32_t)J.cut[2];
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int y = warp; y < J.h; y += nwarps) {
+    unsigned cnt = 0;
+    for (int x = lane; x < J.w; x += 32) {
+      const int64_t p = (int64_t)y * J.w + x;
+      cnt += (J.lab[p] == (int)p && J.size[p] == sstar) ? 1u : 0u;
+    }
+    for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0) J.rowcnt[y] = cnt;
+  }
+}
+
+// One CTA per job: T = label of the m-th (0-based) size-s* root in raster order.
+__global__ void __launch_bounds__(1024) k_cc_select(const CcaJob* __restrict__ jobs) {
+  __shared__ long long s_part[1024];
+  __shared__ int s_row;
+  __shared__ long long s_before;
+  const CcaJob J = jobs[blockIdx.x];
+  const long long m = J.cut[3];
+  if (m <= 0) return;
+  const uint32_t sstar = (uint32_t)J.cut[2];
+  const int tid = threadIdx.x, nt = blockDim.x, h = J.h;
+  const int per = (h + nt - 1) / nt;
+  const int a = tid * per, b = a + per < h ? a + per : h;
+  long long loc = 0;
+  for (int y = a; y < b; ++y) loc += J.rowcnt[y];
+  s_part[tid] = loc;
+  if (tid == 0) s_row = INT_MAX;
+  __syncthreads();
+  for (int o = 1; o < nt; o <<= 1) {
+    long long v = tid >= o ? s_part[tid - o] : 0;
+    __syncthreads();
+    s_part[tid] += v;
+    __syncthreads();
+  }
+  long long run = tid ? s_part[tid - 1] : 0;
+  int cand = INT_MAX;
+  long long cand_before = 0;
+  for (int y = a; y < b; ++y) {
+    long long nxt = run + J.rowcnt[y];
+    if (m < nxt) { cand = y; cand_before = run; break; }
+    run = nxt;
+  }
+  if (cand != INT_MAX) atomicMin(&s_row, cand);  // every later thread also crosses: keep the first row
+  __syncthreads();
+  if (cand != INT_MAX && cand == s_row) s_before = cand_before;
+  __syncthreads();
+  if (tid < 32 && s_row != INT_MAX) {  // warp 0 walks the row 32 pixels at a time
+    long long k = m - s_before;
+    const int64_t base = (int64_t)s_row * J.w;
+    for (int x0 = 0; x0 < J.w; x0 += 32) {
+      const int x = x0 + tid;
+      const int64_t p = base + x;
+      const bool hit = x < J.w && J.lab[p] == (int)p && J.size[p] == sstar;
+      const unsigned mask = __ballot_sync(0xffffffffu, hit);
+      const int c = __popc(mask);
+      if (k < c) {
+        // position of the k-th set bit
+        unsigned mm = mask;
+        for (long long i = 0; i < k; ++i) mm &= mm - 1;
+        if (tid == __ffs(mm) - 1) J.cut[4] = p;
+        break;
+      }
+      k -= c;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_cc_filter(const CcaJob* __restrict__ jobs) {
+  const CcaJob J = jobs[blockIdx.y];
+  const int64_t n = (int64_t)J.w * J.h;
+  const uint32_t sstar = (uint32_t)J.cut[2];
+  const long long T = J.cut[4];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    const int v = J.lab[p];
+    uint8_t keep = 0;
+    if (v >= 0) {
+      const uint32_t sz = J.size[v];
+      const bool gone = sz < sstar || (sz == sstar && (long long)v < T);
+      keep = gone ? 0 : 1;
+    }
+    J.out[p] = keep;
+  }
+}
+
+void launch_cca(const CcaJob* jobs, int n_jobs, int max_w, int max_h, uint32_t* dev_err, cudaStream_t s) {
+  if (n_jobs <= 0) return;
+  dim3 tiles((max_w + CT - 1) / CT, (max_h + CT - 1) / CT, n_jobs);
+  k_cca_local<<<tiles, 256, 0, s>>>(jobs, dev_err);
+  k_cca_merge<<<tiles, 128, 0, s>>>(jobs, dev_err);
+  const int64_t n = (int64_t)max_w * max_h;
+  int bpj = (int)((n + 256 * 8 - 1) / (256 * 8));
+  if (bpj > 1184) bpj = 1184;
+  if (bpj < 1) bpj = 1;
+  k_cca_flatten<<<dim3(bpj, n_jobs), 256, 0, s>>>(jobs);
+}
+
+void launch_cc_filter(const CcaJob* jobs, int n_jobs, int max_w, int max_h, cudaStream_t s) {
+  if (n_jobs <= 0) return;
+  const int64_t n = (int64_t)max_w * max_h;
+  int bpj = (int)((n + 256 * 8 - 1) / (256 * 8));
+  if (bpj > 1184) bpj = 1184;
+  if (bpj < 1) bpj = 1;
+  k_cc_count<<<dim3(bpj, n_jobs), 256, 0, s>>>(jobs);
+  k_cc_hist<<<dim3(bpj, n_jobs), 256, 0, s>>>(jobs);
+  k_cc_cut<<<n_jobs, 1024, 0, s>>>(jobs);
+  int rb = (max_h + 7) / 8;
+  if (rb > 592) rb = 592;
+  k_cc_rowcount<<<dim3(rb, n_jobs), 256, 0, s>>>(jobs);
+  k_cc_select<<<n_jobs, 1024, 0, s>>>(jobs);
+  k_cc_filter<<<dim3(bpj, n_jobs), 256, 0, s>>>(jobs);
+}
+
+}  // namespace sb

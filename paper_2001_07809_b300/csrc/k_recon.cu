@@ -1,0 +1,150 @@
+// Disparity map reconstruction from the boundary disparities (Section III).
+//
+// Algorithm 1 ("Fill"): in each row, every pixel between two consecutive
+// anchors of equal disparity takes that disparity.  Equivalently, a
+// non-anchor pixel is filled exactly when the nearest anchor on its left and
+// the nearest on its right agree.  One warp per row: a left-to-right pass
+// carries the last anchor's disparity through 32-pixel chunks (ballot +
+// shuffle), a right-to-left pass does the same for the next anchor.
+//
+// Algorithm 2 ("Peek"): each pixel still undetermined after Algorithm 1
+// takes, from the nearest determined pixels above and below in its column
+// inside Omega, the smaller when they differ by more than the threshold and
+// else the floor of their mean.  "Determined" refers to the map after
+// Algorithm 1, so the columns are independent: a thread per column, and the
+// column is cut into segments of seg_rows rows whose first/last determined
+// values are summarised first, so a segment can start its sweeps knowing the
+// nearest determined value beyond each of its ends.
+#include "sb_common.cuh"
+
+namespace sb {
+
+namespace {
+constexpr uint16_t NONE = SB_UNDET16;
+}
+
+__global__ void __launch_bounds__(256) k_recon_fill(const ReconJob* __restrict__ jobs) {
+  const ReconJob J = jobs[blockIdx.y];
+  const int y = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (y >= J.h) return;
+  const int lane = threadIdx.x & 31, w = J.w;
+  const uint16_t* src = J.sparse + (int64_t)y * w;
+  uint16_t* dst = J.filled + (int64_t)y * w;
+  // pass 1: disparity of the nearest anchor strictly to the left (NONE if none)
+  uint16_t carry = NONE;
+  for (int x0 = 0; x0 < w; x0 += 32) {
+    const int x = x0 + lane;
+    const uint16_t v = x < w ? src[x] : NONE;
+    const bool anc = v != NONE;
+    const unsigned mask = __ballot_sync(0xffffffffu, anc);
+    const unsigned below = mask & ((1u << lane) - 1u);
+    const int src_lane = below ? 31 - __clz(below) : 0;
+    const uint16_t left = __shfl_sync(0xffffffffu, v, src_lane);
+    const uint16_t pd = below ? left : carry;
+    if (x < w) dst[x] = anc ? v : pd;
+    if (mask) carry = __shfl_sync(0xffffffffu, v, 31 - __clz(mask));
+  }
+  __syncwarp();
+  // pass 2: nearest anchor strictly to the right; fill when both sides agree
+  carry = NONE;
+  const int nchunks = (w + 31) / 32;
+  for (int ci = nchunks - 1; ci >= 0; --ci) {
+    const int x = ci * 32 + lane;
+    const uint16_t v = x < w ? src[x] : NONE;
+    const bool anc = v != NONE;
+    const unsigned mask = __ballot_sync(0xffffffffu, anc);
+    const unsigned above = lane == 31 ? 0u : (mask & ~((2u << lane) - 1u));
+    const int src_lane = above ? __ffs(above) - 1 : 0;
+    const uint16_t right = __shfl_sync(0xffffffffu, v, src_lane);
+    const uint16_t nd = above ? right : carry;
+    if (x < w && !anc) {
+      const uint16_t pd = dst[x];
+      dst[x] = (pd != NONE && pd == nd) ? pd : NONE;
+    }
+    if (mask) carry = __shfl_sync(0xffffffffu, v, __ffs(mask) - 1);
+  }
+}
+
+// first / last determined value of each (segment, column) inside Omega
+__global__ void __launch_bounds__(128) k_recon_peek_summary(const ReconJob* __restrict__ jobs) {
+  const ReconJob J = jobs[blockIdx.z];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int seg = blockIdx.y;
+  const int oy0 = J.r, oy1 = J.h - 1 - J.r;
+  const int nseg = (J.h + J.seg_rows - 1) / J.seg_rows;
+  if (x >= J.w || seg >= nseg) return;
+  const int ya = max(seg * J.seg_rows, oy0), yb = min(seg * J.seg_rows + J.seg_rows - 1, oy1);
+  uint16_t first = NONE, last = NONE;
+  for (int y = ya; y <= yb; ++y) {
+    const uint16_t v = J.filled[(int64_t)y * J.w + x];
+    if (v != NONE) {
+      if (first == NONE) first = v;
+      last = v;
+    }
+  }
+  J.seg_top[(int64_t)seg * J.w + x] = first;
+  J.seg_bot[(int64_t)seg * J.w + x] = last;
+}
+
+__global__ void __launch_bounds__(128) k_recon_peek_apply(const ReconJob* __restrict__ jobs) {
+  const ReconJob J = jobs[blockIdx.z];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int seg = blockIdx.y;
+  const int w = J.w;
+  const int nseg = (J.h + J.seg_rows - 1) / J.seg_rows;
+  if (x >= w || seg >= nseg) return;
+  const int oy0 = J.r, oy1 = J.h - 1 - J.r, ox0 = J.D + J.r, ox1 = w - 1 - J.r;
+  const int sa = seg * J.seg_rows, sb = min(sa + J.seg_rows - 1, J.h - 1);
+  const bool colin = x >= ox0 && x <= ox1;
+  const int ya = max(sa, oy0), yb = min(sb, oy1);
+  // rows of the segment outside Omega (or whole column outside) are 0
+  for (int y = sa; y <= sb; ++y)
+    if (!colin || y < oy0 || y > oy1) J.out[(int64_t)y * w + x] = 0;
+  if (!colin || ya > yb) return;
+  uint16_t above = NONE, below = NONE;
+  for (int s = seg - 1; s >= 0; --s) {
+    const uint16_t v = J.seg_bot[(int64_t)s * w + x];
+    if (v != NONE) { above = v; break; }
+  }
+  for (int s = seg + 1; s < nseg; ++s) {
+    const uint16_t v = J.seg_top[(int64_t)s * w + x];
+    if (v != NONE) { below = v; break; }
+  }
+  // upward sweep: remember the nearest determined value below each pixel
+  uint16_t nb = below;
+  for (int y = yb; y >= ya; --y) {
+    const int64_t p = (int64_t)y * w + x;
+    const uint16_t v = J.filled[p];
+    if (v != NONE) nb = v;
+    J.out[p] = v != NONE ? v : nb;
+  }
+  // downward sweep: combine with the nearest determined value above
+  uint16_t na = above;
+  const int T = J.threshold;
+  for (int y = ya; y <= yb; ++y) {
+    const int64_t p = (int64_t)y * w + x;
+    const uint16_t v = J.filled[p];
+    if (v != NONE) { na = v; continue; }
+    const uint16_t b = J.out[p];
+    uint16_t o;
+    if (na == NONE && b == NONE) o = 0;
+    else if (na == NONE) o = b;
+    else if (b == NONE) o = na;
+    else {
+      const int a = na, c = b;
+      const int range = a > c ? a - c : c - a;
+      o = (uint16_t)(range > T ? min(a, c) : (a + c) / 2);
+    }
+    J.out[p] = o;
+  }
+}
+
+void launch_recon(const ReconJob* jobs, int n_jobs, int max_w, int max_h, int max_nseg, cudaStream_t s) {
+  if (n_jobs <= 0) return;
+  k_recon_fill<<<dim3((max_h + 7) / 8, n_jobs), 256, 0, s>>>(jobs);
+  dim3 g((max_w + 127) / 128, max_nseg, n_jobs);
+  k_recon_peek_summary<<<g, 128, 0, s>>>(jobs);
+  k_recon_peek_apply<<<g, 128, 0, s>>>(jobs);
+}
+
+}  // namespace sb

@@ -1,0 +1,1133 @@
+// C ABI of the selective-blurring library: context, workspace, argument
+// checks, the per-stage entry points and sb_run (per-pair, batched, CUDA
+// graph and host-buffer streaming forms).  All arithmetic of the method runs
+// in the kernels of the other translation units; this file only sizes,
+// places and orders the work.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/sb.h"
+#include "sb_common.cuh"
+
+using namespace sb;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kSegRows = 64;  // Algorithm 2 column segment height
+inline size_t al(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+// ------------------------------------------------------------ job uploads
+// A pinned host ring and a device ring of the same size.  Device reuse is
+// ordered by the stream; host reuse waits for the copy that read it.
+struct Uploader {
+  uint8_t* host = nullptr;
+  uint8_t* dev = nullptr;
+  size_t cap = 0, head = 0;
+  struct Flight { size_t a, b; cudaEvent_t ev; };
+  std::vector<Flight> flights;
+  std::vector<cudaEvent_t> pool;
+
+  cudaError_t init(size_t bytes) {
+    cap = bytes;
+    cudaError_t e = cudaMallocHost(&host, cap);
+    if (e != cudaSuccess) return e;
+    return cudaMalloc(&dev, cap);
+  }
+  void release() {
+    for (auto& f : flights) cudaEventDestroy(f.ev);
+    for (auto ev : pool) cudaEventDestroy(ev);
+    flights.clear();
+    pool.clear();
+    if (host) cudaFreeHost(host);
+    if (dev) cudaFree(dev);
+    host = dev = nullptr;
+  }
+  // copies n bytes to the device; returns the device address
+  void* put(const void* src, size_t bytes, cudaStream_t s, cudaError_t* err) {
+    const size_t n = al(bytes ? bytes : 1);
+    if (n > cap) { *err = cudaErrorMemoryAllocation; return nullptr; }
+    if (head + n > cap) head = 0;
+    const size_t a = head, b = head + n;
+    // wait for in-flight copies that read [a, b)
+    for (size_t i = 0; i < flights.size();) {
+      if (flights[i].a < b && a < flights[i].b) {
+        cudaEventSynchronize(flights[i].ev);
+        pool.push_back(flights[i].ev);
+        flights.erase(flights.begin() + i);
+      } else {
+        ++i;
+      }
+    }
+    if (bytes) memcpy(host + a, src, bytes);
+    *err = cudaMemcpyAsync(dev + a, host + a, n, cudaMemcpyHostToDevice, s);
+    cudaEvent_t ev;
+    if (!pool.empty()) { ev = pool.back(); pool.pop_back(); }
+    else cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    cudaEventRecord(ev, s);
+    flights.push_back({a, b, ev});
+    head = b;
+    return dev + a;
+  }
+};
+
+// ------------------------------------------------------------ workspace
+struct PairWs {
+  uint8_t *Ll, *Lr, *refined, *filtered, *lut;
+  uint32_t *hist, *size_key, *shist, *rowcnt;
+  double* centroids;
+  int32_t *lab, *iters;
+  int64_t* cut;
+  uint16_t *sparse, *filled, *disp, *seg_top, *seg_bot;
+  float* taps;
+  int32_t shist_len, nseg;
+};
+
+struct Geo {
+  int w, h;
+  sb_params p;
+};
+
+size_t pair_ws_bytes(const Geo& g, bool need_disp) {
+  const size_t N = (size_t)g.w * g.h;
+  const int nseg = (g.h + kSegRows - 1) / kSegRows;
+  const size_t shist = (size_t)floor(g.p.cc_remove_fraction * (double)N) + 2;
+  size_t b = 0;
+  b += al(N) * 4;                        // Ll, Lr, refined, filtered
+  b += al(256) + al(256 * 4) + al(256 * 8) + al(8) + al(8 * 8);
+  b += al(N * 4) * 2;                    // size/key, lab
+  b += al(shist * 4) + al((size_t)g.h * 4);
+  b += al(N * 2) * (need_disp ? 3 : 2);  // sparse, filled (+ disp)
+  b += al((size_t)nseg * g.w * 2) * 2;
+  b += al(200 * 4);
+  return b;
+}
+
+PairWs carve(uint8_t* base, const Geo& g, bool need_disp) {
+  const size_t N = (size_t)g.w * g.h;
+  const int nseg = (g.h + kSegRows - 1) / kSegRows;
+  const size_t shist = (size_t)floor(g.p.cc_remove_fraction * (double)N) + 2;
+  PairWs s{};
+  size_t o = 0;
+  auto take = [&](size_t n) { uint8_t* p = base + o; o += al(n); return p; };
+  s.Ll = take(N);
+  s.Lr = take(N);
+  s.refined = take(N);
+  s.filtered = take(N);
+  s.lut = take(256);
+  s.hist = (uint32_t*)take(256 * 4);
+  s.centroids = (double*)take(256 * 8);
+  s.iters = (int32_t*)take(8);
+  s.cut = (int64_t*)take(8 * 8);
+  s.size_key = (uint32_t*)take(N * 4);
+  s.lab = (int32_t*)take(N * 4);
+  s.shist = (uint32_t*)take(shist * 4);
+  s.rowcnt = (uint32_t*)take((size_t)g.h * 4);
+  s.sparse = (uint16_t*)take(N * 2);
+  s.filled = (uint16_t*)take(N * 2);
+  s.disp = need_disp ? (uint16_t*)take(N * 2) : nullptr;
+  s.seg_top = (uint16_t*)take((size_t)nseg * g.w * 2);
+  s.seg_bot = (uint16_t*)take((size_t)nseg * g.w * 2);
+  s.taps = (float*)take(200 * 4);
+  s.shist_len = (int32_t)shist;
+  s.nseg = nseg;
+  return s;
+}
+
+std::vector<float> gauss_taps(float sigma, int* R_out) {
+  const int R = (int)ceil(3.0 * (double)sigma);
+  std::vector<double> g(2 * R + 1);
+  double tot = 0.0;
+  const double s2 = (double)sigma * (double)sigma;
+  for (int i = -R; i <= R; ++i) { g[i + R] = exp(-(double)(i * i) / (2.0 * s2)); tot += g[i + R]; }
+  std::vector<float> out(2 * R + 1);
+  for (int i = 0; i < 2 * R + 1; ++i) out[i] = (float)(g[i] / tot);
+  *R_out = R;
+  return out;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ context
+struct sb_context {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t budget = 0;
+  std::string err;
+  uint64_t launches = 0;
+  uint8_t* tables = nullptr;  // lin (512 B) | coarse (4096 B) | thr (257 x 4 B)
+  uint32_t* dev_err = nullptr;
+  uint8_t* ws = nullptr;
+  size_t ws_bytes = 0;
+  Uploader up;
+  cudaStream_t s_in = nullptr, s_out = nullptr;  // host-buffer streaming
+  double last_density = 0.2;                      // boundary density seen last (for the tuner)
+  // graph cache (batched form)
+  struct GraphEntry {
+    std::string key;
+    cudaGraphExec_t exec = nullptr;
+  };
+  GraphEntry graph;
+  // host-buffer staging
+  uint8_t* stage = nullptr;
+  size_t stage_bytes = 0;
+  // job blob of the graph form: the dry pass records every upload here
+  bool dry = false;       // record uploads only: no memsets, no launches
+  int sink = 0;           // 0: upload ring, 1: blob
+  std::vector<uint8_t> blob;
+  uint8_t* blob_dev = nullptr;
+  size_t blob_cap = 0;
+  uint8_t* blob_host = nullptr;  // pinned staging of the blob
+  cudaEvent_t blob_ev = nullptr;
+  // boundary density feedback for the SAD variant choice
+  int64_t* dens_host = nullptr;  // pinned: N_b of the last pair measured
+  cudaEvent_t dens_ev = nullptr;
+  int64_t dens_px = 0;
+  bool dens_pending = false;
+  // stage profiling
+  bool prof_on = false;
+  cudaEvent_t prof_ev[SB_N_STAGES + 1] = {};
+  bool prof_recorded = false;
+  bool capturing = false;
+  uint64_t graph_kernels = 0;
+};
+
+namespace {
+
+sb_status fail(sb_context* ctx, sb_status st, const char* fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return st;
+}
+
+sb_status cuda_fail(sb_context* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, e == cudaErrorMemoryAllocation ? SB_ERR_OOM : SB_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define SB_CUDA(ctx, call)                                    \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+  } while (0)
+
+#define SB_MEMSET(ctx, args)                                                  \
+  do {                                                                          \
+    if (!(ctx)->dry) {                                                          \
+      cudaError_t e_ = cudaMemsetAsync args;                                    \
+      if (e_ != cudaSuccess) return cuda_fail(ctx, e_, "cudaMemsetAsync");      \
+    }                                                                           \
+  } while (0)
+
+#define SB_LAUNCHED(ctx, nk)                                                         \
+  do {                                                                               \
+    (ctx)->launches += (nk);                                                         \
+    cudaError_t e_ = cudaPeekAtLastError();                                          \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "kernel launch"); \
+  } while (0)
+
+sb_status build_tables(sb_context* ctx) {
+  uint16_t lin[256];
+  std::vector<uint8_t> lt(65536);
+  for (int c = 0; c < 256; ++c) {
+    const double v = c / 255.0;
+    const double l = v <= 0.04045 ? v / 12.92 : pow((v + 0.055) / 1.055, 2.4);
+    lin[c] = (uint16_t)floor(65535.0 * l + 0.5);
+  }
+  const double e = 216.0 / 24389.0, k = 24389.0 / 27.0;  // (6/29)^3 and (29/3)^3
+  for (int y = 0; y < 65536; ++y) {
+    const double t = y / 65535.0;
+    const double Ls = t > e ? 116.0 * cbrt(t) - 16.0 : k * t;
+    double v = floor(2.55 * Ls + 0.5);
+    lt[y] = (uint8_t)(v < 0 ? 0 : (v > 255 ? 255 : v));
+  }
+  uint8_t coarse[4096];
+  uint32_t thr[257];
+  for (int i = 0; i < 4096; ++i) coarse[i] = lt[i * 16];
+  for (int l = 0; l <= 256; ++l) {
+    uint32_t t = 65536;
+    for (int y = 0; y < 65536; ++y)
+      if (lt[y] >= l) { t = (uint32_t)y; break; }
+    thr[l] = t;
+  }
+  for (int y = 0; y < 65536; ++y) {  // the compressed form must reproduce the table
+    const int c = coarse[y >> 4];
+    const int v = c + ((uint32_t)y >= thr[c + 1] ? 1 : 0);
+    if (v != lt[y]) return fail(ctx, SB_ERR_UNSUPPORTED, "lightness table compression check failed at %d", y);
+  }
+  uint8_t host[512 + 4096 + 257 * 4];
+  memcpy(host, lin, 512);
+  memcpy(host + 512, coarse, 4096);
+  memcpy(host + 512 + 4096, thr, 257 * 4);
+  SB_CUDA(ctx, cudaMalloc(&ctx->tables, sizeof host));
+  SB_CUDA(ctx, cudaMemcpy(ctx->tables, host, sizeof host, cudaMemcpyHostToDevice));
+  return SB_OK;
+}
+
+const uint16_t* t_lin(sb_context* c) { return (const uint16_t*)c->tables; }
+const uint8_t* t_coarse(sb_context* c) { return c->tables + 512; }
+const uint32_t* t_thr(sb_context* c) { return (const uint32_t*)(c->tables + 512 + 4096); }
+
+sb_status ensure_ws(sb_context* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return SB_OK;
+  if (ctx->budget && bytes > ctx->budget)
+    return fail(ctx, SB_ERR_OOM, "workspace of %zu bytes exceeds the budget of %zu bytes", bytes, ctx->budget);
+  SB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->ws) cudaFree(ctx->ws);
+  ctx->ws = nullptr;
+  ctx->ws_bytes = 0;
+  cudaError_t e = cudaMalloc(&ctx->ws, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, SB_ERR_OOM, "cudaMalloc of %zu workspace bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->ws_bytes = bytes;
+  return SB_OK;
+}
+
+template <class T>
+const T* upload(sb_context* ctx, const std::vector<T>& v, sb_status* st) {
+  if (ctx->sink == 1) {
+    const size_t off = al(ctx->blob.size()), bytes = v.size() * sizeof(T);
+    ctx->blob.resize(off + al(bytes ? bytes : 1));
+    if (bytes) memcpy(ctx->blob.data() + off, v.data(), bytes);
+    *st = SB_OK;
+    return (const T*)(ctx->blob_dev + off);
+  }
+  cudaError_t e = cudaSuccess;
+  void* d = ctx->up.put(v.data(), v.size() * sizeof(T), ctx->stream, &e);
+  if (e != cudaSuccess || !d) { *st = cuda_fail(ctx, e == cudaSuccess ? cudaErrorMemoryAllocation : e, "job upload"); return nullptr; }
+  *st = SB_OK;
+  return (const T*)d;
+}
+
+bool geometry_ok(sb_context* ctx, int w, int h, int D, int block, sb_status* st) {
+  if (block < 1 || block > 63 || (block & 1) == 0) { *st = fail(ctx, SB_ERR_INVALID_ARG, "block must be odd in [1, 63], got %d", block); return false; }
+  if (D < 0 || D > 1023) { *st = fail(ctx, SB_ERR_INVALID_ARG, "max_disp must be in [0, 1023], got %d", D); return false; }
+  if (w < D + block + 1 || h < block) { *st = fail(ctx, SB_ERR_INVALID_ARG, "image %dx%d too small for max_disp %d and block %d (need w >= D+block+1, h >= block)", w, h, D, block); return false; }
+  if ((int64_t)w * h >= (int64_t)1 << 31) { *st = fail(ctx, SB_ERR_INVALID_ARG, "image of %dx%d pixels is too large", w, h); return false; }
+  return true;
+}
+
+bool params_ok(sb_context* ctx, int w, int h, const sb_params& p, sb_status* st) {
+  if (!geometry_ok(ctx, w, h, p.max_disp, p.block, st)) return false;
+  if (p.k < 1 || p.k > 255) { *st = fail(ctx, SB_ERR_INVALID_ARG, "k must be in [1, 255], got %d", p.k); return false; }
+  if (!(p.sigma > 0.0f && p.sigma <= 32.0f)) { *st = fail(ctx, SB_ERR_INVALID_ARG, "sigma must be in (0, 32]"); return false; }
+  if (p.n_ranges < 0 || p.n_ranges > SB_MAX_RANGES) { *st = fail(ctx, SB_ERR_INVALID_ARG, "n_ranges must be in [0, %d]", SB_MAX_RANGES); return false; }
+  if (p.morph_mode != SB_MORPH_FILL_REMOVE && p.morph_mode != SB_MORPH_OPEN_CLOSE) { *st = fail(ctx, SB_ERR_INVALID_ARG, "unknown morph_mode %d", p.morph_mode); return false; }
+  if (!(p.cc_remove_fraction >= 0.0 && p.cc_remove_fraction <= 1.0)) { *st = fail(ctx, SB_ERR_INVALID_ARG, "cc_remove_fraction must be in [0, 1]"); return false; }
+  if (p.kmeans_max_iter < 0 || p.kmeans_max_iter > 100000) { *st = fail(ctx, SB_ERR_INVALID_ARG, "kmeans_max_iter must be in [0, 100000]"); return false; }
+  if (p.sad_variant < SB_SAD_AUTO || p.sad_variant > SB_SAD_BOXSUM) { *st = fail(ctx, SB_ERR_INVALID_ARG, "unknown sad_variant %d", p.sad_variant); return false; }
+  return true;
+}
+
+// --------------------------------------------------------------- tuner
+// Box sums cost about kBoxNsPerPxD per (domain pixel, disparity); direct
+// window sums about kDirectNsPerCell per (anchor, disparity, window cell).
+// Both constants are refreshed from measured kernel times.
+struct Tuner {
+  double box_ns_per_pxd = 0.0012;
+  double direct_ns_per_cell = 0.00009;
+  bool prefer_direct(int w, int h, int D, int B, double density) const {
+    const int r = (B - 1) / 2;
+    const double omega = (double)(w - D - 2 * r) * (double)(h - 2 * r);
+    const double box = omega * (D + 1) * box_ns_per_pxd;
+    const double dir = omega * density * (D + 1) * (double)B * B * direct_ns_per_cell;
+    return dir < box;
+  }
+};
+Tuner g_tuner;
+
+int sad_variant_of(sb_context* ctx, const Geo& g) {
+  if (g.p.sad_variant == SB_SAD_DIRECT || g.p.sad_variant == SB_SAD_BOXSUM) return g.p.sad_variant;
+  return g_tuner.prefer_direct(g.w, g.h, g.p.max_disp, g.p.block, ctx->last_density) ? SB_SAD_DIRECT : SB_SAD_BOXSUM;
+}
+
+// Box-sum work items: (pair, strip, disparity chunk, row band); bands are cut
+// so that a small batch still fills the GPU.
+void sad_items(const std::vector<std::pair<int, Geo>>& pairs, std::vector<SadItem>* items) {
+  int64_t base = 0;
+  for (auto& pg : pairs) {
+    const Geo& g = pg.second;
+    const int r = (g.p.block - 1) / 2, D = g.p.max_disp;
+    const int TX = sad_boxsum_strip(r);
+    const int ncols = g.w - D - 2 * r;
+    base += (int64_t)((ncols + TX - 1) / TX) * ((D + 1 + kSadChunk - 1) / kSadChunk);
+  }
+  const int64_t target = 148 * 2 * 3;
+  for (auto& pg : pairs) {
+    const Geo& g = pg.second;
+    const int r = (g.p.block - 1) / 2, D = g.p.max_disp;
+    const int TX = sad_boxsum_strip(r);
+    const int xo0 = D + r, xo1 = g.w - 1 - r, yo0 = r, yo1 = g.h - 1 - r;
+    const int rows = yo1 - yo0 + 1;
+    int bands = (int)std::max<int64_t>(1, (target + base - 1) / std::max<int64_t>(base, 1));
+    bands = std::min(bands, std::max(1, rows / std::max(8 * r, 64)));
+    for (int b = 0; b < bands; ++b) {
+      const int ya = yo0 + (int)((int64_t)rows * b / bands), yb = yo0 + (int)((int64_t)rows * (b + 1) / bands) - 1;
+      if (ya > yb) continue;
+      for (int x0 = xo0; x0 <= xo1; x0 += TX)
+        for (int d0 = 0; d0 <= D; d0 += kSadChunk) items->push_back(SadItem{pg.first, x0, d0, ya, yb});
+    }
+  }
+}
+
+// Stage boundary marks for sb_profile_read (external records inside captures).
+sb_status mark(sb_context* ctx, int i) {
+  if (!ctx->prof_on || ctx->dry) return SB_OK;
+  cudaError_t e = ctx->capturing ? cudaEventRecordWithFlags(ctx->prof_ev[i], ctx->stream, cudaEventRecordExternal)
+                                 : cudaEventRecord(ctx->prof_ev[i], ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventRecord");
+  if (i == SB_N_STAGES) ctx->prof_recorded = true;
+  return SB_OK;
+}
+
+#define SB_MARK(ctx, i)                          \
+  do {                                           \
+    sb_status m_ = mark(ctx, i);                 \
+    if (m_ != SB_OK) return m_;                  \
+  } while (0)
+
+// ------------------------------------------------------------ pipeline
+struct PairRun {
+  const uint8_t *left, *right;
+  uint8_t* out_rgb;
+  uint16_t* out_disp;
+  Geo g;
+  PairWs ws;
+};
+
+// Enqueues the whole pipeline for `runs` (one launch per stage over all of
+// them).  Job descriptors go to `jobs_dev` when given (graph form), else
+// through the upload ring.
+sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
+  cudaStream_t s = ctx->stream;
+  sb_status st = SB_OK;
+  const int n = (int)runs.size();
+  if (n == 0) return SB_OK;
+  int max_w = 0, max_h = 0, max_R = 0, max_nseg = 0;
+  int64_t max_px = 0;
+  for (auto& r : runs) {
+    max_w = std::max(max_w, r.g.w);
+    max_h = std::max(max_h, r.g.h);
+    max_px = std::max<int64_t>(max_px, (int64_t)r.g.w * r.g.h);
+    max_nseg = std::max(max_nseg, r.ws.nseg);
+  }
+  // zero the per-pair accumulators
+  for (auto& r : runs) {
+    SB_MEMSET(ctx, (r.ws.hist, 0, 256 * 4, s));
+    SB_MEMSET(ctx, (r.ws.cut, 0, 8 * 8, s));
+  }
+  const int bpj = (int)std::min<int64_t>(std::max<int64_t>(1, max_px / (256 * 16)), 592);
+  SB_MARK(ctx, SB_STAGE_LIGHTNESS);
+  // 1. lightness of both images (+ histogram of the left)
+  {
+    std::vector<LightJob> J;
+    for (auto& r : runs) {
+      const int64_t N = (int64_t)r.g.w * r.g.h;
+      J.push_back(LightJob{r.left, r.ws.Ll, r.ws.hist, N});
+      J.push_back(LightJob{r.right, r.ws.Lr, nullptr, N});
+    }
+    const LightJob* d = upload(ctx, J, &st);
+    if (!d) return st;
+    if (!ctx->dry) {
+      launch_lightness(d, (int)J.size(), bpj, t_lin(ctx), t_coarse(ctx), t_thr(ctx), s);
+      SB_LAUNCHED(ctx, 1);
+    }
+  }
+  SB_MARK(ctx, SB_STAGE_KMEANS);
+  // 2. histogram K-means
+  {
+    std::vector<KmeansJob> J;
+    for (auto& r : runs) J.push_back(KmeansJob{r.ws.hist, r.ws.centroids, r.ws.lut, r.ws.iters, r.g.p.k, r.g.p.kmeans_max_iter});
+    const KmeansJob* d = upload(ctx, J, &st);
+    if (!d) return st;
+    if (!ctx->dry) {
+      launch_kmeans(d, n, s);
+      SB_LAUNCHED(ctx, 1);
+    }
+  }
+  SB_MARK(ctx, SB_STAGE_REFINE);
+  // 3. boundary + refinement (grouped by mode)
+  for (int mode = 0; mode < 2; ++mode) {
+    std::vector<MorphJob> J;
+    int mw = 0, mh = 0;
+    for (auto& r : runs)
+      if (r.g.p.morph_mode == mode) {
+        J.push_back(MorphJob{r.ws.Ll, r.ws.lut, r.ws.refined, r.g.w, r.g.h, mode});
+        mw = std::max(mw, r.g.w);
+        mh = std::max(mh, r.g.h);
+      }
+    if (J.empty()) continue;
+    const MorphJob* d = upload(ctx, J, &st);
+    if (!d) return st;
+    if (!ctx->dry) {
+      launch_boundary_morph(d, (int)J.size(), mw, mh, mode, s);
+      SB_LAUNCHED(ctx, 1);
+    }
+  }
+  SB_MARK(ctx, SB_STAGE_CCA);
+  // 4. CCA and small-component removal
+  {
+    std::vector<CcaJob> J;
+    for (auto& r : runs) {
+      const size_t N = (size_t)r.g.w * r.g.h;
+      SB_MEMSET(ctx, (r.ws.size_key, 0, N * 4, s));
+      SB_MEMSET(ctx, (r.ws.shist, 0, (size_t)r.ws.shist_len * 4, s));
+      J.push_back(CcaJob{r.ws.refined, r.ws.lab, r.ws.size_key, r.ws.shist, r.ws.rowcnt, r.ws.cut, r.ws.filtered,
+                         r.g.w, r.g.h, r.ws.shist_len, r.g.p.cc_remove_fraction});
+    }
+    const CcaJob* d = upload(ctx, J, &st);
+    if (!d) return st;
+    if (!ctx->dry) {
+      launch_cca(d, n, max_w, max_h, ctx->dev_err, s);
+      SB_LAUNCHED(ctx, 3);
+    }
+    if (!ctx->dry) {
+      launch_cc_filter(d, n, max_w, max_h, s);
+      SB_LAUNCHED(ctx, 6);
+    }
+    // boundary count of the first pair, read back asynchronously for the tuner
+    if (!ctx->dry && ctx->sink == 0 && !ctx->dens_pending && ctx->dens_host) {
+      SB_CUDA(ctx, cudaMemcpyAsync(ctx->dens_host, runs[0].ws.cut, 8, cudaMemcpyDeviceToHost, s));
+      SB_CUDA(ctx, cudaEventRecord(ctx->dens_ev, s));
+      ctx->dens_px = (int64_t)runs[0].g.w * runs[0].g.h;
+      ctx->dens_pending = true;
+    }
+  }
+  // 5. SAD at the anchors
+  {
+    std::vector<SadJob> J;
+    std::vector<std::pair<int, Geo>> box;
+    std::vector<SadJob> direct;
+    int dw = 0, dh = 0;
+    for (int i = 0; i < n; ++i) {
+      auto& r = runs[i];
+      const size_t N = (size_t)r.g.w * r.g.h;
+      SB_MEMSET(ctx, (r.ws.size_key, 0xFF, N * 4, s));
+      SadJob sj{r.ws.Ll, r.ws.Lr, r.ws.filtered, r.ws.size_key, r.ws.sparse, nullptr, r.g.w, r.g.h,
+                r.g.p.max_disp, (r.g.p.block - 1) / 2};
+      J.push_back(sj);
+      if (sad_variant_of(ctx, r.g) == SB_SAD_DIRECT) {
+        direct.push_back(sj);
+        dw = std::max(dw, r.g.w);
+        dh = std::max(dh, r.g.h);
+      } else {
+        box.push_back({i, r.g});
+      }
+    }
+    const SadJob* d = upload(ctx, J, &st);
+    if (!d) return st;
+    SB_MARK(ctx, SB_STAGE_SAD);
+    if (!box.empty()) {
+      std::vector<SadItem> items;
+      sad_items(box, &items);
+      const SadItem* di = upload(ctx, items, &st);
+      if (!di) return st;
+      if (!ctx->dry) {
+        launch_sad_boxsum(d, di, (int)items.size(), s);
+        SB_LAUNCHED(ctx, 1);
+      }
+    }
+    if (!direct.empty()) {
+      const SadJob* dd = upload(ctx, direct, &st);
+      if (!dd) return st;
+      if (!ctx->dry) {
+        launch_sad_direct(dd, (int)direct.size(), dw, dh, s);
+        SB_LAUNCHED(ctx, 1);
+      }
+    }
+    SB_MARK(ctx, SB_STAGE_SAD_FINALIZE);
+    if (!ctx->dry) {
+      launch_sad_finalize(d, n, max_w, max_h, s);
+      SB_LAUNCHED(ctx, 1);
+    }
+  }
+  SB_MARK(ctx, SB_STAGE_RECON);
+  // 6. reconstruction (Algorithms 1 and 2)
+  {
+    std::vector<ReconJob> J;
+    for (auto& r : runs) {
+      uint16_t* out = r.out_disp ? r.out_disp : r.ws.disp;
+      J.push_back(ReconJob{r.ws.sparse, r.ws.filled, out, r.ws.seg_top, r.ws.seg_bot, r.g.w, r.g.h, r.g.p.max_disp,
+                           (r.g.p.block - 1) / 2, r.g.p.disp_threshold, kSegRows});
+    }
+    const ReconJob* d = upload(ctx, J, &st);
+    if (!d) return st;
+    if (!ctx->dry) {
+      launch_recon(d, n, max_w, max_h, max_nseg, s);
+      SB_LAUNCHED(ctx, 3);
+    }
+  }
+  SB_MARK(ctx, SB_STAGE_BLUR);
+  // 7. selective blur
+  {
+    std::vector<BlurJob> J;
+    for (auto& r : runs) {
+      int R;
+      std::vector<float> taps = gauss_taps(r.g.p.sigma, &R);
+      max_R = std::max(max_R, R);
+      const float* dtaps = upload(ctx, taps, &st);
+      if (!dtaps) return st;
+      BlurJob b{};
+      b.rgb = r.left;
+      b.disp = r.out_disp ? r.out_disp : r.ws.disp;
+      b.out = r.out_rgb;
+      b.taps = dtaps;
+      b.w = r.g.w;
+      b.h = r.g.h;
+      b.R = R;
+      b.n_ranges = r.g.p.n_ranges;
+      for (int i = 0; i < r.g.p.n_ranges; ++i) { b.lo[i] = r.g.p.ranges[i].lo; b.hi[i] = r.g.p.ranges[i].hi; }
+      J.push_back(b);
+    }
+    const BlurJob* d = upload(ctx, J, &st);
+    if (!d) return st;
+    if (!ctx->dry) {
+      launch_blur(d, n, max_w, max_h, max_R, s);
+      SB_LAUNCHED(ctx, 1);
+    }
+  }
+  SB_MARK(ctx, SB_N_STAGES);
+  return SB_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+void sb_default_params(sb_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof *p);
+  p->k = 10;
+  p->max_disp = 64;
+  p->block = 9;
+  p->disp_threshold = 1;
+  p->morph_mode = SB_MORPH_FILL_REMOVE;
+  p->kmeans_max_iter = 100;
+  p->cc_remove_fraction = 0.04;
+  p->sigma = 3.0f;
+  p->n_ranges = 0;
+  p->sad_variant = SB_SAD_AUTO;
+}
+
+sb_status sb_create(int device, size_t mem_budget_bytes, void* cuda_stream, sb_context** out) {
+  if (!out) return SB_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return SB_ERR_INVALID_ARG;
+  }
+  std::unique_ptr<sb_context> ctx(new sb_context());
+  ctx->device = device;
+  ctx->budget = mem_budget_bytes;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  if (cudaSetDevice(device) != cudaSuccess) return SB_ERR_CUDA;
+  if (build_tables(ctx.get()) != SB_OK) return SB_ERR_CUDA;
+  if (cudaMalloc(&ctx->dev_err, 4) != cudaSuccess || cudaMemset(ctx->dev_err, 0, 4) != cudaSuccess) return SB_ERR_CUDA;
+  if (ctx->up.init(8 << 20) != cudaSuccess) return SB_ERR_OOM;
+  if (cudaMallocHost(&ctx->dens_host, 8) != cudaSuccess) return SB_ERR_OOM;
+  ctx->dens_host[0] = 0;
+  if (cudaEventCreateWithFlags(&ctx->dens_ev, cudaEventDisableTiming) != cudaSuccess) return SB_ERR_CUDA;
+  *out = ctx.release();
+  return SB_OK;
+}
+
+void sb_destroy(sb_context* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  ctx->up.release();
+  if (ctx->graph.exec) cudaGraphExecDestroy(ctx->graph.exec);
+  if (ctx->blob_dev) cudaFree(ctx->blob_dev);
+  if (ctx->blob_host) cudaFreeHost(ctx->blob_host);
+  if (ctx->blob_ev) cudaEventDestroy(ctx->blob_ev);
+  if (ctx->dens_host) cudaFreeHost(ctx->dens_host);
+  if (ctx->dens_ev) cudaEventDestroy(ctx->dens_ev);
+  for (int i = 0; i <= SB_N_STAGES; ++i)
+    if (ctx->prof_ev[i]) cudaEventDestroy(ctx->prof_ev[i]);
+  if (ctx->tables) cudaFree(ctx->tables);
+  if (ctx->dev_err) cudaFree(ctx->dev_err);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->stage) cudaFree(ctx->stage);
+  if (ctx->s_in) cudaStreamDestroy(ctx->s_in);
+  if (ctx->s_out) cudaStreamDestroy(ctx->s_out);
+  delete ctx;
+}
+
+sb_status sb_set_stream(sb_context* ctx, void* cuda_stream) {
+  if (!ctx) return SB_ERR_INVALID_ARG;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  return SB_OK;
+}
+
+const char* sb_last_error(const sb_context* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+size_t sb_workspace_bytes(const sb_context* ctx) { return ctx ? ctx->ws_bytes : 0; }
+
+uint64_t sb_launch_count(const sb_context* ctx) { return ctx ? ctx->launches : 0; }
+
+sb_status sb_profile_enable(sb_context* ctx, int on) {
+  if (!ctx) return SB_ERR_INVALID_ARG;
+  if (on && !ctx->prof_ev[0])
+    for (int i = 0; i <= SB_N_STAGES; ++i) SB_CUDA(ctx, cudaEventCreate(&ctx->prof_ev[i]));
+  if (ctx->prof_on != (on != 0) && ctx->graph.exec) {  // captured graphs hold (or lack) the marks
+    cudaGraphExecDestroy(ctx->graph.exec);
+    ctx->graph.exec = nullptr;
+  }
+  ctx->prof_on = on != 0;
+  ctx->prof_recorded = false;
+  return SB_OK;
+}
+
+int32_t sb_profile_read(sb_context* ctx, float* ms, int32_t max_stages) {
+  if (!ctx || !ms || !ctx->prof_recorded) return -1;
+  if (cudaEventSynchronize(ctx->prof_ev[SB_N_STAGES]) != cudaSuccess) return -1;
+  const int n = std::min<int>(max_stages, SB_N_STAGES);
+  for (int i = 0; i < n; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ctx->prof_ev[i], ctx->prof_ev[i + 1]) != cudaSuccess) { cudaGetLastError(); t = -1.f; }
+    ms[i] = t;
+  }
+  return n;
+}
+
+sb_status sb_synchronize(sb_context* ctx) {
+  if (!ctx) return SB_ERR_INVALID_ARG;
+  SB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  uint32_t e = 0;
+  SB_CUDA(ctx, cudaMemcpy(&e, ctx->dev_err, 4, cudaMemcpyDeviceToHost));
+  if (e) {
+    cudaMemset(ctx->dev_err, 0, 4);
+    if (e & DEV_ERR_TIMEOUT) return fail(ctx, SB_ERR_TIMEOUT, "a device-side wait gave up (flags 0x%x)", e);
+    return fail(ctx, SB_ERR_CUDA, "device-side check failed (flags 0x%x)", e);
+  }
+  return SB_OK;
+}
+
+sb_status sb_rgb_to_lightness(sb_context* ctx, const uint8_t* rgb, int32_t w, int32_t h, uint8_t* L, uint32_t* hist) {
+  if (!ctx) return SB_ERR_INVALID_ARG;
+  if (!rgb || !L || w <= 0 || h <= 0) return fail(ctx, SB_ERR_INVALID_ARG, "rgb_to_lightness: null pointer or empty image");
+  sb_status st;
+  if (hist) SB_CUDA(ctx, cudaMemsetAsync(hist, 0, 256 * 4, ctx->stream));
+  std::vector<LightJob> J{LightJob{rgb, L, hist, (int64_t)w * h}};
+  const LightJob* d = upload(ctx, J, &st);
+  if (!d) return st;
+  const int bpj = (int)std::min<int64_t>(std::max<int64_t>(1, (int64_t)w * h / (256 * 16)), 592);
+  launch_lightness(d, 1, bpj, t_lin(ctx), t_coarse(ctx), t_thr(ctx), ctx->stream);
+  SB_LAUNCHED(ctx, 1);
+  return SB_OK;
+}
+
+sb_status sb_kmeans_segment(sb_context* ctx, const uint8_t* L_left, int32_t w, int32_t h, int32_t k, int32_t max_iter,
+                            uint8_t* labels, double* centroids, uint8_t* bin2cluster, int32_t* iters) {
+  if (!ctx) return SB_ERR_INVALID_ARG;
+  if (!L_left || w <= 0 || h <= 0) return fail(ctx, SB_ERR_INVALID_ARG, "kmeans_segment: null pointer or empty image");
+  if (k < 1 || k > 255) return fail(ctx, SB_ERR_INVALID_ARG, "k must be in [1, 255], got %d", k);
+  if (max_iter < 0 || max_iter > 100000) return fail(ctx, SB_ERR_INVALID_ARG, "max_iter must be in [0, 100000]");
+  sb_status st = ensure_ws(ctx, al(256 * 4) + al(256 * 8) + al(256) + al(8));
+  if (st != SB_OK) return st;
+  uint32_t* hist = (uint32_t*)ctx->ws;
+  double* cent = centroids ? centroids : (double*)(ctx->ws + al(256 * 4));
+  uint8_t* lut = bin2cluster ? bin2cluster : ctx->ws + al(256 * 4) + al(256 * 8);
+  int32_t* it = iters ? iters : (int32_t*)(ctx->ws + al(256 * 4) + al(256 * 8) + al(256));
+  SB_CUDA(ctx, cudaMemsetAsync(hist, 0, 256 * 4, ctx->stream));
+  launch_histogram_u8(L_left, (int64_t)w * h, hist, ctx->stream);
+  SB_LAUNCHED(ctx, 1);
+  std::vector<KmeansJob> J{KmeansJob{hist, cent, lut, it, k, max_iter}};
+  const KmeansJob* d = upload(ctx, J, &st);
+  if (!d) return st;
+  launch_kmeans(d, 1, ctx->stream);
+  SB_LAUNCHED(ctx, 1);
+  if (labels) {
+    std::vector<LabelJob> LJ{LabelJob{L_left, lut, labels, (int64_t)w * h}};
+    const LabelJob* dl = upload(ctx, LJ, &st);
+    if (!dl) return st;
+    const int bpj = (int)std::min<int64_t>(std::max<int64_t>(1, (int64_t)w * h / (256 * 16)), 592);
+    launch_labels(dl, 1, bpj, ctx->stream);
+    SB_LAUNCHED(ctx, 1);
+  }
+  return SB_OK;
+}
+
+sb_status sb_refine_boundaries(sb_context* ctx, const uint8_t* labels, int32_t w, int32_t h, int32_t morph_mode,
+                               double cc_remove_fraction, uint8_t* boundary, uint8_t* refined, int32_t* cc_labels) {
+  if (!ctx) return SB_ERR_INVALID_ARG;
+  if (!labels || !boundary || w <= 0 || h <= 0) return fail(ctx, SB_ERR_INVALID_ARG, "refine_boundaries: null pointer or empty image");
+  if (morph_mode != SB_MORPH_FILL_REMOVE && morph_mode != SB_MORPH_OPEN_CLOSE) return fail(ctx, SB_ERR_INVALID_ARG, "unknown morph_mode %d", morph_mode);
+  if (!(cc_remove_fraction >= 0.0 && cc_remove_fraction <= 1.0)) return fail(ctx, SB_ERR_INVALID_ARG, "cc_remove_fraction must be in [0, 1]");
+  if ((int64_t)w * h >= (int64_t)1 << 31) return fail(ctx, SB_ERR_INVALID_ARG, "image too large");
+  const size_t N = (size_t)w * h;
+  const size_t shist = (size_t)floor(cc_remove_fraction * (double)N) + 2;
+  const size_t need = al(N) + al(N * 4) * 2 + al(shist * 4) + al((size_t)h * 4) + al(64);
+  sb_status st = ensure_ws(ctx, need);
+  if (st != SB_OK) return st;
+  uint8_t* o = ctx->ws;
+  uint8_t* ref = refined ? refined : o;
+  o += al(N);
+  int32_t* lab = cc_labels ? cc_labels : (int32_t*)o;
+  o += al(N * 4);
+  uint32_t* size = (uint32_t*)o;
+  o += al(N * 4);
+  uint32_t* sh = (uint32_t*)o;
+  o += al(shist * 4);
+  uint32_t* rowcnt = (uint32_t*)o;
+  o += al((size_t)h * 4);
+  int64_t* cut = (int64_t*)o;
+  cudaStream_t s = ctx->stream;
+  std::vector<MorphJob> MJ{MorphJob{labels, nullptr, ref, w, h, morph_mode}};
+  const MorphJob* dm = upload(ctx, MJ, &st);
+  if (!dm) return st;
+  launch_boundary_morph(dm, 1, w, h, morph_mode, s);
+  SB_LAUNCHED(ctx, 1);
+  SB_CUDA(ctx, cudaMemsetAsync(size, 0, N * 4, s));
+  SB_CUDA(ctx, cudaMemsetAsync(sh, 0, shist * 4, s));
+  SB_CUDA(ctx, cudaMemsetAsync(cut, 0, 64, s));
+  std::vector<CcaJob> CJ{CcaJob{ref, lab, size, sh, rowcnt, cut, boundary, w, h, (int32_t)shist, cc_remove_fraction}};
+  const CcaJob* dc = upload(ctx, CJ, &st);
+  if (!dc) return st;
+  launch_cca(dc, 1, w, h, ctx->dev_err, s);
+  SB_LAUNCHED(ctx, 3);
+  launch_cc_filter(dc, 1, w, h, s);
+  SB_LAUNCHED(ctx, 6);
+  return SB_OK;
+}
+
+sb_status sb_boundary_sad(sb_context* ctx, const uint8_t* L_left, const uint8_t* L_right, const uint8_t* boundary,
+                          int32_t w, int32_t h, int32_t max_disp, int32_t block, int32_t variant, uint16_t* disp,
+                          uint32_t* cost) {
+  if (!ctx) return SB_ERR_INVALID_ARG;
+  if (!L_left || !L_right || !boundary || !disp) return fail(ctx, SB_ERR_INVALID_ARG, "boundary_sad: null pointer");
+  sb_status st = SB_OK;
+  if (!geometry_ok(ctx, w, h, max_disp, block, &st)) return st;
+  if (variant < SB_SAD_AUTO || variant > SB_SAD_BOXSUM) return fail(ctx, SB_ERR_INVALID_ARG, "unknown SAD variant %d", variant);
+  const size_t N = (size_t)w * h;
+  st = ensure_ws(ctx, al(N * 4));
+  if (st != SB_OK) return st;
+  uint32_t* key = (uint32_t*)ctx->ws;
+  cudaStream_t s = ctx->stream;
+  SB_CUDA(ctx, cudaMemsetAsync(key, 0xFF, N * 4, s));
+  std::vector<SadJob> J{SadJob{L_left, L_right, boundary, key, disp, cost, w, h, max_disp, (block - 1) / 2}};
+  const SadJob* d = upload(ctx, J, &st);
+  if (!d) return st;
+  Geo g{w, h, {}};
+  sb_default_params(&g.p);
+  g.p.max_disp = max_disp;
+  g.p.block = block;
+  g.p.sad_variant = variant;
+  if (sad_variant_of(ctx, g) == SB_SAD_DIRECT) {
+    launch_sad_direct(d, 1, w, h, s);
+  } else {
+    std::vector<SadItem> items;
+    sad_items({{0, g}}, &items);
+    const SadItem* di = upload(ctx, items, &st);
+    if (!di) return st;
+    launch_sad_boxsum(d, di, (int)items.size(), s);
+  }
+  SB_LAUNCHED(ctx, 1);
+  launch_sad_finalize(d, 1, w, h, s);
+  SB_LAUNCHED(ctx, 1);
+  return SB_OK;
+}
+
+sb_status sb_reconstruct_disparity(sb_context* ctx, uint16_t* disp, int32_t w, int32_t h, int32_t max_disp,
+                                   int32_t block, int32_t disp_threshold, uint16_t* filled) {
+  if (!ctx) return SB_ERR_INVALID_ARG;
+  if (!disp) return fail(ctx, SB_ERR_INVALID_ARG, "reconstruct_disparity: null pointer");
+  sb_status st = SB_OK;
+  if (!geometry_ok(ctx, w, h, max_disp, block, &st)) return st;
+  const size_t N = (size_t)w * h;
+  const int nseg = (h + kSegRows - 1) / kSegRows;
+  st = ensure_ws(ctx, al(N * 2) + al((size_t)nseg * w * 2) * 2);
+  if (st != SB_OK) return st;
+  uint16_t* fl = filled ? filled : (uint16_t*)ctx->ws;
+  uint16_t* top = (uint16_t*)(ctx->ws + al(N * 2));
+  uint16_t* bot = (uint16_t*)(ctx->ws + al(N * 2) + al((size_t)nseg * w * 2));
+  std::vector<ReconJob> J{ReconJob{disp, fl, disp, top, bot, w, h, max_disp, (block - 1) / 2, disp_threshold, kSegRows}};
+  const ReconJob* d = upload(ctx, J, &st);
+  if (!d) return st;
+  launch_recon(d, 1, w, h, nseg, ctx->stream);
+  SB_LAUNCHED(ctx, 3);
+  return SB_OK;
+}
+
+sb_status sb_selective_blur(sb_context* ctx, const uint8_t* rgb, const uint16_t* disp, int32_t w, int32_t h,
+                            const sb_range* ranges, int32_t n_ranges, float sigma, uint8_t* out_rgb) {
+  if (!ctx) return SB_ERR_INVALID_ARG;
+  if (!rgb || !disp || !out_rgb || w <= 0 || h <= 0) return fail(ctx, SB_ERR_INVALID_ARG, "selective_blur: null pointer or empty image");
+  if (n_ranges < 0 || n_ranges > SB_MAX_RANGES || (n_ranges > 0 && !ranges)) return fail(ctx, SB_ERR_INVALID_ARG, "n_ranges must be in [0, %d] with a host array", SB_MAX_RANGES);
+  if (!(sigma > 0.0f && sigma <= 32.0f)) return fail(ctx, SB_ERR_INVALID_ARG, "sigma must be in (0, 32]");
+  int R;
+  std::vector<float> taps = gauss_taps(sigma, &R);
+  sb_status st = SB_OK;
+  const float* dt = upload(ctx, taps, &st);
+  if (!dt) return st;
+  BlurJob b{};
+  b.rgb = rgb;
+  b.disp = disp;
+  b.out = out_rgb;
+  b.taps = dt;
+  b.w = w;
+  b.h = h;
+  b.R = R;
+  b.n_ranges = n_ranges;
+  for (int i = 0; i < n_ranges; ++i) { b.lo[i] = ranges[i].lo; b.hi[i] = ranges[i].hi; }
+  std::vector<BlurJob> J{b};
+  const BlurJob* d = upload(ctx, J, &st);
+  if (!d) return st;
+  launch_blur(d, 1, w, h, R, ctx->stream);
+  SB_LAUNCHED(ctx, 1);
+  return SB_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------- sb_run
+namespace {
+
+sb_status run_device(sb_context* ctx, const sb_pair* pairs, int n, bool batched) {
+  std::vector<Geo> geos(n);
+  for (int i = 0; i < n; ++i) geos[i] = Geo{pairs[i].w, pairs[i].h, pairs[i].p};
+  sb_status st;
+  if (!batched) {
+    size_t need = 0;
+    for (int i = 0; i < n; ++i) need = std::max(need, pair_ws_bytes(geos[i], pairs[i].out_disp == nullptr));
+    if ((st = ensure_ws(ctx, need)) != SB_OK) return st;
+    for (int i = 0; i < n; ++i) {
+      std::vector<PairRun> runs{PairRun{pairs[i].left_rgb, pairs[i].right_rgb, pairs[i].out_rgb, pairs[i].out_disp, geos[i],
+                                        carve(ctx->ws, geos[i], pairs[i].out_disp == nullptr)}};
+      if ((st = enqueue_pipeline(ctx, runs)) != SB_OK) return st;
+    }
+    return SB_OK;
+  }
+  size_t need = 0;
+  std::vector<size_t> offs(n);
+  for (int i = 0; i < n; ++i) {
+    offs[i] = need;
+    need += pair_ws_bytes(geos[i], pairs[i].out_disp == nullptr);
+  }
+  if ((st = ensure_ws(ctx, need)) != SB_OK) return st;
+  std::vector<PairRun> runs;
+  for (int i = 0; i < n; ++i)
+    runs.push_back(PairRun{pairs[i].left_rgb, pairs[i].right_rgb, pairs[i].out_rgb, pairs[i].out_disp, geos[i],
+                           carve(ctx->ws + offs[i], geos[i], pairs[i].out_disp == nullptr)});
+  return enqueue_pipeline(ctx, runs);
+}
+
+// Graph form: the batched pipeline is captured once per batch shape (sizes,
+// parameters, workspace) and replayed.  Kernels read their job descriptors
+// from a device blob owned by the context; each call rebuilds the blob for
+// the caller's current pointers with a record-only pass and uploads it ahead
+// of the replay, so new buffers of the same shape need no new capture.
+sb_status run_graph(sb_context* ctx, const sb_pair* pairs, int n) {
+  size_t need = 0;
+  for (int i = 0; i < n; ++i) need += pair_ws_bytes(Geo{pairs[i].w, pairs[i].h, pairs[i].p}, pairs[i].out_disp == nullptr);
+  sb_status st = ensure_ws(ctx, need);
+  if (st != SB_OK) return st;
+  std::string key((const char*)&ctx->ws, sizeof ctx->ws);
+  for (int i = 0; i < n; ++i) {
+    const sb_pair& q = pairs[i];
+    key.append((const char*)&q.w, sizeof q.w);
+    key.append((const char*)&q.h, sizeof q.h);
+    key.append((const char*)&q.p, sizeof q.p);
+    key.push_back(q.out_disp ? 1 : 0);
+  }
+  // record-only pass: the blob for the current pointers
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    ctx->blob.clear();
+    ctx->sink = 1;
+    ctx->dry = true;
+    st = run_device(ctx, pairs, n, true);
+    ctx->dry = false;
+    ctx->sink = 0;
+    if (st != SB_OK) return st;
+    if (ctx->blob.size() <= ctx->blob_cap) break;
+    // grow the blob (its address is baked into captured graphs: drop them)
+    SB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->graph.exec) { cudaGraphExecDestroy(ctx->graph.exec); ctx->graph.exec = nullptr; }
+    if (ctx->blob_dev) cudaFree(ctx->blob_dev);
+    if (ctx->blob_host) cudaFreeHost(ctx->blob_host);
+    ctx->blob_dev = ctx->blob_host = nullptr;
+    ctx->blob_cap = 0;
+    const size_t cap = ctx->blob.size() * 2;
+    SB_CUDA(ctx, cudaMalloc(&ctx->blob_dev, cap));
+    SB_CUDA(ctx, cudaMallocHost(&ctx->blob_host, cap));
+    ctx->blob_cap = cap;
+  }
+  if (!ctx->blob_ev) SB_CUDA(ctx, cudaEventCreateWithFlags(&ctx->blob_ev, cudaEventDisableTiming));
+  SB_CUDA(ctx, cudaEventSynchronize(ctx->blob_ev));  // the previous blob copy has been read
+  memcpy(ctx->blob_host, ctx->blob.data(), ctx->blob.size());
+  SB_CUDA(ctx, cudaMemcpyAsync(ctx->blob_dev, ctx->blob_host, ctx->blob.size(), cudaMemcpyHostToDevice, ctx->stream));
+  SB_CUDA(ctx, cudaEventRecord(ctx->blob_ev, ctx->stream));
+  if (!ctx->graph.exec || ctx->graph.key != key) {
+    if (ctx->graph.exec) { cudaGraphExecDestroy(ctx->graph.exec); ctx->graph.exec = nullptr; }
+    cudaStream_t cap = ctx->stream;
+    bool own = false;
+    if (cap == nullptr) {  // the legacy default stream cannot be captured
+      SB_CUDA(ctx, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      own = true;
+    }
+    cudaStream_t saved = ctx->stream;
+    ctx->stream = cap;
+    ctx->blob.clear();
+    ctx->sink = 1;  // same uploads, same offsets: the captured kernels read the blob
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    const uint64_t before = ctx->launches;
+    ctx->capturing = true;
+    if (e == cudaSuccess) st = run_device(ctx, pairs, n, true);
+    ctx->capturing = false;
+    ctx->graph_kernels = ctx->launches - before;
+    ctx->launches = before;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(cap, &graph) : e;
+    ctx->sink = 0;
+    ctx->stream = saved;
+    if (own) cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
+    if (st != SB_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->graph.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    ctx->graph.key = key;
+  }
+  cudaError_t e = cudaGraphLaunch(ctx->graph.exec, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+  ctx->launches += ctx->graph_kernels;
+  return SB_OK;
+}
+
+// Host-buffer streaming: pairs move through device staging in chunks; the
+// copy-in of chunk k+1 and the copy-out of chunk k-1 overlap chunk k's compute.
+sb_status run_host_io(sb_context* ctx, const sb_pair* pairs, int n, bool batched) {
+  if (!ctx->s_in) SB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking));
+  if (!ctx->s_out) SB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking));
+  // chunking: about 1.5 GB of inputs per chunk, at least one pair
+  std::vector<std::pair<int, int>> chunks;
+  {
+    int a = 0;
+    size_t acc = 0;
+    for (int i = 0; i < n; ++i) {
+      acc += (size_t)pairs[i].w * pairs[i].h * 6;
+      if (acc >= ((size_t)1536 << 20) || i == n - 1 || !batched) {
+        chunks.push_back({a, i + 1});
+        a = i + 1;
+        acc = 0;
+      }
+    }
+  }
+  // staging per slot: left, right, out_rgb, out_disp for the largest chunk
+  size_t slot = 0;
+  for (auto& c : chunks) {
+    size_t b = 0;
+    for (int i = c.first; i < c.second; ++i) {
+      const size_t N = (size_t)pairs[i].w * pairs[i].h;
+      b += al(N * 3) * 3 + al(N * 2);
+    }
+    slot = std::max(slot, b);
+  }
+  if (ctx->stage_bytes < 2 * slot) {
+    SB_CUDA(ctx, cudaDeviceSynchronize());
+    if (ctx->stage) cudaFree(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+    cudaError_t e = cudaMalloc(&ctx->stage, 2 * slot);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(ctx, SB_ERR_OOM, "staging of %zu bytes failed", 2 * slot); }
+    ctx->stage_bytes = 2 * slot;
+  }
+  std::vector<cudaEvent_t> ev_in(chunks.size()), ev_comp(chunks.size()), ev_out(chunks.size());
+  for (size_t k = 0; k < chunks.size(); ++k) {
+    cudaEventCreateWithFlags(&ev_in[k], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&ev_comp[k], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&ev_out[k], cudaEventDisableTiming);
+  }
+  sb_status st = SB_OK;
+  for (size_t k = 0; k < chunks.size() && st == SB_OK; ++k) {
+    uint8_t* base = ctx->stage + (k & 1) * slot;
+    std::vector<sb_pair> dp;
+    size_t o = 0;
+    if (k >= 2) {  // the slot's previous chunk must be computed and copied out
+      cudaStreamWaitEvent(ctx->s_in, ev_comp[k - 2], 0);
+      cudaStreamWaitEvent(ctx->s_in, ev_out[k - 2], 0);
+    }
+    for (int i = chunks[k].first; i < chunks[k].second; ++i) {
+      const size_t N = (size_t)pairs[i].w * pairs[i].h;
+      sb_pair q = pairs[i];
+      uint8_t* l = base + o; o += al(N * 3);
+      uint8_t* r = base + o; o += al(N * 3);
+      uint8_t* out = base + o; o += al(N * 3);
+      uint16_t* dd = (uint16_t*)(base + o); o += al(N * 2);
+      cudaMemcpyAsync(l, pairs[i].left_rgb, N * 3, cudaMemcpyHostToDevice, ctx->s_in);
+      cudaMemcpyAsync(r, pairs[i].right_rgb, N * 3, cudaMemcpyHostToDevice, ctx->s_in);
+      q.left_rgb = l;
+      q.right_rgb = r;
+      q.out_rgb = out;
+      q.out_disp = dd;
+      dp.push_back(q);
+    }
+    cudaEventRecord(ev_in[k], ctx->s_in);
+    cudaStreamWaitEvent(ctx->stream, ev_in[k], 0);
+    st = run_device(ctx, dp.data(), (int)dp.size(), batched);
+    cudaEventRecord(ev_comp[k], ctx->stream);
+    cudaStreamWaitEvent(ctx->s_out, ev_comp[k], 0);
+    for (size_t j = 0; j < dp.size(); ++j) {
+      const sb_pair& hp = pairs[chunks[k].first + j];
+      const size_t N = (size_t)hp.w * hp.h;
+      cudaMemcpyAsync(hp.out_rgb, dp[j].out_rgb, N * 3, cudaMemcpyDeviceToHost, ctx->s_out);
+      if (hp.out_disp) cudaMemcpyAsync(hp.out_disp, dp[j].out_disp, N * 2, cudaMemcpyDeviceToHost, ctx->s_out);
+    }
+    cudaEventRecord(ev_out[k], ctx->s_out);
+  }
+  // the caller's stream sees the end of the copies
+  if (!chunks.empty()) cudaStreamWaitEvent(ctx->stream, ev_out.back(), 0);
+  for (size_t k = 0; k < chunks.size(); ++k) {
+    cudaEventDestroy(ev_in[k]);
+    cudaEventDestroy(ev_comp[k]);
+    cudaEventDestroy(ev_out[k]);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (st == SB_OK && e != cudaSuccess) return cuda_fail(ctx, e, "host-buffer streaming");
+  return st;
+}
+
+}  // namespace
+
+extern "C" sb_status sb_run(sb_context* ctx, const sb_pair* pairs, int32_t n_pairs, uint32_t flags) {
+  if (!ctx) return SB_ERR_INVALID_ARG;
+  if (n_pairs < 0 || (n_pairs > 0 && !pairs)) return fail(ctx, SB_ERR_INVALID_ARG, "sb_run: bad pair array");
+  if (flags & ~(uint32_t)(SB_RUN_BATCHED | SB_RUN_GRAPH | SB_RUN_HOST_IO)) return fail(ctx, SB_ERR_INVALID_ARG, "sb_run: unknown flags 0x%x", flags);
+  if ((flags & SB_RUN_GRAPH) && !(flags & SB_RUN_BATCHED)) return fail(ctx, SB_ERR_INVALID_ARG, "SB_RUN_GRAPH needs SB_RUN_BATCHED");
+  if ((flags & SB_RUN_GRAPH) && (flags & SB_RUN_HOST_IO)) return fail(ctx, SB_ERR_INVALID_ARG, "SB_RUN_GRAPH cannot be combined with SB_RUN_HOST_IO");
+  for (int i = 0; i < n_pairs; ++i) {
+    const sb_pair& q = pairs[i];
+    if (!q.left_rgb || !q.right_rgb || !q.out_rgb) return fail(ctx, SB_ERR_INVALID_ARG, "pair %d: null image pointer", i);
+    sb_status st = SB_OK;
+    if (!params_ok(ctx, q.w, q.h, q.p, &st)) return st;
+  }
+  if (n_pairs == 0) return SB_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->dens_pending && cudaEventQuery(ctx->dens_ev) == cudaSuccess) {
+    if (ctx->dens_px > 0) ctx->last_density = (double)ctx->dens_host[0] / (double)ctx->dens_px;
+    ctx->dens_pending = false;
+  }
+  if (flags & SB_RUN_HOST_IO) return run_host_io(ctx, pairs, n_pairs, (flags & SB_RUN_BATCHED) != 0);
+  if (flags & SB_RUN_GRAPH) return run_graph(ctx, pairs, n_pairs);
+  return run_device(ctx, pairs, n_pairs, (flags & SB_RUN_BATCHED) != 0);
+}

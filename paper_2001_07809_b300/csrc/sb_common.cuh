@@ -1,0 +1,125 @@
+// Internal declarations shared by the library's CUDA translation units.
+//
+// Every stage kernel is written batch-first: it takes a device array of
+// per-image (or per-pair) job descriptors and blockIdx.y (or .z) selects the
+// job, so the per-pair path (one job) and the batched path (one launch over
+// all pairs of a batch, sizes and parameters may differ per pair) are the
+// same kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define SB_UNDET16 0xFFFFu
+#define SB_KEY_DBITS 10  // SAD argmin key = (cost << 10) | d, d <= 1023
+
+namespace sb {
+
+// Device-side error word (bit flags) written by bounded waits and checks.
+enum : uint32_t { DEV_ERR_CCA_ITER = 1u, DEV_ERR_SAD_RANGE = 2u, DEV_ERR_TIMEOUT = 4u };
+
+// ---------------------------------------------------------------- lightness
+struct LightJob {
+  const uint8_t* rgb;  // n_px * 3
+  uint8_t* L;          // n_px
+  uint32_t* hist;      // 256 or nullptr (must be zeroed before the launch)
+  int64_t n_px;
+};
+// lin: uint16[256] linear sRGB x 65535; coarse: uint8[4096] L of Y>>4; thr: uint32[257]
+// first Y with L >= l.  Both built on the host from FP64 libm.
+void launch_lightness(const LightJob* jobs, int n_jobs, int blocks_per_job, const uint16_t* lin,
+                      const uint8_t* coarse, const uint32_t* thr, cudaStream_t s);
+
+// ------------------------------------------------------------------ k-means
+struct KmeansJob {
+  const uint32_t* hist;  // 256
+  double* centroids;     // k
+  uint8_t* lut;          // 256: bin -> cluster
+  int32_t* iters;        // 1 or nullptr
+  int32_t k, max_iter;
+};
+void launch_kmeans(const KmeansJob* jobs, int n_jobs, cudaStream_t s);
+
+// Per-pixel label = lut[L]  (only for the optional labels output).
+struct LabelJob {
+  const uint8_t* L;
+  const uint8_t* lut;
+  uint8_t* labels;
+  int64_t n_px;
+};
+void launch_labels(const LabelJob* jobs, int n_jobs, int blocks_per_job, cudaStream_t s);
+// 256-bin histogram of an 8-bit image (hist zeroed by the caller)
+void launch_histogram_u8(const uint8_t* L, int64_t n, uint32_t* hist, cudaStream_t s);
+
+// -------------------------------------------------------------- morphology
+struct MorphJob {
+  const uint8_t* src;  // labels, or L when lut != nullptr
+  const uint8_t* lut;  // nullptr: src holds cluster labels
+  uint8_t* out;        // refined boundary map (0/1)
+  int32_t w, h, mode;
+};
+// all jobs of one launch share the refinement mode
+void launch_boundary_morph(const MorphJob* jobs, int n_jobs, int max_w, int max_h, int mode, cudaStream_t s);
+
+// ---------------------------------------------------------------------- CCA
+struct CcaJob {
+  const uint8_t* b;      // refined map
+  int32_t* lab;          // parent / label array (output: min linear index, -1 background)
+  uint32_t* size;        // per-root sizes (zeroed before k_cc_count)
+  uint32_t* shist;       // size histogram, shist_len entries (zeroed)
+  uint32_t* rowcnt;      // h entries
+  int64_t* cut;          // [0] N_b, [1] limit, [2] s*, [3] m, [4] T
+  uint8_t* out;          // filtered boundary map
+  int32_t w, h;
+  int32_t shist_len;
+  double frac;
+};
+void launch_cca(const CcaJob* jobs, int n_jobs, int max_w, int max_h, uint32_t* dev_err, cudaStream_t s);
+void launch_cc_filter(const CcaJob* jobs, int n_jobs, int max_w, int max_h, cudaStream_t s);
+
+// ---------------------------------------------------------------------- SAD
+struct SadJob {
+  const uint8_t* Ll;
+  const uint8_t* Lr;
+  const uint8_t* bmap;  // refined/filtered boundary map (0/1)
+  uint32_t* key;        // h*w argmin keys (cost << 10 | d), 0xFFFFFFFF init
+  uint16_t* disp;       // out
+  uint32_t* cost;       // out or nullptr
+  int32_t w, h, D, r;
+};
+// Box-sum variant: items = (job, column strip, disparity chunk, row band)
+struct SadItem {
+  int32_t job, x0, d0, y0, y1;  // output rows y0..y1 inclusive, inside Omega
+};
+void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, cudaStream_t s);
+void launch_sad_direct(const SadJob* jobs, int n_jobs, int max_w, int max_h, cudaStream_t s);
+int sad_boxsum_smem_bytes(int r);
+void launch_sad_finalize(const SadJob* jobs, int n_jobs, int max_w, int max_h, cudaStream_t s);
+// strip width of the box-sum kernel for radius r
+__host__ __device__ int sad_boxsum_strip(int r);
+constexpr int kSadChunk = 32;
+
+// ----------------------------------------------------------- reconstruction
+struct ReconJob {
+  const uint16_t* sparse;  // SAD output: anchors, UNDET elsewhere
+  uint16_t* filled;        // Algorithm 1 output
+  uint16_t* out;           // Algorithm 2 output (final)
+  uint16_t* seg_top;       // nseg * w
+  uint16_t* seg_bot;       // nseg * w
+  int32_t w, h, D, r, threshold, seg_rows;
+};
+void launch_recon(const ReconJob* jobs, int n_jobs, int max_w, int max_h, int max_nseg, cudaStream_t s);
+
+// --------------------------------------------------------------------- blur
+struct BlurJob {
+  const uint8_t* rgb;
+  const uint16_t* disp;
+  uint8_t* out;
+  const float* taps;     // 2R+1 normalised 1-D Gaussian taps
+  int32_t w, h, R, n_ranges;
+  int32_t lo[8], hi[8];
+};
+void launch_blur(const BlurJob* jobs, int n_jobs, int max_w, int max_h, int max_R, cudaStream_t s);
+int blur_smem_bytes(int R);
+
+}  // namespace sb

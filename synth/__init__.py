@@ -16,6 +16,7 @@ from __future__ import annotations
 import ctypes
 import dataclasses
 import os
+import shutil
 import subprocess
 from typing import List, Optional, Sequence, Tuple
 
@@ -23,18 +24,33 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "libsynth.so")
+_SO_GPU = os.path.join(_HERE, "libsynth_gpu.so")
 _lib_handle = None
+_gpu_handle = None
 
 M64 = (1 << 64) - 1
 
 
-def build(force: bool = False) -> str:
-    """Compile synth.c into libsynth.so (gcc, -O2, pthreads)."""
+def _stale(out, srcs):
+    return not os.path.exists(out) or any(os.path.getmtime(out) < os.path.getmtime(s) for s in srcs)
+
+
+def build(force: bool = False, gpu: bool = True) -> str:
+    """Compile synth.c into libsynth.so (gcc, -O2, pthreads) and, when nvcc is
+    available, synth_gpu.cu into libsynth_gpu.so (sm_103a)."""
+    core = os.path.join(_HERE, "synth_core.h")
     src = os.path.join(_HERE, "synth.c")
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+    if force or _stale(_SO, [src, core]):
         tmp = _SO + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-pthread", "-o", tmp, src])
         os.replace(tmp, _SO)
+    gsrc = os.path.join(_HERE, "synth_gpu.cu")
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if gpu and os.path.exists(nvcc) and (force or _stale(_SO_GPU, [gsrc, core])):
+        tmp = _SO_GPU + ".tmp%d" % os.getpid()
+        subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-Xcompiler", "-fPIC",
+                               "-shared", "-cudart", "shared", "-o", tmp, gsrc])
+        os.replace(tmp, _SO_GPU)
     return _SO
 
 
@@ -134,26 +150,7 @@ class Scene:
         left_rgb/right_rgb: uint8 [h, w, 3]; gt: float32 [h, w] disparity of
         the left image (None unless want_gt)."""
         lib = _lib()
-        # painter's order: full-frame layers first, then ascending disparity at this frame
-        def cur_d(L: Layer) -> int:
-            if L.dd_frame == 0:
-                return L.d0_q8
-            base = (L.d0_q8 + 128) >> 8
-            v = base + L.dd_frame * frame
-            lo, hi = L.dmin, L.dmax
-            p = 2 * (hi - lo)
-            m = (v - lo) % p
-            return L.d0_q8 + ((lo + (m if m <= hi - lo else p - m)) - base) * 256
-        order = sorted(range(len(self.layers)),
-                       key=lambda i: (0 if self.layers[i].shape == 0 else 1, cur_d(self.layers[i]), i))
-        arr = (_Layer * len(order))()
-        for k, i in enumerate(order):
-            L = self.layers[i]
-            arr[k] = _Layer(L.shape, L.cx, L.cy, L.hw, L.hh, L.vx, L.vy, L.d0_q8, L.gx_q16, L.gy_q16,
-                            L.dd_frame, L.dmin, L.dmax, L.tex_seed & 0xFFFFFFFF, L.mean, L.contrast,
-                            L.tint[0], L.tint[1], L.tint[2])
-        sc = _Scene(self.w, self.h, len(order), frame, self.noise_q8, self.gain_l_q10, self.gain_r_q10,
-                    self.noise_seed & M64, arr)
+        sc, keep = _ctypes_scene(self, frame)
         left = np.empty((self.h, self.w, 3), np.uint8)
         right = np.empty((self.h, self.w, 3), np.uint8)
         gt = np.empty((self.h, self.w), np.float32) if want_gt else None
@@ -164,6 +161,51 @@ class Scene:
         if rc != 0:
             raise ValueError("synth_render rejected the scene")
         return left, right, gt
+
+
+def _gpu_lib():
+    global _gpu_handle
+    if _gpu_handle is None:
+        build()
+        lib = ctypes.CDLL(_SO_GPU)
+        lib.synth_render_device.argtypes = [ctypes.POINTER(_Scene), ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p]
+        lib.synth_render_device.restype = ctypes.c_int
+        _gpu_handle = lib
+    return _gpu_handle
+
+
+def _ctypes_scene(scene: "Scene", frame: int):
+    def cur_d(L: Layer) -> int:
+        if L.dd_frame == 0:
+            return L.d0_q8
+        base = (L.d0_q8 + 128) >> 8
+        v = base + L.dd_frame * frame
+        lo, hi = L.dmin, L.dmax
+        p = 2 * (hi - lo)
+        m = (v - lo) % p
+        return L.d0_q8 + ((lo + (m if m <= hi - lo else p - m)) - base) * 256
+    order = sorted(range(len(scene.layers)),
+                   key=lambda i: (0 if scene.layers[i].shape == 0 else 1, cur_d(scene.layers[i]), i))
+    arr = (_Layer * len(order))()
+    for k, i in enumerate(order):
+        L = scene.layers[i]
+        arr[k] = _Layer(L.shape, L.cx, L.cy, L.hw, L.hh, L.vx, L.vy, L.d0_q8, L.gx_q16, L.gy_q16,
+                        L.dd_frame, L.dmin, L.dmax, L.tex_seed & 0xFFFFFFFF, L.mean, L.contrast,
+                        L.tint[0], L.tint[1], L.tint[2])
+    sc = _Scene(scene.w, scene.h, len(order), frame, scene.noise_q8, scene.gain_l_q10, scene.gain_r_q10,
+                scene.noise_seed & M64, arr)
+    return sc, arr
+
+
+def render_device(scene: "Scene", frame: int, left, right, gt=None, stream=0):
+    """Render a frame into device tensors (uint8 [h, w, 3] x2, float32 [h, w]
+    or None) with the CUDA build; same bytes as Scene.render."""
+    sc, keep = _ctypes_scene(scene, frame)
+    rc = _gpu_lib().synth_render_device(ctypes.byref(sc), left.data_ptr(), right.data_ptr(),
+                                        gt.data_ptr() if gt is not None else None, stream)
+    if rc != 0:
+        raise RuntimeError("synth_render_device failed with %d" % rc)
 
 
 @dataclasses.dataclass

@@ -1,0 +1,48 @@
+"""The C-ABI library loads and exports every function include/sb.h declares
+(no compute: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "sb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"^\s*(?:[\w\s\*]+?)\b(sb_\w+)\s*\(", src, flags=re.M))
+    return sorted(n for n in names if not n.startswith("sb_status"))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    from paper_2001_07809_b300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    names = _declared()
+    assert "sb_run" in names and "sb_boundary_sad" in names and len(names) >= 14
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_header_compiles_as_c():
+    import subprocess, tempfile
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write('#include "sb.h"\nint main(void){sb_params p; sb_default_params(&p); return p.k != 10;}\n')
+        subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-I", os.path.join(ROOT, "include"), c])
+
+
+def test_binding_struct_layout_matches_header():
+    import subprocess, tempfile
+    import paper_2001_07809_b300 as sb
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write('#include <stdio.h>\n#include <stddef.h>\n#include "sb.h"\nint main(void){'
+                           'printf("%zu %zu %zu %zu %zu\\n", sizeof(sb_params), sizeof(sb_pair), offsetof(sb_params, sigma),'
+                           ' offsetof(sb_params, sad_variant), offsetof(sb_pair, out_rgb)); return 0;}\n')
+        exe = os.path.join(d, "t")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        got = [int(v) for v in subprocess.check_output([exe]).split()]
+    want = [ctypes.sizeof(sb.sb_params), ctypes.sizeof(sb.sb_pair), sb.sb_params.sigma.offset,
+            sb.sb_params.sad_variant.offset, sb.sb_pair.out_rgb.offset]
+    assert got == want

@@ -1,0 +1,320 @@
+"""Parity of every CUDA stage with the CPU oracle (bit-exact; blur within one
+level), on seeded synthetic inputs.  Stage tests feed each kernel the
+oracle's own input for that stage; pipeline tests run sb_run end to end and
+compare with the oracle's whole pipeline."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+import paper_2001_07809_b300 as sb  # noqa: E402
+from gpu_helpers import blur, dev, host, kmeans, lightness, recon, refine, run_pairs, sad  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+RNG = np.random.default_rng(2024)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = sb.Context(0)
+    yield c
+    c.close()
+
+
+# ------------------------------------------------------------------ lightness
+def test_lightness_every_rgb_triple(ctx):
+    r, g, b = np.meshgrid(np.arange(256), np.arange(256), np.arange(256), indexing="ij")
+    rgb = np.stack([r, g, b], -1).astype(np.uint8).reshape(4096, 4096, 3)
+    L, hist = lightness(ctx, rgb)
+    want = oracle.rgb_to_lightness(rgb)
+    assert np.array_equal(L, want)
+    assert np.array_equal(hist, np.bincount(want.ravel(), minlength=256))
+
+
+@pytest.mark.parametrize("h,w", [(1, 1), (3, 5), (17, 33), (240, 320), (101, 999)])
+def test_lightness_shapes(ctx, h, w):
+    rgb = RNG.integers(0, 256, (h, w, 3)).astype(np.uint8)
+    L, hist = lightness(ctx, rgb)
+    assert np.array_equal(L, oracle.rgb_to_lightness(rgb))
+    assert np.array_equal(hist, oracle.histogram(L))
+
+
+# --------------------------------------------------------------------- kmeans
+@pytest.mark.parametrize("K", [1, 2, 4, 6, 8, 10, 33, 255])
+def test_kmeans_bit_exact(ctx, K):
+    vals = np.concatenate([RNG.normal(m, s, 3000) for m, s in ((30, 8), (90, 20), (160, 5), (215, 12))])
+    L = np.clip(np.round(vals), 0, 255).astype(np.uint8).reshape(60, 200)
+    c, lut, it, labels = kmeans(ctx, L, K)
+    oc, olut, oit = oracle.kmeans_hist(oracle.histogram(L), K, 100)
+    assert it == oit
+    assert np.array_equal(c.view(np.uint64), oc.view(np.uint64))   # FP64 bits
+    assert np.array_equal(lut, olut)
+    assert np.array_equal(labels, olut[L])
+
+
+def test_kmeans_flat_and_single_level(ctx):
+    L = np.full((20, 30), 77, np.uint8)
+    c, lut, it, _ = kmeans(ctx, L, 3)
+    oc, olut, oit = oracle.kmeans_hist(oracle.histogram(L), 3)
+    assert np.array_equal(c, oc) and np.array_equal(lut, olut) and it == oit
+
+
+# ------------------------------------------------------------- refinement + CCA
+@pytest.mark.parametrize("shape", [(48, 64), (97, 131), (240, 320), (333, 517)])
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("frac", [0.0, 0.04, 0.3])
+def test_refine_boundaries_bit_exact(ctx, shape, mode, frac):
+    h, w = shape
+    K = 4
+    raw = RNG.integers(0, K, (h // 4 + 1, w // 4 + 1))
+    labels = np.kron(raw, np.ones((4, 4), np.int64))[:h, :w]
+    noise = RNG.random((h, w)) < 0.05
+    labels = np.where(noise, RNG.integers(0, K, (h, w)), labels).astype(np.uint8)
+    ref, lab, bnd = refine(ctx, labels, mode, frac)
+    o_b0 = oracle.boundary(labels)
+    o_ref = oracle.refine(o_b0, mode)
+    o_lab, _ = oracle.cca(o_ref)
+    o_bnd = oracle.cc_filter(o_ref, o_lab, frac)
+    assert np.array_equal(ref, o_ref)
+    assert np.array_equal(lab, o_lab)
+    assert np.array_equal(bnd, o_bnd)
+
+
+@pytest.mark.parametrize("frac", [0.01, 0.04, 0.2])
+def test_cc_cut_inside_a_size_class(ctx, frac):
+    # many equal-size components: the cut falls inside the size class, so the
+    # smallest-label rule decides which of them go
+    h, w = 300, 400
+    labels = np.zeros((h, w), np.uint8)
+    for y in range(2, h - 2, 6):
+        for x in range(2, w - 2, 6):
+            labels[y, x] = 1 + (x // 6) % 3              # isolated dots -> equal 8-px rings
+    labels[100:180, 50:350] = 3                         # and one large ring
+    ref, lab, bnd = refine(ctx, labels, 0, frac)
+    o_ref = oracle.refine(oracle.boundary(labels), 0)
+    o_lab, _ = oracle.cca(o_ref)
+    o_bnd = oracle.cc_filter(o_ref, o_lab, frac)
+    assert np.array_equal(lab, o_lab)
+    removed = int(o_ref.sum() - o_bnd.sum())
+    assert 0 < removed < int(o_ref.sum())
+    assert np.array_equal(bnd, o_bnd)
+
+
+def test_refine_degenerate(ctx):
+    # K = 1: no boundary at all; one label row; a single pixel image
+    for labels in (np.zeros((40, 50), np.uint8), np.array([[0, 1, 1, 0, 2]], np.uint8), np.zeros((1, 1), np.uint8)):
+        ref, lab, bnd = refine(ctx, labels)
+        o_ref = oracle.refine(oracle.boundary(labels), 0)
+        o_lab, _ = oracle.cca(o_ref)
+        assert np.array_equal(ref, o_ref) and np.array_equal(lab, o_lab)
+        assert np.array_equal(bnd, oracle.cc_filter(o_ref, o_lab, 0.04))
+
+
+def test_cca_long_snake_spans_many_tiles(ctx):
+    # one 8-connected component winding through every 32x32 tile
+    h, w = 130, 200
+    b = np.zeros((h, w), np.uint8)
+    for y in range(0, h, 4):
+        b[y, :] = 1
+        b[y:y + 4, (w - 1) if (y // 4) % 2 == 0 else 0] = 1
+    labels = b  # two labels -> boundary map from them is irrelevant; test CCA through refine of labels
+    o_ref = oracle.refine(oracle.boundary(labels), 0)
+    ref, lab, _ = refine(ctx, labels)
+    o_lab, n = oracle.cca(o_ref)
+    assert np.array_equal(ref, o_ref) and np.array_equal(lab, o_lab)
+
+
+# ------------------------------------------------------------------------ SAD
+SAD_CASES = [
+    # (h, w, D, B)
+    (40, 60, 0, 1), (40, 60, 5, 3), (61, 97, 31, 9), (61, 97, 32, 9), (61, 97, 33, 9),
+    (70, 260, 64, 15), (90, 600, 40, 31), (80, 420, 100, 41), (70, 300, 64, 63), (47, 340, 255, 5),
+    (65, 700, 256, 41),
+]
+
+
+@pytest.mark.parametrize("h,w,D,B", SAD_CASES)
+@pytest.mark.parametrize("variant", [sb.SB_SAD_BOXSUM, sb.SB_SAD_DIRECT])
+def test_sad_bit_exact(ctx, h, w, D, B, variant):
+    Ll = RNG.integers(0, 256, (h, w)).astype(np.uint8)
+    shift = min(D, 7)
+    Lr = np.roll(Ll, -shift, axis=1)
+    Lr = np.clip(Lr.astype(int) + RNG.integers(-6, 7, (h, w)), 0, 255).astype(np.uint8)
+    bmap = (RNG.random((h, w)) < 0.2).astype(np.uint8)
+    disp, cost = sad(ctx, Ll, Lr, bmap, D, B, variant)
+    anchor = oracle.anchor_mask(bmap, D, B)
+    od, oc = oracle.boundary_sad(Ll, Lr, anchor, D, B)
+    assert np.array_equal(disp, od)
+    assert np.array_equal(cost, oc)
+
+
+def test_sad_flat_images_tie_to_smallest_d(ctx):
+    h, w, D, B = 30, 120, 20, 7
+    Ll = np.full((h, w), 100, np.uint8)
+    Lr = np.full((h, w), 100, np.uint8)
+    bmap = np.ones((h, w), np.uint8)
+    for variant in (sb.SB_SAD_BOXSUM, sb.SB_SAD_DIRECT):
+        disp, cost = sad(ctx, Ll, Lr, bmap, D, B, variant)
+        anchor = oracle.anchor_mask(bmap, D, B).astype(bool)
+        assert np.all(disp[anchor] == 0) and np.all(cost[anchor] == 0)
+        assert np.all(disp[~anchor] == sb.UNDETERMINED)
+
+
+def test_sad_extreme_costs(ctx):
+    # maximal per-pixel differences: costs up to 63*63*255 must not overflow the key
+    h, w, D, B = 70, 200, 20, 63
+    Ll = np.zeros((h, w), np.uint8)
+    Lr = np.full((h, w), 255, np.uint8)
+    bmap = np.ones((h, w), np.uint8)
+    for variant in (sb.SB_SAD_BOXSUM, sb.SB_SAD_DIRECT):
+        disp, cost = sad(ctx, Ll, Lr, bmap, D, B, variant)
+        anchor = oracle.anchor_mask(bmap, D, B).astype(bool)
+        od, oc = oracle.boundary_sad(Ll, Lr, anchor.astype(np.uint8), D, B)
+        assert np.array_equal(disp, od) and np.array_equal(cost, oc)
+        assert np.all(oc[anchor] == 63 * 63 * 255) and np.all(od[anchor] == 0)
+
+
+# ------------------------------------------------------------ reconstruction
+@pytest.mark.parametrize("h,w,D,B,T", [(50, 80, 4, 3, 1), (130, 140, 10, 5, 0), (200, 333, 20, 9, 3),
+                                       (257, 64, 0, 1, -1), (300, 50, 8, 7, 1000)])
+def test_recon_bit_exact(ctx, h, w, D, B, T):
+    bmap = (RNG.random((h, w)) < 0.15).astype(np.uint8)
+    anchor = oracle.anchor_mask(bmap, D, B)
+    sparse = np.full((h, w), oracle.UNDET, np.uint16)
+    vals = RNG.integers(0, 6, (h, w)).astype(np.uint16)      # few values -> many equal neighbours
+    sparse[anchor == 1] = vals[anchor == 1]
+    filled, final = recon(ctx, sparse, D, B, T)
+    o_filled = oracle.recon_fill(sparse, anchor)
+    o_final = oracle.recon_peek(o_filled, D, B, T)
+    assert np.array_equal(filled, o_filled)
+    assert np.array_equal(final, o_final)
+
+
+def test_recon_paper_rows_and_columns(ctx, golden_dir):
+    # the hand-worked Algorithm 1 rows, stacked into one image with block 1, D 0
+    import os
+    from test_oracle_pins import _blocks, _parse_row
+    for tag, rows in _blocks(os.path.join(golden_dir, "alg1_rows.txt")):
+        d = dict(rows)
+        a = np.array([_parse_row(d["anchors"])], np.uint16)
+        e = np.array([_parse_row(d["expected"])], np.uint16)
+        filled, _ = recon(ctx, a, 0, 1, 1)
+        assert np.array_equal(filled, e), tag
+
+
+# ---------------------------------------------------------------------- blur
+@pytest.mark.parametrize("sigma", [0.5, 1.0, 2.0, 3.0, 5.0, 8.0, 13.7, 32.0])
+def test_blur_within_one_level(ctx, sigma):
+    h, w = (90, 150) if sigma <= 8 else (260, 300)
+    rgb = RNG.integers(0, 256, (h, w, 3)).astype(np.uint8)
+    disp = RNG.integers(0, 40, (h, w)).astype(np.uint16)
+    ranges = [(10, 20), (30, 31)]
+    out = blur(ctx, rgb, disp, ranges, sigma)
+    want = oracle.selective_blur(rgb, disp, ranges, sigma)
+    diff = np.abs(out.astype(int) - want.astype(int))
+    assert diff.max() <= 1
+    keep = ((disp >= 10) & (disp <= 20)) | ((disp >= 30) & (disp <= 31))
+    assert np.array_equal(out[keep], rgb[keep])
+
+
+def test_blur_constant_image_unchanged(ctx):
+    rgb = np.full((140, 260, 3), 93, np.uint8)
+    rgb[..., 2] = 250
+    out = blur(ctx, rgb, np.zeros((140, 260), np.uint16), [], 6.0)
+    assert np.array_equal(out, rgb)
+
+
+# ----------------------------------------------------------- whole pipeline
+def _compare_full(res_rgb, res_disp, left, right, p):
+    want = oracle.run(left, right, p)
+    assert np.array_equal(res_disp, want.disp)
+    assert np.abs(res_rgb.astype(int) - want.out_rgb.astype(int)).max() <= 1
+    return want
+
+
+@pytest.mark.parametrize("flags", [sb.SB_RUN_PLAIN, sb.SB_RUN_BATCHED, sb.SB_RUN_BATCHED | sb.SB_RUN_GRAPH])
+@pytest.mark.parametrize("variant", [sb.SB_SAD_BOXSUM, sb.SB_SAD_DIRECT])
+def test_pipeline_c1_full(ctx, flags, variant):
+    sc, p, _ = synth.workload("c1")
+    left, right, _ = sc.render()
+    (o_rgb, o_disp), = run_pairs(ctx, [(left, right, p)], flags, variant)
+    _compare_full(o_rgb, o_disp, left, right, p)
+
+
+def test_pipeline_ragged_and_open_close(ctx):
+    r = synth.Rng(99)
+    layers = [synth.Layer(0, 150, 120, 333, 257, 5 * 256, 90, 70, r.u64() & 0xFFFFFFFF)]
+    for i, d in enumerate((14, 25, 33)):
+        layers.append(synth.Layer(1 + i % 2, r.randint(80, 260), r.randint(40, 200), r.randint(20, 50),
+                                  r.randint(20, 40), d * 256, 60 + 50 * i, 70, r.u64() & 0xFFFFFFFF))
+    sc = synth.Scene(333, 257, layers, noise_q8=300, noise_seed=7)
+    left, right, _ = sc.render()
+    for mode, T in ((1, 0), (0, 2)):
+        p = synth.Params(k=5, max_disp=40, block=11, sigma=2.5, ranges=[(0, 9), (30, 40)], disp_threshold=T,
+                         morph_mode=mode)
+        (o_rgb, o_disp), = run_pairs(ctx, [(left, right, p)], sb.SB_RUN_PLAIN)
+        _compare_full(o_rgb, o_disp, left, right, p)
+
+
+def test_batched_and_graph_equal_plain_on_uneven_batch(ctx):
+    items = []
+    for i, (w, h, D, B, K) in enumerate([(200, 120, 24, 7, 3), (321, 203, 48, 13, 5), (150, 150, 16, 5, 4),
+                                         (400, 90, 64, 9, 6)]):
+        r = synth.Rng(500 + i)
+        layers = synth._c2_style_layers(r, w, h, D, contrast=60)
+        sc = synth.Scene(w, h, layers, noise_q8=256, noise_seed=r.u64())
+        left, right, _ = sc.render()
+        items.append((left, right, synth.Params(k=K, max_disp=D, block=B, sigma=1.5 + i, ranges=[(D // 3, D)])))
+    plain = run_pairs(ctx, items, sb.SB_RUN_PLAIN)
+    batched = run_pairs(ctx, items, sb.SB_RUN_BATCHED)
+    graph = run_pairs(ctx, items, sb.SB_RUN_BATCHED | sb.SB_RUN_GRAPH)
+    graph2 = run_pairs(ctx, items, sb.SB_RUN_BATCHED | sb.SB_RUN_GRAPH)   # replay
+    for a, b, c, d in zip(plain, batched, graph, graph2):
+        for u, v, x, y in zip(a, b, c, d):
+            assert np.array_equal(u, v) and np.array_equal(u, x) and np.array_equal(u, y)
+    for (left, right, p), (o_rgb, o_disp) in zip(items, plain):
+        _compare_full(o_rgb, o_disp, left, right, p)
+
+
+def test_host_io_equals_device(ctx):
+    sc, p, _ = synth.workload("c1")
+    left, right, _ = sc.render()
+    (d_rgb, d_disp), = run_pairs(ctx, [(left, right, p)], sb.SB_RUN_BATCHED)
+    for flags in (sb.SB_RUN_HOST_IO, sb.SB_RUN_HOST_IO | sb.SB_RUN_BATCHED):
+        hl = torch.from_numpy(left).pin_memory()
+        hr = torch.from_numpy(right).pin_memory()
+        ho = torch.empty(left.shape, dtype=torch.uint8).pin_memory()
+        hd = torch.empty(left.shape[:2], dtype=torch.int16).pin_memory()
+        from gpu_helpers import params_of
+        sb.sb_run(ctx, [sb.Pair(hl, hr, params_of(p), ho, hd)], flags)
+        ctx.synchronize()
+        assert np.array_equal(ho.numpy(), d_rgb)
+        assert np.array_equal(hd.numpy().view(np.uint16), d_disp)
+
+
+def test_invalid_arguments_raise(ctx):
+    left = torch.zeros((20, 30, 3), dtype=torch.uint8, device="cuda")
+    out = torch.zeros_like(left)
+    bad = [sb.make_params(max_disp=40, block=9), sb.make_params(max_disp=4, block=8),
+           sb.make_params(max_disp=4, block=5, k=0), sb.make_params(max_disp=4, block=5, sigma=0.0)]
+    for p in bad:
+        with pytest.raises(sb.SbError) as ei:
+            sb.sb_run(ctx, [sb.Pair(left, left, p, out)])
+        assert ei.value.status == 1
+    ok = sb.make_params(max_disp=4, block=5, k=2)
+    sb.sb_run(ctx, [sb.Pair(left, left, ok, out)])    # the context is still usable
+    ctx.synchronize()
+
+
+def test_minimum_sizes(ctx):
+    for (D, B) in ((0, 1), (3, 3), (10, 5)):
+        w, h = D + B + 1, B
+        left = RNG.integers(0, 256, (h, w, 3)).astype(np.uint8)
+        right = RNG.integers(0, 256, (h, w, 3)).astype(np.uint8)
+        p = synth.Params(k=2, max_disp=D, block=B, sigma=1.0, ranges=[(0, 0)])
+        (o_rgb, o_disp), = run_pairs(ctx, [(left, right, p)], sb.SB_RUN_PLAIN)
+        _compare_full(o_rgb, o_disp, left, right, p)
