@@ -1,0 +1,166 @@
+"""Continuous-batching request loop over sb_run (the served form).
+
+Requests (a stereo pair in pinned host memory plus its parameters) arrive at
+any time through ``Server.submit``.  A scheduler thread admits waiting
+requests in arrival order while their device-memory estimate fits the budget,
+batches everything admitted into one ``sb_run(SB_RUN_BATCHED)`` call on the
+first free stream (two streams, so a new batch overlaps the one on the GPU),
+and resolves each request's future when its batch's completion event has
+fired.  Inputs, intermediate maps and results of admitted requests stay
+resident on the device until the batch completes; results are copied back to
+pinned host memory in the same stream.
+
+The pipeline is deterministic per pair, so a request's result does not depend
+on what it was batched with.
+"""
+from __future__ import annotations
+
+import collections
+import concurrent.futures as cf
+import threading
+import time
+from typing import List, Optional
+
+import torch
+
+from . import Context, Pair, SB_RUN_BATCHED, sb_params, sb_run
+
+
+def request_bytes(h: int, w: int) -> int:
+    """Device bytes one admitted request holds: RGB in (2x3), RGB out (3),
+    disparity out (2) and the library workspace (about 18 bytes per pixel)."""
+    n = h * w
+    return n * (6 + 3 + 2 + 18) + (1 << 20)
+
+
+class Request:
+    __slots__ = ("left", "right", "params", "future", "arrival", "done", "bytes", "out_rgb", "out_disp", "h", "w")
+
+    def __init__(self, left, right, params: sb_params):
+        self.left, self.right, self.params = left, right, params
+        self.h, self.w = int(left.shape[0]), int(left.shape[1])
+        self.future: cf.Future = cf.Future()
+        self.arrival = time.perf_counter()
+        self.done: Optional[float] = None
+        self.bytes = request_bytes(self.h, self.w)
+        self.out_rgb = torch.empty((self.h, self.w, 3), dtype=torch.uint8, pin_memory=True)
+        self.out_disp = torch.empty((self.h, self.w), dtype=torch.int16, pin_memory=True)
+
+
+class Server:
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 40 << 30, max_batch: int = 64, n_streams: int = 2):
+        self.device = device
+        self.budget = int(mem_budget_bytes)
+        self.max_batch = max_batch
+        torch.cuda.set_device(device)
+        self.streams = [torch.cuda.Stream(device) for _ in range(n_streams)]
+        self.ctxs = [Context(device, 0, s) for s in self.streams]
+        self.busy = [None] * n_streams   # (event, requests, device tensors) per stream
+        self.queue: collections.deque = collections.deque()
+        self.used = 0
+        self.cv = threading.Condition()
+        self.running = True
+        self.completed: List[Request] = []
+        self.batches = 0
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.thread.start()
+
+    # ------------------------------------------------------------ client side
+    def submit(self, left_host, right_host, params: sb_params) -> cf.Future:
+        """Queue one pair (pinned host uint8 [h, w, 3] tensors); the future
+        resolves to (out_rgb, out_disp) host tensors."""
+        req = Request(left_host, right_host, params)
+        if req.bytes > self.budget:
+            req.future.set_exception(MemoryError("request needs %d bytes, budget is %d" % (req.bytes, self.budget)))
+            return req.future
+        with self.cv:
+            self.queue.append(req)
+            self.cv.notify()
+        return req.future
+
+    def close(self):
+        with self.cv:
+            self.running = False
+            self.cv.notify()
+        self.thread.join()
+        for c in self.ctxs:
+            c.close()
+
+    def latencies(self) -> List[float]:
+        return [r.done - r.arrival for r in self.completed]
+
+    # ---------------------------------------------------------- scheduler side
+    def _finish(self, i: int):
+        ev, reqs, _keep = self.busy[i]
+        now = time.perf_counter()
+        self.busy[i] = None
+        err = None
+        try:
+            self.ctxs[i].synchronize()
+        except Exception as e:  # a failed batch fails its requests, the server keeps going
+            err = e
+        for r in reqs:
+            r.done = now
+            self.used -= r.bytes
+            if err is None:
+                r.future.set_result((r.out_rgb, r.out_disp))
+            else:
+                r.future.set_exception(err)
+            self.completed.append(r)
+
+    def _launch(self, i: int, reqs: List[Request]):
+        s = self.streams[i]
+        keep = []
+        pairs = []
+        with torch.cuda.stream(s):
+            for r in reqs:
+                dl = r.left.to(self.device, non_blocking=True)
+                dr = r.right.to(self.device, non_blocking=True)
+                do = torch.empty((r.h, r.w, 3), dtype=torch.uint8, device=self.device)
+                dd = torch.empty((r.h, r.w), dtype=torch.int16, device=self.device)
+                keep += [dl, dr, do, dd]
+                pairs.append(Pair(dl, dr, r.params, do, dd))
+            sb_run(self.ctxs[i], pairs, SB_RUN_BATCHED)
+            for r, q in zip(reqs, pairs):
+                r.out_rgb.copy_(q.out_rgb, non_blocking=True)
+                r.out_disp.copy_(q.out_disp, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        self.busy[i] = (ev, reqs, keep)
+        self.batches += 1
+
+    def _loop(self):
+        while True:
+            with self.cv:
+                if not self.running and not self.queue and all(b is None for b in self.busy):
+                    return
+            for i, b in enumerate(self.busy):
+                if b is not None and b[0].query():
+                    self._finish(i)
+            free = [i for i, b in enumerate(self.busy) if b is None]
+            launched = False
+            if free:
+                with self.cv:
+                    batch = []
+                    while self.queue and len(batch) < self.max_batch and self.used + self.queue[0].bytes <= self.budget:
+                        r = self.queue.popleft()
+                        self.used += r.bytes
+                        batch.append(r)
+                if batch:
+                    self._launch(free[0], batch)
+                    launched = True
+            if not launched:
+                with self.cv:
+                    if self.running and not self.queue:
+                        self.cv.wait(timeout=0.0005)
+                    elif not free:
+                        pass
+                time.sleep(0.0001)
+
+
+def percentile(vals, q):
+    v = sorted(vals)
+    if not v:
+        return None
+    k = min(len(v) - 1, max(0, int(round(q / 100.0 * (len(v) - 1)))))
+    return v[k]
