@@ -187,6 +187,25 @@ enum {
  * Results are identical for every flag combination. */
 sb_status sb_run(sb_context* ctx, const sb_pair* pairs, int32_t n_pairs, uint32_t flags);
 
+/* Boundary SAD for callers that cannot allocate device memory: a plug-in
+ * inside a host application that owns all device memory through its own
+ * pool, or a real-time loop that must never call cudaMalloc (it can
+ * synchronise the device).  The paper has no counterpart; this is a service
+ * of the library.  Same result as sb_boundary_sad, but no context: the call
+ * queues its work on cuda_stream (a cudaStream_t, NULL = legacy default
+ * stream) and allocates nothing.  Its scratch (one 32-bit key per pixel plus
+ * the launch descriptors, about 16.25 MB) is a static device array that
+ * every GPU loading the library holds until the process exits; images above
+ * SB_STATIC_MAX_PIXELS pixels are rejected with SB_ERR_INVALID_ARG.  The
+ * first call on a device looks up the array's device address (make it before
+ * any stream capture).  All calls share the array: calls that overlap on the
+ * GPU (other streams, other threads) race and must be ordered by the caller.
+ * errbuf: NULL or errbuf_len bytes that receive a message on failure. */
+#define SB_STATIC_MAX_PIXELS 4194304
+sb_status sb_boundary_sad_static(const uint8_t* L_left, const uint8_t* L_right, const uint8_t* boundary, int32_t w,
+                                 int32_t h, int32_t max_disp, int32_t block, int32_t variant, uint16_t* disp,
+                                 uint32_t* cost, void* cuda_stream, char* errbuf, size_t errbuf_len);
+
 /* Number of kernel launches the library has issued on this context so far
  * (a graph replay counts every kernel node it runs). */
 uint64_t sb_launch_count(const sb_context* ctx);
