@@ -127,17 +127,48 @@ __global__ void __launch_bounds__(256) k_cca_flatten(const CcaJob* __restrict__ 
   }
 }
 
+// Component sizes: each 32x32 tile first counts its pixels per root in a
+// small shared-memory hash table, then adds one total per (tile, root) to the
+// global size array, so a large component costs one atomic per tile it
+// touches instead of one per pixel.  Also counts the boundary pixels.
 __global__ void __launch_bounds__(256) k_cc_count(const CcaJob* __restrict__ jobs) {
-  const CcaJob J = jobs[blockIdx.y];
-  const int64_t n = (int64_t)J.w * J.h;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  unsigned cnt = 0;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-    const int v = J.lab[p];
-    if (v >= 0) { atomicAdd(&J.size[v], 1u); ++cnt; }
+  constexpr int HS = 256;  // hash slots (a tile rarely holds more than a few dozen roots)
+  __shared__ int s_key[HS];
+  __shared__ unsigned s_cnt[HS];
+  __shared__ unsigned s_total;
+  const CcaJob J = jobs[blockIdx.z];
+  const int tx0 = blockIdx.x * CT, ty0 = blockIdx.y * CT;
+  if (tx0 >= J.w || ty0 >= J.h) return;
+  for (int i = threadIdx.x; i < HS; i += blockDim.x) { s_key[i] = -1; s_cnt[i] = 0; }
+  if (threadIdx.x == 0) s_total = 0;
+  __syncthreads();
+  unsigned mine = 0;
+  for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) {
+    const int x = tx0 + (i & (CT - 1)), y = ty0 + (i >> 5);
+    if (x >= J.w || y >= J.h) continue;
+    const int v = J.lab[(int64_t)y * J.w + x];
+    if (v < 0) continue;
+    ++mine;
+    unsigned hsh = ((unsigned)v * 2654435761u) >> 24;  // 8 bits
+    bool placed = false;
+    volatile int* vkey = s_key;
+    for (int probe = 0; probe < HS; ++probe) {
+      const int slot = (hsh + probe) & (HS - 1);
+      const int k = vkey[slot];
+      if (k == v || (k == -1 && (atomicCAS(&s_key[slot], -1, v) == -1 || vkey[slot] == v))) {
+        atomicAdd(&s_cnt[slot], 1u);
+        placed = true;
+        break;
+      }
+    }
+    if (!placed) atomicAdd(&J.size[v], 1u);  // table full: count directly
   }
-  for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(reinterpret_cast<unsigned long long*>(&J.cut[0]), (unsigned long long)cnt);
+  for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&s_total, mine);
+  __syncthreads();
+  for (int i = threadIdx.x; i < HS; i += blockDim.x)
+    if (s_key[i] >= 0 && s_cnt[i]) atomicAdd(&J.size[s_key[i]], s_cnt[i]);
+  if (threadIdx.x == 0 && s_total) atomicAdd(reinterpret_cast<unsigned long long*>(&J.cut[0]), (unsigned long long)s_total);
 }
 
 __device__ __forceinline__ int64_t removal_limit(const CcaJob& J) {
@@ -313,7 +344,7 @@ void launch_cc_filter(const CcaJob* jobs, int n_jobs, int max_w, int max_h, cuda
   int bpj = (int)((n + 256 * 8 - 1) / (256 * 8));
   if (bpj > 1184) bpj = 1184;
   if (bpj < 1) bpj = 1;
-  k_cc_count<<<dim3(bpj, n_jobs), 256, 0, s>>>(jobs);
+  k_cc_count<<<dim3((max_w + CT - 1) / CT, (max_h + CT - 1) / CT, n_jobs), 256, 0, s>>>(jobs);
   k_cc_hist<<<dim3(bpj, n_jobs), 256, 0, s>>>(jobs);
   k_cc_cut<<<n_jobs, 1024, 0, s>>>(jobs);
   int rb = (max_h + 7) / 8;

@@ -8,11 +8,13 @@
 // columns, a band of rows and a chunk of 32 disparities.
 //   Stage A: thread t owns column c = x0 - r + t and keeps the 32 vertical
 //     window sums V_d(y, c) = sum_{|i|<=r} |L(y+i, c) - R(y+i, c-d)| in
-//     registers, sliding down one row per step.  Four disparities at a time:
-//     one packed |L - R| of four bytes for the entering row and one for the
-//     leaving row (vabsdiff4), interleaved with prmt, and two mixed-sign dp4a
-//     add (entering - leaving) per disparity.  Rows are staged in a shared
-//     memory ring so that every byte is read from HBM once per CTA.
+//     registers as 16 packed u16 pairs, sliding down one row per step.  Four
+//     disparities at a time: one packed |L - R| of four bytes for the
+//     entering row and one for the leaving row (vabsdiff4), split into even
+//     and odd bytes (lop3 / prmt), and lane-wise u16 add-subtract (iadd3).
+//     Rows are staged with cp.async into a shared-memory ring one group of
+//     rows ahead, so every byte is read from HBM once per CTA and the copy
+//     overlaps the arithmetic.
 //   Stage B: lanes = disparities; a warp slides the horizontal sum
 //     S = sum_{|j|<=r} V(c+j) along its row segment and, at anchor pixels
 //     (warp-uniform test), reduces (S << 10 | d) over the 32 lanes with
@@ -26,24 +28,44 @@ namespace sb {
 
 namespace {
 constexpr int kThreads = 256;
-constexpr int kGroup = 4;        // rows per Stage A -> Stage B hand-off
-constexpr int kVsColBytes = 64;  // 32 disparities x uint16
-constexpr int kRowBytes = 576;   // staged bytes per row: 256 L + up to 320 R
+constexpr int kGroup = 4;                       // output rows per Stage A -> Stage B hand-off
+constexpr int kVsCols = 240;                    // columns of a strip incl. the 2r halo (TX + 2r)
+constexpr int kVsStride = 80;                   // bytes per column of 32 u16 sums (+16: conflict-free STS.128)
+constexpr int kLBytes = 272;                    // staged L bytes per row (240 + 16-byte alignment slack)
+constexpr int kRBytes = 320;                    // staged R bytes per row (240 + 31 + slack + look-ahead)
+constexpr int kRowBytes = kLBytes + kRBytes;    // 592, a multiple of 16
+constexpr int kBBytes = 272;                    // staged boundary-map bytes per output row
 
-__device__ __forceinline__ uint32_t dp4a_us(uint32_t a, uint32_t b, uint32_t c) {
-  uint32_t d;
-  asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-  return d;
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src));
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-__device__ __forceinline__ int vs_off(int g, int col, int lane) {
-  return g * (kThreads * kVsColBytes) + col * kVsColBytes + 16 * ((lane >> 3) ^ ((col >> 1) & 3)) + 2 * (lane & 7);
+// Copy 16-byte chunk `ch` of the image segment that starts at absolute byte
+// offset a16 (a multiple of 16, possibly outside the image) into dst.  Bytes
+// outside the image buffer of n bytes are never used by the caller: a chunk
+// that starts before the buffer is read from offset 0 instead, a chunk that
+// runs past its end is copied byte by byte with the index clamped.  `fast`
+// (16-byte aligned image base) selects cp.async for whole in-buffer chunks.
+__device__ __forceinline__ void stage_chunk(uint8_t* dst, const uint8_t* img, int64_t n, int64_t a16, int ch,
+                                            bool fast) {
+  int64_t src = a16 + 16 * (int64_t)ch;
+  if (src < 0) src = 0;
+  if (fast && src + 16 <= n) {
+    cp_async16(dst + 16 * ch, img + src);
+  } else {
+#pragma unroll 1
+    for (int k = 0; k < 16; ++k) {
+      const int64_t q = src + k < n ? src + k : n - 1;
+      dst[16 * ch + k] = img[q];
+    }
+  }
 }
-
-__device__ __forceinline__ int floor4(int v) { return v >= 0 ? (v & ~3) : -(((-v) + 3) & ~3); }
 }  // namespace
 
-__host__ __device__ int sad_boxsum_strip(int r) { return (kThreads - 2 * r) & ~7; }
+__host__ __device__ int sad_boxsum_strip(int r) { return (kVsCols - 2 * r) & ~7; }
 
 __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __restrict__ jobs,
                                                             const SadItem* __restrict__ items) {
@@ -51,96 +73,132 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
   const SadItem it = items[blockIdx.x];
   const SadJob J = jobs[it.job];
   const int r = J.r, D = J.D, w = J.w;
-  const int ring = 2 * r + 1 + kGroup;
-  uint8_t* s_ring = smem;                                 // ring rows of kRowBytes
-  uint8_t* s_zero = smem + ring * kRowBytes;              // one zero row
-  uint8_t* s_vs = s_zero + kRowBytes;                     // kGroup x 256 columns x 64 B
+  const int64_t npx = (int64_t)w * J.h;
+  const int ring = 2 * r + 1 + 2 * kGroup;                // + one group staged ahead
+  uint8_t* s_ring = smem;                                 // ring rows: [L | R]
+  uint8_t* s_zero = s_ring + ring * kRowBytes;            // zero row (warm-up leaving rows)
+  uint8_t* s_bm = s_zero + kRowBytes;                     // 2 x kGroup boundary-map rows
+  uint8_t* s_vs = s_bm + 2 * kGroup * kBBytes;            // kGroup x kVsCols x kVsStride
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int TX = sad_boxsum_strip(r);
   const int NC = TX + 2 * r;
   const int x0 = it.x0, d0 = it.d0;
   const int xo0 = D + r, xo1 = w - 1 - r;                 // Omega columns
   const int cstart = x0 - r;                              // strip column 0
-  const int rbase = floor4(cstart - d0 - 31);             // first staged R byte (4-aligned)
-  const int y_first = it.y0;                              // first output row of the band (>= r)
-  const int y_last = it.y1;                               // last output row (inclusive)
+  const int rstart = cstart - d0 - 31;                    // first R byte any thread needs
+  const int y_first = it.y0, y_last = it.y1;              // output rows of the band
+  const bool fast = (((uintptr_t)J.Ll | (uintptr_t)J.Lr | (uintptr_t)J.bmap) & 15) == 0;
+  const int nchL = (15 + NC + 15) / 16, nchR = (15 + NC + 31 + 4 + 15) / 16, nchB = (15 + TX + 15) / 16;
 
   for (int i = tid; i < kRowBytes / 4; i += kThreads) reinterpret_cast<uint32_t*>(s_zero)[i] = 0u;
 
-  // Stage A state
-  uint32_t V[32];
-#pragma unroll
-  for (int k = 0; k < 32; ++k) V[k] = 0u;
-  const int c = cstart + tid;
-  const int rel = (c - d0 - 31) - rbase;                  // >= 0 by construction
-  const int q = rel >> 2, sh = (rel & 3) * 8;
-
-  // virtual output rows run from y_first - 2r (warm-up) to y_last
-  for (int yg = y_first - 2 * r; yg <= y_last; yg += kGroup) {
+  // stage the entering rows of the group starting at virtual output row yg, and
+  // the boundary-map rows of its real output rows, into buffer `buf`; thread
+  // tid copies chunk (tid & 63) of ring row (tid >> 6) and chunk (tid & 15) of
+  // boundary row (tid >> 4): at most 35 chunks per ring row, 16 per map row
+  const int per = nchL + nchR;
+  auto stage = [&](int yg, int slot_first, int buf) {
     const int ng = min(kGroup, y_last - yg + 1);
-    __syncthreads();  // previous readers of the ring slots being refilled are done
-    // stage entering rows yin = yg + k + r for k < ng
-    for (int k = 0; k < ng; ++k) {
-      const int yin = yg + k + r;
-      uint8_t* row = s_ring + ((yin % ring + ring) % ring) * kRowBytes;
-      const uint8_t* gl = J.Ll + (int64_t)yin * w;
-      const uint8_t* gr = J.Lr + (int64_t)yin * w;
-      for (int i = tid; i < kRowBytes; i += kThreads) {
-        uint8_t v = 0;
-        if (i < 256) {
-          const int x = cstart + i;
-          if (x >= 0 && x < w) v = gl[x];
-        } else {
-          const int x = rbase + (i - 256);
-          if (x >= 0 && x < w) v = gr[x];
-        }
-        row[i] = v;
+    {
+      const int k = tid >> 6, ch = tid & 63;
+      if (k < ng && ch < per) {
+        const int yin = yg + k + r;
+        const int sl = slot_first + k < ring ? slot_first + k : slot_first + k - ring;
+        uint8_t* row = s_ring + sl * kRowBytes;
+        const int64_t ro = (int64_t)yin * w;
+        if (ch < nchL) stage_chunk(row, J.Ll, npx, (ro + cstart) & ~(int64_t)15, ch, fast);
+        else stage_chunk(row + kLBytes, J.Lr, npx, (ro + rstart) & ~(int64_t)15, ch - nchL, fast);
       }
     }
-    __syncthreads();
+    {
+      const int k = tid >> 4, ch = tid & 15;
+      const int y = yg + k;
+      if (k < ng && ch < nchB && y >= y_first)
+        stage_chunk(s_bm + (buf * kGroup + k) * kBBytes, J.bmap, npx, ((int64_t)y * w + x0) & ~(int64_t)15, ch, fast);
+    }
+    cp_async_commit();
+  };
+
+  // Stage A state: 32 vertical window sums as 16 packed u16 pairs.  For word g,
+  // Ve[g] holds disparities (d0+31-4g | d0+29-4g) and Vo[g] (d0+30-4g | d0+28-4g).
+  uint32_t Ve[8], Vo[8];
+#pragma unroll
+  for (int g = 0; g < 8; ++g) Ve[g] = Vo[g] = 0u;
+
+  // Stage B: where lane (disparity d0 + lane) finds its u16 in a column
+  int lanepos;
+  {
+    const int u = 31 - lane, g = u >> 2, b = u & 3;
+    lanepos = 4 * g + 2 * (b & 1) + (b >> 1);
+  }
+
+  // ring slot and 16-byte alignment offsets of the first entering row of the
+  // current group, advanced incrementally (no division in the row loop).  The
+  // leaving row y - r - 1 is 2r + 1 rows before the entering row y + r, which
+  // is 2*kGroup slots ahead in the ring.
+  const int wm = w & 15, back = ((2 * r + 1) * w) & 15;
+  int slot = (y_first - r) % ring;                            // entering row of the first group
+  int offL = (int)(((int64_t)(y_first - r) * w + cstart) & 15);
+  int offR = (int)(((int64_t)(y_first - r) * w + rstart) & 15);
+  int k_iter = 0;
+  stage(y_first - 2 * r, slot, 0);
+  // virtual output rows run from y_first - 2r (warm-up) to y_last
+  for (int yg = y_first - 2 * r; yg <= y_last; yg += kGroup, ++k_iter) {
+    const int ng = min(kGroup, y_last - yg + 1);
+    const int buf = k_iter & 1;
+    cp_async_wait_all();
+    __syncthreads();  // this group's rows have landed; the previous Stage B is done
+    const int slot_next = slot + kGroup < ring ? slot + kGroup : slot + kGroup - ring;
+    if (yg + kGroup <= y_last) stage(yg + kGroup, slot_next, buf ^ 1);
     // Stage A: ng row steps
-    for (int k = 0; k < ng; ++k) {
-      const int y = yg + k;  // output row of this step (virtual when < y_first)
-      const int yin = y + r, yout = y - r - 1;
-      const uint8_t* rin = s_ring + ((yin % ring + ring) % ring) * kRowBytes;
-      const uint8_t* rout = (yout < y_first - r) ? s_zero : s_ring + ((yout % ring + ring) % ring) * kRowBytes;
-      if (tid < NC) {
-        const uint32_t Lin = (uint32_t)rin[tid] * 0x01010101u;
-        const uint32_t Lout = (uint32_t)rout[tid] * 0x01010101u;
-        const uint32_t* Rin = reinterpret_cast<const uint32_t*>(rin + 256) + q;
-        const uint32_t* Rout = reinterpret_cast<const uint32_t*>(rout + 256) + q;
-        uint32_t wi = Rin[0], wo = Rout[0];
+    if (tid < NC) {
+      int sin = slot, offLi = offL, offRi = offR;
+#pragma unroll 1
+      for (int k = 0; k < ng; ++k) {
+        const int y = yg + k;
+        const bool real_out = y - r - 1 >= y_first - r;
+        int sout = sin + 2 * kGroup;
+        if (sout >= ring) sout -= ring;
+        const uint8_t* rin = s_ring + sin * kRowBytes;
+        const uint8_t* rout = real_out ? s_ring + sout * kRowBytes : s_zero;
+        const int offLo = real_out ? ((offLi - back) & 15) : 0, offRo = real_out ? ((offRi - back) & 15) : 0;
+        const uint32_t Lin = (uint32_t)rin[offLi + tid] * 0x01010101u;
+        const uint32_t Lout = (uint32_t)rout[offLo + tid] * 0x01010101u;
+        const int ji = tid + offRi, jo = tid + offRo;
+        const uint32_t* Ri = reinterpret_cast<const uint32_t*>(rin + kLBytes) + (ji >> 2);
+        const uint32_t* Ro = reinterpret_cast<const uint32_t*>(rout + kLBytes) + (jo >> 2);
+        const int shi = (ji & 3) * 8, sho = (jo & 3) * 8;
+        uint32_t wi = Ri[0], wo = Ro[0];
 #pragma unroll
         for (int g = 0; g < 8; ++g) {
-          const uint32_t wi2 = Rin[g + 1], wo2 = Rout[g + 1];
-          const uint32_t ri = __funnelshift_r(wi, wi2, sh), ro = __funnelshift_r(wo, wo2, sh);
+          const uint32_t wi2 = Ri[g + 1], wo2 = Ro[g + 1];
+          const uint32_t ri = __funnelshift_r(wi, wi2, shi), ro = __funnelshift_r(wo, wo2, sho);
           wi = wi2;
           wo = wo2;
+          // byte b of ri/ro is disparity d0 + 31 - 4g - b
           const uint32_t ai = __vabsdiffu4(Lin, ri), ao = __vabsdiffu4(Lout, ro);
-          const uint32_t lo = __byte_perm(ai, ao, 0x5140), hi = __byte_perm(ai, ao, 0x7362);
-          // byte b of word g holds disparity d0 + 31 - 4g - b
-          V[31 - 4 * g] = dp4a_us(lo, 0x0000FF01u, V[31 - 4 * g]);
-          V[30 - 4 * g] = dp4a_us(lo, 0xFF010000u, V[30 - 4 * g]);
-          V[29 - 4 * g] = dp4a_us(hi, 0x0000FF01u, V[29 - 4 * g]);
-          V[28 - 4 * g] = dp4a_us(hi, 0xFF010000u, V[28 - 4 * g]);
+          // lane-wise u16 updates: sums stay in [0, 63*255], so no carry or
+          // borrow crosses the 16-bit lanes
+          Ve[g] = Ve[g] + (ai & 0x00FF00FFu) - (ao & 0x00FF00FFu);
+          Vo[g] = Vo[g] + __byte_perm(ai, 0u, 0x4341) - __byte_perm(ao, 0u, 0x4341);
         }
         if (y >= y_first) {
-          uint4* dst = reinterpret_cast<uint4*>(s_vs + k * (kThreads * kVsColBytes) + tid * kVsColBytes);
+          uint4* dst = reinterpret_cast<uint4*>(s_vs + (k * kVsCols + tid) * kVsStride);
 #pragma unroll
-          for (int qd = 0; qd < 4; ++qd) {
-            uint4 v;
-            v.x = __byte_perm(V[8 * qd + 0], V[8 * qd + 1], 0x5410);
-            v.y = __byte_perm(V[8 * qd + 2], V[8 * qd + 3], 0x5410);
-            v.z = __byte_perm(V[8 * qd + 4], V[8 * qd + 5], 0x5410);
-            v.w = __byte_perm(V[8 * qd + 6], V[8 * qd + 7], 0x5410);
-            dst[qd ^ ((tid >> 1) & 3)] = v;
-          }
+          for (int m = 0; m < 4; ++m) dst[m] = make_uint4(Ve[2 * m], Vo[2 * m], Ve[2 * m + 1], Vo[2 * m + 1]);
         }
+        sin = sin + 1 < ring ? sin + 1 : 0;
+        offLi = (offLi + wm) & 15;
+        offRi = (offRi + wm) & 15;
       }
     }
+    slot = slot_next;
+    offL = (offL + kGroup * wm) & 15;
+    offR = (offR + kGroup * wm) & 15;
     if (yg + ng - 1 < y_first) continue;  // still warming up
     __syncthreads();
-    // Stage B: warp -> (row slot, half strip); lane -> disparity
+    // Stage B: warp -> (row slot, half strip); lane -> disparity.  The warp
+    // slides the horizontal window along its half strip, 8 outputs per block.
     {
       const int g = warp >> 1, half = warp & 1;
       const int y = yg + g;
@@ -148,26 +206,46 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
         const int HW = TX / 2;
         const int xa = half * HW, xb = min(half * HW + HW, TX);
         const int d = d0 + lane;
-        const bool dvalid = d <= D;
-        const uint16_t* vs = reinterpret_cast<const uint16_t*>(s_vs);
-        auto V16 = [&](int col) -> uint32_t { return vs[vs_off(g, col, lane) >> 1]; };
+        const uint32_t dbits = d <= D ? (uint32_t)d : 0xFFFFFFFFu;  // invalid lanes never win
+        const uint16_t* vcol = reinterpret_cast<const uint16_t*>(s_vs + g * kVsCols * kVsStride) + lanepos;
+        constexpr int CS = kVsStride / 2;                              // u16 per column
+        const uint8_t* bm = s_bm + (buf * kGroup + g) * kBBytes + (int)(((int64_t)y * w + x0) & 15);
+        uint32_t* krow = J.key + (int64_t)y * w + x0;
+        auto anchor = [&](int xi) -> bool {  // strip-relative output column
+          const int xl = x0 + xi;
+          return xi < xb && xl >= xo0 && xl <= xo1 && (xl == xo0 || xl == xo1 || bm[xi]);
+        };
+        auto emit = [&](uint32_t S, int xi) {
+          const uint32_t key = dbits == 0xFFFFFFFFu ? 0xFFFFFFFFu : ((S << SB_KEY_DBITS) | dbits);
+          const uint32_t kmin = __reduce_min_sync(0xffffffffu, key);
+          if (lane == 0) atomicMin(&krow[xi], kmin);
+        };
         uint32_t S = 0;
-        for (int j = 0; j <= 2 * r; ++j) S += V16(xa + j);
-        const uint8_t* brow = J.bmap + (int64_t)y * w;
-        uint32_t* krow = J.key + (int64_t)y * w;
-        for (int xbase = xa; xbase < xb; xbase += 32) {
-          const int xl = x0 + xbase + lane;
-          bool anc = false;
-          if (xbase + lane < xb && xl >= xo0 && xl <= xo1) anc = (xl == xo0) || (xl == xo1) || brow[xl];
-          uint32_t mask = __ballot_sync(0xffffffffu, anc);
+        for (int j = 0; j <= 2 * r; ++j) S += vcol[(xa + j) * CS];
+        if (anchor(xa)) emit(S, xa);
+        for (int xbase = xa + 1; xbase < xb; xbase += 32) {
+          const unsigned mask = __ballot_sync(0xffffffffu, anchor(xbase + lane));
           const int n = min(32, xb - xbase);
-          for (int i = 0; i < n; ++i) {
-            const int xi = xbase + i;
-            if (xi > xa) S += V16(xi + 2 * r) - V16(xi - 1);
-            if (mask & (1u << i)) {
-              const uint32_t key = dvalid ? ((S << SB_KEY_DBITS) | (uint32_t)d) : 0xFFFFFFFFu;
-              const uint32_t kmin = __reduce_min_sync(0xffffffffu, key);
-              if (lane == 0) atomicMin(&krow[x0 + xi], kmin);
+          const uint16_t* pin = vcol + (xbase + 2 * r) * CS;   // entering column of output xbase
+          const uint16_t* pout = vcol + (xbase - 1) * CS;      // leaving column
+#pragma unroll 1
+          for (int i = 0; i < n; i += 8) {
+            uint32_t in[8], out[8], Sv[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              in[k] = pin[(i + k) * CS];
+              out[k] = pout[(i + k) * CS];
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              if (i + k < n) S += in[k] - out[k];
+              Sv[k] = S;
+            }
+            const unsigned bits = (mask >> i) & 0xFFu;
+            if (bits) {
+#pragma unroll
+              for (int k = 0; k < 8; ++k)
+                if (bits & (1u << k)) emit(Sv[k], xbase + i + k);
             }
           }
         }
@@ -177,18 +255,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
 }
 
 int sad_boxsum_smem_bytes(int r) {
-  const int ring = 2 * r + 1 + kGroup;
-  return (ring + 1) * kRowBytes + kGroup * kThreads * kVsColBytes;
+  const int ring = 2 * r + 1 + 2 * kGroup;
+  // + 16 columns: the unrolled Stage B block reads (and discards) up to 7
+  // columns past the end of a row slot
+  return (ring + 1) * kRowBytes + 2 * kGroup * kBBytes + kGroup * kVsCols * kVsStride + 16 * kVsStride;
 }
 
-void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, cudaStream_t s) {
+void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, cudaStream_t s) {
   if (n_items <= 0) return;
-  static int configured = 0;
-  const int smem = sad_boxsum_smem_bytes(31);
-  if (!configured) {
-    cudaFuncSetAttribute(k_sad_boxsum, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    configured = 1;
-  }
+  const int smem = sad_boxsum_smem_bytes(max_r);
+  cudaFuncSetAttribute(k_sad_boxsum, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_sad_boxsum<<<n_items, kThreads, smem, s>>>(jobs, items);
 }
 

@@ -538,8 +538,10 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
       sad_items(box, &items);
       const SadItem* di = upload(ctx, items, &st);
       if (!di) return st;
+      int max_r = 0;
+      for (auto& b : box) max_r = std::max(max_r, (b.second.p.block - 1) / 2);
       if (!ctx->dry) {
-        launch_sad_boxsum(d, di, (int)items.size(), s);
+        launch_sad_boxsum(d, di, (int)items.size(), max_r, s);
         SB_LAUNCHED(ctx, 1);
       }
     }
@@ -839,7 +841,7 @@ sb_status sb_boundary_sad(sb_context* ctx, const uint8_t* L_left, const uint8_t*
     sad_items({{0, g}}, &items);
     const SadItem* di = upload(ctx, items, &st);
     if (!di) return st;
-    launch_sad_boxsum(d, di, (int)items.size(), s);
+    launch_sad_boxsum(d, di, (int)items.size(), (block - 1) / 2, s);
   }
   SB_LAUNCHED(ctx, 1);
   launch_sad_finalize(d, 1, w, h, s);

@@ -91,7 +91,8 @@ struct SadJob {
 struct SadItem {
   int32_t job, x0, d0, y0, y1;  // output rows y0..y1 inclusive, inside Omega
 };
-void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, cudaStream_t s);
+// max_r: the largest block radius among the items (sizes shared memory)
+void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, cudaStream_t s);
 void launch_sad_direct(const SadJob* jobs, int n_jobs, int max_w, int max_h, cudaStream_t s);
 int sad_boxsum_smem_bytes(int r);
 void launch_sad_finalize(const SadJob* jobs, int n_jobs, int max_w, int max_h, cudaStream_t s);

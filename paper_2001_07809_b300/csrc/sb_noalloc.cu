@@ -139,7 +139,7 @@ extern "C" sb_status sb_boundary_sad_static(const uint8_t* L_left, const uint8_t
   if (direct)
     launch_sad_direct(djob, 1, w, h, s);
   else
-    launch_sad_boxsum(djob, (const SadItem*)(desc + 256), n_items, s);
+    launch_sad_boxsum(djob, (const SadItem*)(desc + 256), n_items, r, s);
   launch_sad_finalize(djob, 1, w, h, s);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
