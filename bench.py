@@ -176,6 +176,29 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------- multi-rank bookkeeping
+def rank_frames(rank: int, pairs: int):
+    """Frames of the video a rank processes: each rank takes its own `pairs`
+    consecutive frames (weak scaling, no data shared between ranks)."""
+    return list(range(rank * pairs, rank * pairs + pairs))
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The slowest rank's step time (the only cross-rank exchange of the bench)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(pairs_per_rank: int, world: int, ms_per_step_max: float) -> float:
+    """Whole-job pairs/s: all ranks' pairs over the slowest rank's step time."""
+    return pairs_per_rank * world / (ms_per_step_max / 1000.0)
+
+
 # ---------------------------------------------------------------- GPU side
 def anchor_counts(ctx, sb, torch, lefts, rights, params):
     """Anchors per pair (refined boundary pixels in the domain plus its border
@@ -198,6 +221,128 @@ def anchor_counts(ctx, sb, torch, lefts, rights, params):
     return [int(v) for v in torch.stack(out).cpu()]
 
 
+def uneven_measure(sb, torch, n_pairs=64, steps=3):
+    """Uneven batch (workload c4): 64 pairs, seeds 100-163, mixed resolution,
+    max disparity, block, K, interest range and sigma, in one batched launch
+    (CUDA graph) against the per-pair form on the same GPU; outputs compared."""
+    import synth
+    stream = torch.cuda.current_stream().cuda_stream
+    pairs, px = [], 0
+    for i in range(n_pairs):
+        sc, p, _ = synth.workload("c4", i)
+        dl = torch.empty((sc.h, sc.w, 3), dtype=torch.uint8, device="cuda")
+        dr = torch.empty_like(dl)
+        synth.render_device(sc, 0, dl, dr, None, stream)
+        params = sb.make_params(k=p.k, max_disp=p.max_disp, block=p.block, disp_threshold=p.disp_threshold,
+                                sigma=p.sigma, ranges=p.ranges)
+        o = torch.empty_like(dl)
+        d = torch.empty((sc.h, sc.w), dtype=torch.int16, device="cuda")
+        pairs.append(sb.Pair(dl, dr, params, o, d))
+        px += sc.w * sc.h
+    ctx = sb.Context(0)
+    res = {}
+    outs = {}
+    for name, flags in (("batched", sb.SB_RUN_BATCHED | sb.SB_RUN_GRAPH), ("per_pair", sb.SB_RUN_PLAIN)):
+        sb.sb_run(ctx, pairs, flags)
+        ctx.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            sb.sb_run(ctx, pairs, flags)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[name] = {"ms_per_step": ms, "pairs_s": n_pairs / (ms / 1000.0)}
+        outs[name] = [(q.out_rgb.clone(), q.out_disp.clone()) for q in pairs[::9]]
+    ctx.close()
+    res["identical"] = all(torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+                           for a, b in zip(outs["batched"], outs["per_pair"]))
+    res["pairs"] = n_pairs
+    res["megapixels"] = px / 1e6
+    return res
+
+
+def serve_measure(sb, torch, rates=(50.0, 150.0, 300.0), n_requests=240, pool=32, seed=7):
+    """Served form: requests drawn like the mixed-resolution workload (c5),
+    Poisson arrivals at each rate into the continuous-batching server (40 GB
+    admission budget), p50/p99 latency and achieved pairs/s; beside it, the
+    same requests executed one by one (host copy in, sb_run per pair, copy
+    out) on the same GPU."""
+    import synth
+    from paper_2001_07809_b300.serve import Server, percentile
+    reqs = []
+    stream = torch.cuda.current_stream().cuda_stream
+    for i in range(pool):
+        sc, p, _ = synth.workload("c5", i)
+        dl = torch.empty((sc.h, sc.w, 3), dtype=torch.uint8, device="cuda")
+        dr = torch.empty_like(dl)
+        synth.render_device(sc, 0, dl, dr, None, stream)
+        params = sb.make_params(k=p.k, max_disp=p.max_disp, block=p.block, disp_threshold=p.disp_threshold,
+                                sigma=p.sigma, ranges=p.ranges)
+        reqs.append((dl.cpu().pin_memory(), dr.cpu().pin_memory(), params))
+    torch.cuda.synchronize()
+    out = {"requests_per_rate": n_requests, "distinct_pairs": pool, "budget_gb": 40}
+    # one by one: copy in, one sb_run, copy out into pinned buffers, per request
+    ctx = sb.Context(0)
+    hout = {}
+    for hl, _, _ in reqs:
+        h, w = int(hl.shape[0]), int(hl.shape[1])
+        if (h, w) not in hout:
+            hout[(h, w)] = (torch.empty((h, w, 3), dtype=torch.uint8, pin_memory=True),
+                            torch.empty((h, w), dtype=torch.int16, pin_memory=True))
+    lat = []
+    for i in range(-pool, min(n_requests, 3 * pool)):      # the first pool requests warm up
+        hl, hr, p = reqs[i % pool]
+        t0 = time.perf_counter()
+        dl, dr = hl.cuda(non_blocking=True), hr.cuda(non_blocking=True)
+        o = torch.empty_like(dl)
+        d = torch.empty(dl.shape[:2], dtype=torch.int16, device="cuda")
+        sb.sb_run(ctx, [sb.Pair(dl, dr, p, o, d)], sb.SB_RUN_PLAIN)
+        ho, hd = hout[(int(hl.shape[0]), int(hl.shape[1]))]
+        ho.copy_(o, non_blocking=True)
+        hd.copy_(d, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        if i >= 0:
+            lat.append(time.perf_counter() - t0)
+    ctx.close()
+    out["one_by_one"] = {"p50_ms": 1e3 * percentile(lat, 50), "p99_ms": 1e3 * percentile(lat, 99),
+                         "pairs_s": len(lat) / sum(lat)}
+    rng = __import__("numpy").random.default_rng(seed)
+    for rate in rates:
+        srv = Server(0, mem_budget_bytes=40 << 30, max_batch=64)
+        pending = threading.Semaphore(0)
+
+        def done(f, srv=srv, pending=pending):
+            if f.exception() is None:
+                srv.recycle(f.result())
+            pending.release()
+
+        # warm-up: every distinct pair twice, in one burst
+        for i in range(2 * pool):
+            srv.submit(*reqs[i % pool]).add_done_callback(done)
+        for _ in range(2 * pool):
+            pending.acquire(timeout=300)
+        srv.completed.clear()
+        b0 = srv.batches
+        arrivals = synth.poisson_arrivals(n_requests, rate, seed)
+        t_start = time.perf_counter()
+        for i, ta in enumerate(arrivals):
+            now = time.perf_counter() - t_start
+            if ta > now:
+                time.sleep(ta - now)
+            srv.submit(*reqs[int(rng.integers(pool))]).add_done_callback(done)
+        for _ in range(n_requests):
+            if not pending.acquire(timeout=600):
+                raise RuntimeError("served request did not complete")
+        t_end = time.perf_counter()
+        lat = srv.latencies()
+        batches = srv.batches - b0
+        srv.close()
+        out["rate_%g" % rate] = {"p50_ms": 1e3 * percentile(lat, 50), "p99_ms": 1e3 * percentile(lat, 99),
+                                 "pairs_s": n_requests / (t_end - t_start), "batches": batches}
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -215,12 +360,8 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_ranks(v):
+        return max_over_ranks(v, world, "cuda")
 
     P, H, W = args.pairs, H_C3, W_C3
     scene = synth.scene_c3()
@@ -229,8 +370,8 @@ def run_ours(args):
     outs = torch.empty((P, H, W, 3), dtype=torch.uint8, device="cuda")
     disps = torch.empty((P, H, W), dtype=torch.int16, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
-    for i in range(P):  # each rank renders its own frames of the video
-        synth.render_device(scene, rank * P + i, lefts[i], rights[i], None, stream)
+    for i, f in enumerate(rank_frames(rank, P)):  # each rank renders its own frames of the video
+        synth.render_device(scene, f, lefts[i], rights[i], None, stream)
     torch.cuda.synchronize()
 
     params = sb.make_params(k=K_C3, max_disp=D_C3, block=B_C3, disp_threshold=1, sigma=SIGMA_C3,
@@ -265,8 +406,8 @@ def run_ours(args):
     launches = ctx.launch_count() - l0
     barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
-    ms_max = max_over_ranks(ms)
-    value = P * world / (ms_max / 1000.0)
+    ms_max = max_ranks(ms)
+    value = aggregate_rate(P, world, ms_max)
     stage_avg = [statistics.mean(s[i] for s in stage_ms) for i in range(len(sb.STAGES))]
     ctx.profile_enable(False)
 
@@ -281,7 +422,7 @@ def run_ours(args):
     e1.record()
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1) / plain_steps
-    plain_value = P * world / (max_over_ranks(plain_ms) / 1000.0)
+    plain_value = aggregate_rate(P, world, max_ranks(plain_ms))
     # identical outputs batched vs plain (spot check of one pair)
     ref_out, ref_disp = outs[7].clone(), disps[7].clone()
     sb.sb_run(ctx, pairs, flags)
@@ -322,11 +463,19 @@ def run_ours(args):
             ctx.synchronize()
         t1 = time.perf_counter()
         barrier()
-        e2e_s = max_over_ranks((t1 - t0) / e2e_steps)
+        e2e_s = max_ranks((t1 - t0) / e2e_steps)
         same = same and bool(torch.equal(ho[7].cuda(), outs[7]))
         e2e = {"value": P * world / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": P * H * W * 6,
                "d2h_bytes_per_step": P * H * W * 5, "ms_per_step": e2e_s * 1000.0}
         del hl, hr, ho, hd
+
+    serving = uneven = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        del lefts, rights, outs, disps, pairs
+        torch.cuda.empty_cache()
+        uneven = uneven_measure(sb, torch)
+        torch.cuda.empty_cache()
+        serving = serve_measure(sb, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -352,6 +501,8 @@ def run_ours(args):
                          "peak_note": "148 SMs x 128 INT32 lanes x %.0f MHz (max SM clock)" % sm_max,
                          "ops_per_launch": ops},
             "e2e": e2e,
+            "uneven_batch": uneven,
+            "serving": serving,
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -372,6 +523,7 @@ def main():
     ap.add_argument("--pairs", type=int, default=P_C3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

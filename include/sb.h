@@ -64,8 +64,10 @@ typedef struct {
  * 3x3 opening followed by a 3x3 closing. */
 enum { SB_MORPH_FILL_REMOVE = 0, SB_MORPH_OPEN_CLOSE = 1 };
 
-/* SAD implementation: chosen by the library's tuner, exhaustive window sums
- * at each boundary pixel, or running box sums over the domain. */
+/* SAD implementation: chosen per pair on the device from the pair's own
+ * boundary-pixel count N_b and a cost model (direct iff N_b * B^2 is small
+ * against w * h), exhaustive window sums at each boundary pixel, or running
+ * box sums over the domain.  Both are exact and give identical results. */
 enum { SB_SAD_AUTO = 0, SB_SAD_DIRECT = 1, SB_SAD_BOXSUM = 2 };
 
 typedef struct {

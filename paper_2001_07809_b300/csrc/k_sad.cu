@@ -16,12 +16,15 @@
 //     rows ahead, so every byte is read from HBM once per CTA and the copy
 //     overlaps the arithmetic.
 //   Stage B: lanes = disparities; a warp slides the horizontal sum
-//     S = sum_{|j|<=r} V(c+j) along its row segment and, at anchor pixels
+//     S = sum_{|j|<=r} V(c+j) along its row segment in blocks of 8 outputs
+//     (a zero column before each row of column sums lets every output use
+//     the same add-entering / drop-leaving update) and, at anchor pixels
 //     (warp-uniform test), reduces (S << 10 | d) over the 32 lanes with
 //     redux.sync and atomically keeps the minimum in the per-pixel key.
 // Direct variant (for low boundary density and small blocks): a warp per
 // anchor, lanes = disparities, vabsdiff4.add over the re-aligned 4-byte
 // words of each window row.
+#include <algorithm>
 #include "sb_common.cuh"
 
 namespace sb {
@@ -29,7 +32,7 @@ namespace sb {
 namespace {
 constexpr int kThreads = 256;
 constexpr int kGroup = 4;                       // output rows per Stage A -> Stage B hand-off
-constexpr int kVsCols = 240;                    // columns of a strip incl. the 2r halo (TX + 2r)
+constexpr int kVsCols = 248;                    // column slots per row: a zero column, then TX + 2r columns
 constexpr int kVsStride = 80;                   // bytes per column of 32 u16 sums (+16: conflict-free STS.128)
 constexpr int kLBytes = 272;                    // staged L bytes per row (240 + 16-byte alignment slack)
 constexpr int kRBytes = 320;                    // staged R bytes per row (240 + 31 + slack + look-ahead)
@@ -65,13 +68,14 @@ __device__ __forceinline__ void stage_chunk(uint8_t* dst, const uint8_t* img, in
 }
 }  // namespace
 
-__host__ __device__ int sad_boxsum_strip(int r) { return (kVsCols - 2 * r) & ~7; }
+__host__ __device__ int sad_boxsum_strip(int r) { return (kVsCols - 1 - 2 * r) & ~15; }
 
 __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __restrict__ jobs,
                                                             const SadItem* __restrict__ items) {
   extern __shared__ __align__(16) uint8_t smem[];
   const SadItem it = items[blockIdx.x];
   const SadJob J = jobs[it.job];
+  if (sad_use_direct(J)) return;                          // the direct kernel serves this pair
   const int r = J.r, D = J.D, w = J.w;
   const int64_t npx = (int64_t)w * J.h;
   const int ring = 2 * r + 1 + 2 * kGroup;                // + one group staged ahead
@@ -91,6 +95,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
   const int nchL = (15 + NC + 15) / 16, nchR = (15 + NC + 31 + 4 + 15) / 16, nchB = (15 + TX + 15) / 16;
 
   for (int i = tid; i < kRowBytes / 4; i += kThreads) reinterpret_cast<uint32_t*>(s_zero)[i] = 0u;
+  for (int i = tid; i < kGroup * (kVsStride / 4); i += kThreads)   // column 0 of every row slot is zero
+    reinterpret_cast<uint32_t*>(s_vs + (i / (kVsStride / 4)) * kVsCols * kVsStride)[i % (kVsStride / 4)] = 0u;
 
   // stage the entering rows of the group starting at virtual output row yg, and
   // the boundary-map rows of its real output rows, into buffer `buf`; thread
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
           Vo[g] = Vo[g] + __byte_perm(ai, 0u, 0x4341) - __byte_perm(ao, 0u, 0x4341);
         }
         if (y >= y_first) {
-          uint4* dst = reinterpret_cast<uint4*>(s_vs + (k * kVsCols + tid) * kVsStride);
+          uint4* dst = reinterpret_cast<uint4*>(s_vs + (k * kVsCols + tid + 1) * kVsStride);
 #pragma unroll
           for (int m = 0; m < 4; ++m) dst[m] = make_uint4(Ve[2 * m], Vo[2 * m], Ve[2 * m + 1], Vo[2 * m + 1]);
         }
@@ -220,31 +226,33 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
           const uint32_t kmin = __reduce_min_sync(0xffffffffu, key);
           if (lane == 0) atomicMin(&krow[xi], kmin);
         };
+        // S starts as the window of output xa - 1 (column xa - 1 + j, shifted by
+        // the zero column: slot column xa + j), then every output adds its
+        // entering column and drops its leaving one; HW is a multiple of 8.
         uint32_t S = 0;
         for (int j = 0; j <= 2 * r; ++j) S += vcol[(xa + j) * CS];
-        if (anchor(xa)) emit(S, xa);
-        for (int xbase = xa + 1; xbase < xb; xbase += 32) {
+        for (int xbase = xa; xbase < xb; xbase += 32) {
           const unsigned mask = __ballot_sync(0xffffffffu, anchor(xbase + lane));
           const int n = min(32, xb - xbase);
-          const uint16_t* pin = vcol + (xbase + 2 * r) * CS;   // entering column of output xbase
-          const uint16_t* pout = vcol + (xbase - 1) * CS;      // leaving column
+          const uint16_t* pin = vcol + (xbase + 2 * r + 1) * CS;  // slot column of strip column x + 2r
+          const uint16_t* pout = vcol + xbase * CS;             // slot column of x - 1
 #pragma unroll 1
           for (int i = 0; i < n; i += 8) {
-            uint32_t in[8], out[8], Sv[8];
+            uint32_t Sv[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-              in[k] = pin[(i + k) * CS];
-              out[k] = pout[(i + k) * CS];
-            }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              if (i + k < n) S += in[k] - out[k];
+              S += (uint32_t)pin[(i + k) * CS] - (uint32_t)pout[(i + k) * CS];
               Sv[k] = S;
             }
             const unsigned bits = (mask >> i) & 0xFFu;
-            if (bits) {
+            if (bits & 0x0Fu) {
 #pragma unroll
-              for (int k = 0; k < 8; ++k)
+              for (int k = 0; k < 4; ++k)
+                if (bits & (1u << k)) emit(Sv[k], xbase + i + k);
+            }
+            if (bits & 0xF0u) {
+#pragma unroll
+              for (int k = 4; k < 8; ++k)
                 if (bits & (1u << k)) emit(Sv[k], xbase + i + k);
             }
           }
@@ -256,9 +264,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
 
 int sad_boxsum_smem_bytes(int r) {
   const int ring = 2 * r + 1 + 2 * kGroup;
-  // + 16 columns: the unrolled Stage B block reads (and discards) up to 7
-  // columns past the end of a row slot
-  return (ring + 1) * kRowBytes + 2 * kGroup * kBBytes + kGroup * kVsCols * kVsStride + 16 * kVsStride;
+  return (ring + 1) * kRowBytes + 2 * kGroup * kBBytes + kGroup * kVsCols * kVsStride;
 }
 
 void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, cudaStream_t s) {
@@ -281,92 +287,126 @@ __device__ __forceinline__ uint32_t load_word(const uint8_t* base, int64_t off, 
 }
 }  // namespace
 // One warp per (row, 32-column chunk); every anchor of the chunk is matched
-// by the whole warp, lanes = disparities d0 + lane for d0 = 0, 32, ...
-__global__ void __launch_bounds__(256) k_sad_direct(const SadJob* __restrict__ jobs) {
-  const SadJob J = jobs[blockIdx.z];
-  const int r = J.r, D = J.D, w = J.w, B = 2 * r + 1;
-  const int y = r + blockIdx.y;
-  if (y > J.h - 1 - r) return;
-  const int lane = threadIdx.x & 31;
-  const int xo0 = D + r, xo1 = w - 1 - r;
-  const int x = xo0 + (blockIdx.x * 8 + (threadIdx.x >> 5)) * 32 + lane;
-  bool anc = false;
-  if (x <= xo1) anc = (x == xo0) || (x == xo1) || J.bmap[(int64_t)y * w + x];
-  uint32_t mask = __ballot_sync(0xffffffffu, anc);
-  const int nw = (B + 3) >> 2;                         // words per window row
-  const int64_t nimg = (int64_t)w * J.h;
-  const uint32_t lastmask = (B & 3) ? (0xFFFFFFFFu >> (8 * (4 - (B & 3)))) : 0xFFFFFFFFu;
-  while (mask) {
-    const int i = __ffs(mask) - 1;
-    mask &= mask - 1;
-    const int xa = x - lane + i;                        // the anchor
-    uint32_t best = 0xFFFFFFFFu;
-    for (int d0 = 0; d0 <= D; d0 += 32) {
-      const int d = d0 + lane;
-      const bool dv = d <= D;
-      const int dd = dv ? d : D;                        // keep addresses inside the image
-      uint32_t acc = 0;
-      const int lstart = xa - r, rstart = xa - r - dd;
-      for (int iy = -r; iy <= r; ++iy) {
-        // word-aligned absolute offsets of the window starts in this row
-        const int64_t row = (int64_t)(y + iy) * w;
-        const int64_t labs = row + lstart, rabs = row + rstart;
-        const int64_t la = labs & ~(int64_t)3, ra = rabs & ~(int64_t)3;
-        const int lsh = (int)(labs & 3) * 8, rsh = (int)(rabs & 3) * 8;
-        uint32_t lp = load_word(J.Ll, la, nimg), rp = load_word(J.Lr, ra, nimg);
-        for (int k = 0; k < nw; ++k) {
-          const uint32_t ln = load_word(J.Ll, la + 4 * k + 4, nimg);
-          const uint32_t rn = load_word(J.Lr, ra + 4 * k + 4, nimg);
-          uint32_t lw = __funnelshift_r(lp, ln, lsh), rw = __funnelshift_r(rp, rn, rsh);
-          lp = ln;
-          rp = rn;
-          if (k == nw - 1) { lw &= lastmask; rw &= lastmask; }
-          asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %0;" : "+r"(acc) : "r"(lw), "r"(rw));
+// by the whole warp, lanes = disparities d0 + lane for d0 = 0, 32, ...  A
+// persistent grid walks the jobs in order; a job served by the box-sum kernel
+// costs each CTA one descriptor read.
+__global__ void __launch_bounds__(256) k_sad_direct(const SadJob* __restrict__ jobs, int n_jobs) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j = 0; j < n_jobs; ++j) {
+    const SadJob J = jobs[j];
+    if (!sad_use_direct(J)) continue;
+    const int r = J.r, D = J.D, w = J.w, B = 2 * r + 1;
+    const int xo0 = D + r, xo1 = w - 1 - r;
+    const int xblocks = (xo1 - xo0 + 256) / 256;          // 256-column blocks of Omega
+    const int64_t units = (int64_t)(J.h - 2 * r) * xblocks;
+    const int nw = (B + 3) >> 2;                           // words per window row
+    const int64_t nimg = (int64_t)w * J.h;
+    const uint32_t lastmask = (B & 3) ? (0xFFFFFFFFu >> (8 * (4 - (B & 3)))) : 0xFFFFFFFFu;
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+      const int y = r + (int)(u / xblocks);
+      const int x = xo0 + ((int)(u % xblocks) * 8 + wid) * 32 + lane;
+      bool anc = false;
+      if (x <= xo1) anc = (x == xo0) || (x == xo1) || J.bmap[(int64_t)y * w + x];
+      uint32_t mask = __ballot_sync(0xffffffffu, anc);
+      while (mask) {
+        const int i = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int xa = x - lane + i;                        // the anchor
+        uint32_t best = 0xFFFFFFFFu;
+        for (int d0 = 0; d0 <= D; d0 += 32) {
+          const int d = d0 + lane;
+          const bool dv = d <= D;
+          const int dd = dv ? d : D;                        // keep addresses inside the image
+          uint32_t acc = 0;
+          const int lstart = xa - r, rstart = xa - r - dd;
+          for (int iy = -r; iy <= r; ++iy) {
+            // word-aligned absolute offsets of the window starts in this row
+            const int64_t row = (int64_t)(y + iy) * w;
+            const int64_t labs = row + lstart, rabs = row + rstart;
+            const int64_t la = labs & ~(int64_t)3, ra = rabs & ~(int64_t)3;
+            const int lsh = (int)(labs & 3) * 8, rsh = (int)(rabs & 3) * 8;
+            uint32_t lp = load_word(J.Ll, la, nimg), rp = load_word(J.Lr, ra, nimg);
+            for (int k = 0; k < nw; ++k) {
+              const uint32_t ln = load_word(J.Ll, la + 4 * k + 4, nimg);
+              const uint32_t rn = load_word(J.Lr, ra + 4 * k + 4, nimg);
+              uint32_t lw = __funnelshift_r(lp, ln, lsh), rw = __funnelshift_r(rp, rn, rsh);
+              lp = ln;
+              rp = rn;
+              if (k == nw - 1) { lw &= lastmask; rw &= lastmask; }
+              asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %0;" : "+r"(acc) : "r"(lw), "r"(rw));
+            }
+          }
+          const uint32_t key = dv ? ((acc << SB_KEY_DBITS) | (uint32_t)d) : 0xFFFFFFFFu;
+          best = min(best, __reduce_min_sync(0xffffffffu, key));
         }
+        if (lane == 0) J.key[(int64_t)y * w + xa] = best;
       }
-      const uint32_t key = dv ? ((acc << SB_KEY_DBITS) | (uint32_t)d) : 0xFFFFFFFFu;
-      best = min(best, __reduce_min_sync(0xffffffffu, key));
     }
-    if (lane == 0) J.key[(int64_t)y * w + xa] = best;
   }
 }
 
-void launch_sad_direct(const SadJob* jobs, int n_jobs, int max_w, int max_h, cudaStream_t s) {
+void launch_sad_direct(const SadJob* jobs, int n_jobs, cudaStream_t s) {
   if (n_jobs <= 0) return;
-  dim3 grid((max_w + 255) / 256, max_h, n_jobs);
-  k_sad_direct<<<grid, 256, 0, s>>>(jobs);
+  static int grid = 0;
+  if (!grid) {
+    int dev = 0, sms = 148, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sad_direct, 256, 0);
+    grid = sms * std::max(1, per_sm);
+  }
+  k_sad_direct<<<grid, 256, 0, s>>>(jobs, n_jobs);
 }
 
-// keys -> disparity (uint16, UNDET off the anchors) and cost
-__global__ void __launch_bounds__(256) k_sad_finalize(const SadJob* __restrict__ jobs) {
-  const SadJob J = jobs[blockIdx.y];
-  const int w = J.w, h = J.h, r = J.r;
-  const int xo0 = J.D + r, xo1 = w - 1 - r;
-  const int64_t n = (int64_t)w * h;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-    const int y = (int)(p / w), x = (int)(p - (int64_t)y * w);
-    const bool in = y >= r && y <= h - 1 - r && x >= xo0 && x <= xo1;
-    const bool anc = in && (x == xo0 || x == xo1 || J.bmap[p]);
-    uint16_t dv = SB_UNDET16;
-    uint32_t cv = 0;
-    if (anc) {
-      const uint32_t k = J.key[p];
-      dv = (uint16_t)(k & ((1u << SB_KEY_DBITS) - 1));
-      cv = k >> SB_KEY_DBITS;
-    }
-    J.disp[p] = dv;
-    if (J.cost) J.cost[p] = cv;
+// Nonzero bytes of each map (the boundary count the variant choice reads);
+// out[i] must be zero on entry.
+__global__ void __launch_bounds__(256) k_count_nonzero(const uint8_t* const* __restrict__ maps,
+                                                       const int64_t* __restrict__ n, int64_t* __restrict__ out) {
+  const uint8_t* m = maps[blockIdx.y];
+  const int64_t N = n[blockIdx.y];
+  unsigned long long c = 0;
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < N; i += (int64_t)gridDim.x * 256) c += m[i] != 0;
+  for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  __shared__ unsigned long long s_c[8];
+  if ((threadIdx.x & 31) == 0) s_c[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int i = 0; i < 8; ++i) t += s_c[i];
+    if (t) atomicAdd(reinterpret_cast<unsigned long long*>(&out[blockIdx.y]), t);
   }
+}
+
+void launch_count_nonzero(const uint8_t* const* maps, const int64_t* n, int64_t* out, int n_maps, cudaStream_t s) {
+  if (n_maps <= 0) return;
+  k_count_nonzero<<<dim3(148, n_maps), 256, 0, s>>>(maps, n, out);
+}
+
+// keys -> disparity (uint16, UNDET off the anchors) and cost; grid = (column
+// blocks of 256, rows, jobs)
+__global__ void __launch_bounds__(256) k_sad_finalize(const SadJob* __restrict__ jobs) {
+  const SadJob J = jobs[blockIdx.z];
+  const int w = J.w, h = J.h, r = J.r;
+  const int y = blockIdx.y, x = blockIdx.x * 256 + threadIdx.x;
+  if (y >= h || x >= w) return;
+  const int xo0 = J.D + r, xo1 = w - 1 - r;
+  const int64_t p = (int64_t)y * w + x;
+  const bool in = y >= r && y <= h - 1 - r && x >= xo0 && x <= xo1;
+  const bool anc = in && (x == xo0 || x == xo1 || J.bmap[p]);
+  uint16_t dv = SB_UNDET16;
+  uint32_t cv = 0;
+  if (anc) {
+    const uint32_t k = J.key[p];
+    dv = (uint16_t)(k & ((1u << SB_KEY_DBITS) - 1));
+    cv = k >> SB_KEY_DBITS;
+  }
+  J.disp[p] = dv;
+  if (J.cost) J.cost[p] = cv;
 }
 
 void launch_sad_finalize(const SadJob* jobs, int n_jobs, int max_w, int max_h, cudaStream_t s) {
   if (n_jobs <= 0) return;
-  const int64_t n = (int64_t)max_w * max_h;
-  int bpj = (int)((n + 256 * 8 - 1) / (256 * 8));
-  if (bpj > 1184) bpj = 1184;
-  if (bpj < 1) bpj = 1;
-  k_sad_finalize<<<dim3(bpj, n_jobs), 256, 0, s>>>(jobs);
+  k_sad_finalize<<<dim3((max_w + 255) / 256, max_h, n_jobs), 256, 0, s>>>(jobs);
 }
 
 }  // namespace sb

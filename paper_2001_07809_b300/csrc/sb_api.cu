@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <memory>
 #include <string>
@@ -170,7 +171,6 @@ struct sb_context {
   size_t ws_bytes = 0;
   Uploader up;
   cudaStream_t s_in = nullptr, s_out = nullptr;  // host-buffer streaming
-  double last_density = 0.2;                      // boundary density seen last (for the tuner)
   // graph cache (batched form)
   struct GraphEntry {
     std::string key;
@@ -188,11 +188,6 @@ struct sb_context {
   size_t blob_cap = 0;
   uint8_t* blob_host = nullptr;  // pinned staging of the blob
   cudaEvent_t blob_ev = nullptr;
-  // boundary density feedback for the SAD variant choice
-  int64_t* dens_host = nullptr;  // pinned: N_b of the last pair measured
-  cudaEvent_t dens_ev = nullptr;
-  int64_t dens_px = 0;
-  bool dens_pending = false;
   // stage profiling
   bool prof_on = false;
   cudaEvent_t prof_ev[SB_N_STAGES + 1] = {};
@@ -286,11 +281,21 @@ sb_status ensure_ws(sb_context* ctx, size_t bytes) {
   if (bytes <= ctx->ws_bytes) return SB_OK;
   if (ctx->budget && bytes > ctx->budget)
     return fail(ctx, SB_ERR_OOM, "workspace of %zu bytes exceeds the budget of %zu bytes", bytes, ctx->budget);
+  // grow by at least half again, so that a context fed batches of varying
+  // size (a serving loop) re-allocates, and synchronises, a few times only
+  size_t grow = ctx->ws_bytes + ctx->ws_bytes / 2;
+  if (ctx->budget && grow > ctx->budget) grow = ctx->budget;
   SB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (ctx->ws) cudaFree(ctx->ws);
   ctx->ws = nullptr;
   ctx->ws_bytes = 0;
-  cudaError_t e = cudaMalloc(&ctx->ws, bytes);
+  cudaError_t e = cudaErrorMemoryAllocation;
+  if (grow > bytes) {
+    e = cudaMalloc(&ctx->ws, grow);
+    if (e == cudaSuccess) bytes = grow;
+    else cudaGetLastError();   // no room for the margin: take the exact size
+  }
+  if (e != cudaSuccess) e = cudaMalloc(&ctx->ws, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(ctx, SB_ERR_OOM, "cudaMalloc of %zu workspace bytes failed: %s", bytes, cudaGetErrorString(e));
@@ -338,23 +343,33 @@ bool params_ok(sb_context* ctx, int w, int h, const sb_params& p, sb_status* st)
 // --------------------------------------------------------------- tuner
 // Box sums cost about kBoxNsPerPxD per (domain pixel, disparity); direct
 // window sums about kDirectNsPerCell per (anchor, disparity, window cell).
-// Both constants are refreshed from measured kernel times.
-struct Tuner {
-  double box_ns_per_pxd = 0.0012;
-  double direct_ns_per_cell = 0.00009;
-  bool prefer_direct(int w, int h, int D, int B, double density) const {
-    const int r = (B - 1) / 2;
-    const double omega = (double)(w - D - 2 * r) * (double)(h - 2 * r);
-    const double box = omega * (D + 1) * box_ns_per_pxd;
-    const double dir = omega * density * (D + 1) * (double)B * B * direct_ns_per_cell;
-    return dir < box;
-  }
-};
-Tuner g_tuner;
+// With N_b boundary pixels in the image, the direct variant is the cheaper
+// one iff N_b |Omega|/(w h) B^2 c_direct < |Omega| c_box, i.e. N_b below
+// w h c_box / (B^2 c_direct).  The count is only known on the device once
+// the boundary map exists, so the host passes that limit with each job and
+// the kernels compare it with the pair's own count (no read-back, and a
+// replayed graph re-decides for every new frame).
+constexpr double kBoxNsPerPxD = 0.0012;
+constexpr double kDirectNsPerCell = 0.00009;
 
-int sad_variant_of(sb_context* ctx, const Geo& g) {
-  if (g.p.sad_variant == SB_SAD_DIRECT || g.p.sad_variant == SB_SAD_BOXSUM) return g.p.sad_variant;
-  return g_tuner.prefer_direct(g.w, g.h, g.p.max_disp, g.p.block, ctx->last_density) ? SB_SAD_DIRECT : SB_SAD_BOXSUM;
+// (nb, nb_direct_max) of a job; *direct_possible / *box_possible say which
+// kernels may serve it.
+void sad_choice(const Geo& g, const int64_t* nb, SadJob* j, bool* direct_possible, bool* box_possible) {
+  if (g.p.sad_variant == SB_SAD_DIRECT || g.p.sad_variant == SB_SAD_BOXSUM) {
+    const bool dir = g.p.sad_variant == SB_SAD_DIRECT;
+    j->nb = nullptr;
+    j->nb_direct_max = dir ? 1 : -1;
+    *direct_possible = dir;
+    *box_possible = !dir;
+    return;
+  }
+  const double B = g.p.block;
+  const double lim = (double)g.w * g.h * kBoxNsPerPxD / (B * B * kDirectNsPerCell);
+  const int64_t m = (int64_t)std::ceil(lim) - 1;   // N_b <= m  <=>  N_b < lim
+  j->nb = m >= 0 ? nb : nullptr;
+  j->nb_direct_max = m;
+  *direct_possible = m >= 0;
+  *box_possible = true;
 }
 
 // Box-sum work items: (pair, strip, disparity chunk, row band); bands are cut
@@ -501,34 +516,23 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
       launch_cc_filter(d, n, max_w, max_h, s);
       SB_LAUNCHED(ctx, 6);
     }
-    // boundary count of the first pair, read back asynchronously for the tuner
-    if (!ctx->dry && ctx->sink == 0 && !ctx->dens_pending && ctx->dens_host) {
-      SB_CUDA(ctx, cudaMemcpyAsync(ctx->dens_host, runs[0].ws.cut, 8, cudaMemcpyDeviceToHost, s));
-      SB_CUDA(ctx, cudaEventRecord(ctx->dens_ev, s));
-      ctx->dens_px = (int64_t)runs[0].g.w * runs[0].g.h;
-      ctx->dens_pending = true;
-    }
   }
   // 5. SAD at the anchors
   {
     std::vector<SadJob> J;
     std::vector<std::pair<int, Geo>> box;
-    std::vector<SadJob> direct;
-    int dw = 0, dh = 0;
+    bool any_direct = false;
     for (int i = 0; i < n; ++i) {
       auto& r = runs[i];
       const size_t N = (size_t)r.g.w * r.g.h;
       SB_MEMSET(ctx, (r.ws.size_key, 0xFF, N * 4, s));
       SadJob sj{r.ws.Ll, r.ws.Lr, r.ws.filtered, r.ws.size_key, r.ws.sparse, nullptr, r.g.w, r.g.h,
-                r.g.p.max_disp, (r.g.p.block - 1) / 2};
+                r.g.p.max_disp, (r.g.p.block - 1) / 2, nullptr, -1};
+      bool dp = false, bp = true;
+      sad_choice(r.g, r.ws.cut, &sj, &dp, &bp);   // cut[0]: boundary pixels of the refined map
       J.push_back(sj);
-      if (sad_variant_of(ctx, r.g) == SB_SAD_DIRECT) {
-        direct.push_back(sj);
-        dw = std::max(dw, r.g.w);
-        dh = std::max(dh, r.g.h);
-      } else {
-        box.push_back({i, r.g});
-      }
+      any_direct |= dp;
+      if (bp) box.push_back({i, r.g});
     }
     const SadJob* d = upload(ctx, J, &st);
     if (!d) return st;
@@ -545,13 +549,9 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
         SB_LAUNCHED(ctx, 1);
       }
     }
-    if (!direct.empty()) {
-      const SadJob* dd = upload(ctx, direct, &st);
-      if (!dd) return st;
-      if (!ctx->dry) {
-        launch_sad_direct(dd, (int)direct.size(), dw, dh, s);
-        SB_LAUNCHED(ctx, 1);
-      }
+    if (any_direct && !ctx->dry) {
+      launch_sad_direct(d, n, s);
+      SB_LAUNCHED(ctx, 1);
     }
     SB_MARK(ctx, SB_STAGE_SAD_FINALIZE);
     if (!ctx->dry) {
@@ -644,9 +644,6 @@ sb_status sb_create(int device, size_t mem_budget_bytes, void* cuda_stream, sb_c
   if (build_tables(ctx.get()) != SB_OK) return SB_ERR_CUDA;
   if (cudaMalloc(&ctx->dev_err, 4) != cudaSuccess || cudaMemset(ctx->dev_err, 0, 4) != cudaSuccess) return SB_ERR_CUDA;
   if (ctx->up.init(8 << 20) != cudaSuccess) return SB_ERR_OOM;
-  if (cudaMallocHost(&ctx->dens_host, 8) != cudaSuccess) return SB_ERR_OOM;
-  ctx->dens_host[0] = 0;
-  if (cudaEventCreateWithFlags(&ctx->dens_ev, cudaEventDisableTiming) != cudaSuccess) return SB_ERR_CUDA;
   *out = ctx.release();
   return SB_OK;
 }
@@ -661,8 +658,6 @@ void sb_destroy(sb_context* ctx) {
   if (ctx->blob_dev) cudaFree(ctx->blob_dev);
   if (ctx->blob_host) cudaFreeHost(ctx->blob_host);
   if (ctx->blob_ev) cudaEventDestroy(ctx->blob_ev);
-  if (ctx->dens_host) cudaFreeHost(ctx->dens_host);
-  if (ctx->dens_ev) cudaEventDestroy(ctx->dens_ev);
   for (int i = 0; i <= SB_N_STAGES; ++i)
     if (ctx->prof_ev[i]) cudaEventDestroy(ctx->prof_ev[i]);
   if (ctx->tables) cudaFree(ctx->tables);
@@ -821,29 +816,43 @@ sb_status sb_boundary_sad(sb_context* ctx, const uint8_t* L_left, const uint8_t*
   if (!geometry_ok(ctx, w, h, max_disp, block, &st)) return st;
   if (variant < SB_SAD_AUTO || variant > SB_SAD_BOXSUM) return fail(ctx, SB_ERR_INVALID_ARG, "unknown SAD variant %d", variant);
   const size_t N = (size_t)w * h;
-  st = ensure_ws(ctx, al(N * 4));
+  st = ensure_ws(ctx, al(N * 4) + al(8));
   if (st != SB_OK) return st;
   uint32_t* key = (uint32_t*)ctx->ws;
+  int64_t* count = (int64_t*)(ctx->ws + al(N * 4));
   cudaStream_t s = ctx->stream;
   SB_CUDA(ctx, cudaMemsetAsync(key, 0xFF, N * 4, s));
-  std::vector<SadJob> J{SadJob{L_left, L_right, boundary, key, disp, cost, w, h, max_disp, (block - 1) / 2}};
-  const SadJob* d = upload(ctx, J, &st);
-  if (!d) return st;
   Geo g{w, h, {}};
   sb_default_params(&g.p);
   g.p.max_disp = max_disp;
   g.p.block = block;
   g.p.sad_variant = variant;
-  if (sad_variant_of(ctx, g) == SB_SAD_DIRECT) {
-    launch_sad_direct(d, 1, w, h, s);
-  } else {
+  SadJob job{L_left, L_right, boundary, key, disp, cost, w, h, max_disp, (block - 1) / 2, nullptr, -1};
+  bool dp = false, bp = true;
+  sad_choice(g, count, &job, &dp, &bp);
+  if (dp && bp) {   // both possible: count the boundary pixels on the device
+    SB_CUDA(ctx, cudaMemsetAsync(count, 0, 8, s));
+    const uint8_t* const* dm = upload(ctx, std::vector<const uint8_t*>{boundary}, &st);
+    if (!dm) return st;
+    const int64_t* dn = upload(ctx, std::vector<int64_t>{(int64_t)N}, &st);
+    if (!dn) return st;
+    launch_count_nonzero(dm, dn, count, 1, s);
+    SB_LAUNCHED(ctx, 1);
+  }
+  const SadJob* d = upload(ctx, std::vector<SadJob>{job}, &st);
+  if (!d) return st;
+  if (bp) {
     std::vector<SadItem> items;
     sad_items({{0, g}}, &items);
     const SadItem* di = upload(ctx, items, &st);
     if (!di) return st;
     launch_sad_boxsum(d, di, (int)items.size(), (block - 1) / 2, s);
+    SB_LAUNCHED(ctx, 1);
   }
-  SB_LAUNCHED(ctx, 1);
+  if (dp) {
+    launch_sad_direct(d, 1, s);
+    SB_LAUNCHED(ctx, 1);
+  }
   launch_sad_finalize(d, 1, w, h, s);
   SB_LAUNCHED(ctx, 1);
   return SB_OK;
@@ -1125,10 +1134,6 @@ extern "C" sb_status sb_run(sb_context* ctx, const sb_pair* pairs, int32_t n_pai
   }
   if (n_pairs == 0) return SB_OK;
   cudaSetDevice(ctx->device);
-  if (ctx->dens_pending && cudaEventQuery(ctx->dens_ev) == cudaSuccess) {
-    if (ctx->dens_px > 0) ctx->last_density = (double)ctx->dens_host[0] / (double)ctx->dens_px;
-    ctx->dens_pending = false;
-  }
   if (flags & SB_RUN_HOST_IO) return run_host_io(ctx, pairs, n_pairs, (flags & SB_RUN_BATCHED) != 0);
   if (flags & SB_RUN_GRAPH) return run_graph(ctx, pairs, n_pairs);
   return run_device(ctx, pairs, n_pairs, (flags & SB_RUN_BATCHED) != 0);

@@ -86,14 +86,24 @@ struct SadJob {
   uint16_t* disp;       // out
   uint32_t* cost;       // out or nullptr
   int32_t w, h, D, r;
+  // Variant choice, taken on the device from the pair's own boundary count:
+  // the direct kernel serves the job iff *nb <= nb_direct_max, the box-sum
+  // kernel otherwise (nb null: direct iff nb_direct_max >= 0).
+  const int64_t* nb;
+  int64_t nb_direct_max;
 };
+
+__device__ __forceinline__ bool sad_use_direct(const SadJob& J) {
+  return J.nb ? (*J.nb <= J.nb_direct_max) : (J.nb_direct_max >= 0);
+}
 // Box-sum variant: items = (job, column strip, disparity chunk, row band)
 struct SadItem {
   int32_t job, x0, d0, y0, y1;  // output rows y0..y1 inclusive, inside Omega
 };
 // max_r: the largest block radius among the items (sizes shared memory)
 void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, cudaStream_t s);
-void launch_sad_direct(const SadJob* jobs, int n_jobs, int max_w, int max_h, cudaStream_t s);
+void launch_sad_direct(const SadJob* jobs, int n_jobs, cudaStream_t s);
+void launch_count_nonzero(const uint8_t* const* maps, const int64_t* n, int64_t* out, int n_maps, cudaStream_t s);
 int sad_boxsum_smem_bytes(int r);
 void launch_sad_finalize(const SadJob* jobs, int n_jobs, int max_w, int max_h, cudaStream_t s);
 // strip width of the box-sum kernel for radius r
@@ -121,6 +131,6 @@ struct BlurJob {
   int32_t lo[8], hi[8];
 };
 void launch_blur(const BlurJob* jobs, int n_jobs, int max_w, int max_h, int max_R, cudaStream_t s);
-int blur_smem_bytes(int R);
+__host__ __device__ int blur_smem_bytes(int R);
 
 }  // namespace sb

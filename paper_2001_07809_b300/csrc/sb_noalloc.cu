@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -94,21 +95,33 @@ extern "C" sb_status sb_boundary_sad_static(const uint8_t* L_left, const uint8_t
   uint32_t* key = (uint32_t*)base;
   uint8_t* desc = base + kKeyBytes;
 
-  // descriptors: one job, then the box-sum work items (strip x disparity chunk x row band)
+  // descriptors: one job (and, at kCountOff, the boundary map, its size and a
+  // zeroed count for the device-side variant choice), then the box-sum work
+  // items (strip x disparity chunk x row band)
   const int r = (block - 1) / 2;
-  SadJob job{L_left, L_right, boundary, key, disp, cost, w, h, max_disp, r};
-  const int xo0 = max_disp + r, xo1 = w - 1 - r, yo0 = r, yo1 = h - 1 - r;
-  const int rows = yo1 - yo0 + 1, ncols = xo1 - xo0 + 1;
-  bool direct = variant == SB_SAD_DIRECT;
-  if (variant == SB_SAD_AUTO) {  // same cost model as the context path, at a 20 % boundary density
-    const double box = (double)(max_disp + 1) * 0.0012;
-    const double dir = 0.2 * (max_disp + 1) * (double)block * block * 0.00009;
-    direct = dir < box;
+  constexpr size_t kCountOff = 192;
+  static_assert(sizeof(SadJob) <= kCountOff, "job descriptor overlaps the count block");
+  SadJob job{L_left, L_right, boundary, key, disp, cost, w, h, max_disp, r, nullptr, -1};
+  bool run_direct = variant == SB_SAD_DIRECT, run_box = variant == SB_SAD_BOXSUM;
+  if (variant == SB_SAD_AUTO) {   // same cost model as the context path, decided from the map's own count
+    const double lim = (double)w * h * 0.0012 / ((double)block * block * 0.00009);
+    job.nb_direct_max = (int64_t)std::ceil(lim) - 1;
+    job.nb = job.nb_direct_max >= 0 ? (const int64_t*)(desc + kCountOff + 16) : nullptr;
+    run_direct = job.nb_direct_max >= 0;
+    run_box = true;
+  } else {
+    job.nb_direct_max = run_direct ? 1 : -1;
   }
-  std::vector<uint8_t> blob(256);
+  const int64_t npx = (int64_t)w * h, zero = 0;
+  std::vector<uint8_t> blob(256, 0);
   memcpy(blob.data(), &job, sizeof job);
+  memcpy(blob.data() + kCountOff, &boundary, sizeof boundary);
+  memcpy(blob.data() + kCountOff + 8, &npx, 8);
+  memcpy(blob.data() + kCountOff + 16, &zero, 8);
   int n_items = 0;
-  if (!direct) {
+  if (run_box) {
+    const int xo0 = max_disp + r, xo1 = w - 1 - r, yo0 = r, yo1 = h - 1 - r;
+    const int rows = yo1 - yo0 + 1, ncols = xo1 - xo0 + 1;
     const int TX = sad_boxsum_strip(r);
     const int64_t base_items = (int64_t)((ncols + TX - 1) / TX) * ((max_disp + 1 + kSadChunk - 1) / kSadChunk);
     int bands = (int)std::max<int64_t>(1, (888 + base_items - 1) / base_items);
@@ -136,10 +149,11 @@ extern "C" sb_status sb_boundary_sad_static(const uint8_t* L_left, const uint8_t
     return report(errbuf, errbuf_len, SB_ERR_CUDA, msg);
   }
   const SadJob* djob = (const SadJob*)desc;
-  if (direct)
-    launch_sad_direct(djob, 1, w, h, s);
-  else
-    launch_sad_boxsum(djob, (const SadItem*)(desc + 256), n_items, r, s);
+  if (run_direct && run_box)
+    launch_count_nonzero((const uint8_t* const*)(desc + kCountOff), (const int64_t*)(desc + kCountOff + 8),
+                         (int64_t*)(desc + kCountOff + 16), 1, s);
+  if (run_box) launch_sad_boxsum(djob, (const SadItem*)(desc + 256), n_items, r, s);
+  if (run_direct) launch_sad_direct(djob, 1, s);
   launch_sad_finalize(djob, 1, w, h, s);
   e = cudaGetLastError();
   if (e != cudaSuccess) {

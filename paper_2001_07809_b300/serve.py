@@ -10,6 +10,11 @@ fired.  Inputs, intermediate maps and results of admitted requests stay
 resident on the device until the batch completes; results are copied back to
 pinned host memory in the same stream.
 
+Pinned result buffers come from a per-shape free list that the scheduler
+fills; a client that is done with a result hands its buffers back with
+``Server.recycle`` so that steady-state serving pins no new host memory (a
+fresh pinned allocation costs milliseconds and holds the interpreter lock).
+
 The pipeline is deterministic per pair, so a request's result does not depend
 on what it was batched with.
 """
@@ -19,7 +24,7 @@ import collections
 import concurrent.futures as cf
 import threading
 import time
-from typing import List, Optional
+from typing import Dict, List, Tuple
 
 import torch
 
@@ -34,17 +39,15 @@ def request_bytes(h: int, w: int) -> int:
 
 
 class Request:
-    __slots__ = ("left", "right", "params", "future", "arrival", "done", "bytes", "out_rgb", "out_disp", "h", "w")
+    __slots__ = ("left", "right", "params", "future", "arrival", "bytes", "out_rgb", "out_disp", "h", "w")
 
     def __init__(self, left, right, params: sb_params):
         self.left, self.right, self.params = left, right, params
         self.h, self.w = int(left.shape[0]), int(left.shape[1])
         self.future: cf.Future = cf.Future()
         self.arrival = time.perf_counter()
-        self.done: Optional[float] = None
         self.bytes = request_bytes(self.h, self.w)
-        self.out_rgb = torch.empty((self.h, self.w, 3), dtype=torch.uint8, pin_memory=True)
-        self.out_disp = torch.empty((self.h, self.w), dtype=torch.int16, pin_memory=True)
+        self.out_rgb = self.out_disp = None
 
 
 class Server:
@@ -60,8 +63,10 @@ class Server:
         self.used = 0
         self.cv = threading.Condition()
         self.running = True
-        self.completed: List[Request] = []
+        self.completed: List[Tuple[float, float]] = []   # (arrival, done) per finished request
         self.batches = 0
+        self._free: Dict[Tuple[int, int], list] = collections.defaultdict(list)
+        self._free_lock = threading.Lock()
         self.thread = threading.Thread(target=self._loop, daemon=True)
         self.thread.start()
 
@@ -87,7 +92,22 @@ class Server:
             c.close()
 
     def latencies(self) -> List[float]:
-        return [r.done - r.arrival for r in self.completed]
+        return [d - a for a, d in self.completed]
+
+    def recycle(self, result):
+        """Return a result's (out_rgb, out_disp) host buffers for reuse; the
+        caller must not touch them afterwards."""
+        rgb, disp = result
+        with self._free_lock:
+            self._free[(int(rgb.shape[0]), int(rgb.shape[1]))].append((rgb, disp))
+
+    def _take_outputs(self, h: int, w: int):
+        with self._free_lock:
+            lst = self._free.get((h, w))
+            if lst:
+                return lst.pop()
+        return (torch.empty((h, w, 3), dtype=torch.uint8, pin_memory=True),
+                torch.empty((h, w), dtype=torch.int16, pin_memory=True))
 
     # ---------------------------------------------------------- scheduler side
     def _finish(self, i: int):
@@ -100,13 +120,13 @@ class Server:
         except Exception as e:  # a failed batch fails its requests, the server keeps going
             err = e
         for r in reqs:
-            r.done = now
             self.used -= r.bytes
+            self.completed.append((r.arrival, now))
             if err is None:
                 r.future.set_result((r.out_rgb, r.out_disp))
             else:
                 r.future.set_exception(err)
-            self.completed.append(r)
+            r.left = r.right = r.out_rgb = r.out_disp = None
 
     def _launch(self, i: int, reqs: List[Request]):
         s = self.streams[i]
@@ -114,6 +134,7 @@ class Server:
         pairs = []
         with torch.cuda.stream(s):
             for r in reqs:
+                r.out_rgb, r.out_disp = self._take_outputs(r.h, r.w)
                 dl = r.left.to(self.device, non_blocking=True)
                 dr = r.right.to(self.device, non_blocking=True)
                 do = torch.empty((r.h, r.w, 3), dtype=torch.uint8, device=self.device)

@@ -178,6 +178,41 @@ def test_sad_extreme_costs(ctx):
         assert np.all(oc[anchor] == 63 * 63 * 255) and np.all(od[anchor] == 0)
 
 
+@pytest.mark.parametrize("density,B", [(0.0, 9), (0.01, 3), (0.5, 25), (0.2, 41)])
+def test_sad_auto_choice_is_exact(ctx, density, B):
+    # the automatic choice is taken on the device from the map's own count;
+    # whichever kernel serves the map, the result is the oracle's
+    h, w, D = 90, 400, 48
+    Ll = RNG.integers(0, 256, (h, w)).astype(np.uint8)
+    Lr = np.clip(np.roll(Ll, -5, axis=1).astype(int) + RNG.integers(-4, 5, (h, w)), 0, 255).astype(np.uint8)
+    bmap = (RNG.random((h, w)) < density).astype(np.uint8)
+    disp, cost = sad(ctx, Ll, Lr, bmap, D, B, sb.SB_SAD_AUTO)
+    od, oc = oracle.boundary_sad(Ll, Lr, oracle.anchor_mask(bmap, D, B), D, B)
+    assert np.array_equal(disp, od) and np.array_equal(cost, oc)
+
+
+def test_batched_auto_mixes_variants_per_pair(ctx):
+    # a boundary-free pair (only the domain's edge columns are anchors: the
+    # direct kernel serves it) batched with textured pairs (box sums serve
+    # them): every pair equals its forced-variant result and the oracle
+    items = []
+    flat = np.full((96, 300, 3), 90, np.uint8)
+    items.append((flat, flat.copy(), synth.Params(k=4, max_disp=40, block=9, sigma=2.0, ranges=[(10, 20)])))
+    for i in range(2):
+        r = synth.Rng(700 + i)
+        sc = synth.Scene(320, 120, synth._c2_style_layers(r, 320, 120, 48, contrast=50), noise_q8=512,
+                         noise_seed=r.u64())
+        left, right, _ = sc.render(want_gt=False)
+        items.append((left, right, synth.Params(k=6, max_disp=48, block=(25, 9)[i], sigma=3.0, ranges=[(0, 16)])))
+    auto = run_pairs(ctx, items, sb.SB_RUN_BATCHED)
+    for variant in (sb.SB_SAD_BOXSUM, sb.SB_SAD_DIRECT):
+        forced = run_pairs(ctx, items, sb.SB_RUN_BATCHED, sad_variant=variant)
+        for (a_rgb, a_disp), (f_rgb, f_disp) in zip(auto, forced):
+            assert np.array_equal(a_rgb, f_rgb) and np.array_equal(a_disp, f_disp)
+    for (left, right, p), (o_rgb, o_disp) in zip(items, auto):
+        _compare_full(o_rgb, o_disp, left, right, p)
+
+
 # ------------------------------------------------------------ reconstruction
 @pytest.mark.parametrize("h,w,D,B,T", [(50, 80, 4, 3, 1), (130, 140, 10, 5, 0), (200, 333, 20, 9, 3),
                                        (257, 64, 0, 1, -1), (300, 50, 8, 7, 1000)])
