@@ -46,6 +46,7 @@ def needs_build() -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not needs_build():
+        build_peak()
         return LIB
     nvcc = _nvcc()
     os.makedirs(BUILD_DIR, exist_ok=True)
@@ -70,7 +71,26 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)
+    build_peak(force)
     return LIB
+
+
+PEAK_SRC = os.path.join(HERE, "peak", "int_peak.cu")
+PEAK_LIB = os.path.join(HERE, "peak", "libsb_peak.so")
+
+
+def build_peak(force: bool = False) -> str:
+    """The instruction-rate microbenchmark (peak/int_peak.cu -> peak/libsb_peak.so)."""
+    if not force and os.path.exists(PEAK_LIB) and os.path.getmtime(PEAK_LIB) >= os.path.getmtime(PEAK_SRC):
+        return PEAK_LIB
+    tmp = PEAK_LIB + ".tmp%d" % os.getpid()
+    cmd = [_nvcc()] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-cudart", "shared",
+                              PEAK_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for %s:\n%s%s" % (PEAK_SRC, r.stdout, r.stderr))
+    os.replace(tmp, PEAK_LIB)
+    return PEAK_LIB
 
 
 if __name__ == "__main__":

@@ -6,8 +6,9 @@
 // then a vertical pass.  Each thread produces 16 consecutive outputs per
 // pass, sliding a 16-value register window over the input so that every
 // shared-memory load feeds 16 FMAs (the tap is a warp-uniform broadcast);
-// taps are padded with zeros only to a multiple of 8.  The three channels
-// are staged together when the tile fits in shared memory.
+// exactly 2R+1 taps are applied (whole blocks of 16, then a predicated
+// tail).  The three channels are staged together, by 16-byte cp.async copies
+// of each input row's byte run, when the tile fits in shared memory.
 // Only pixels whose disparity lies in no range of interest take the blurred
 // value; the rest are copied, and a tile with no such pixel is copied as is.
 #include "sb_common.cuh"
@@ -20,8 +21,8 @@ constexpr int BY = 112;   // output rows per tile (a multiple of OB)
 constexpr int OB = 16;    // outputs per thread per pass (register window)
 constexpr int kBlurThreads = 256;
 constexpr int kAll3Limit = 110 * 1024;  // stage the three channels together up to this size (2 CTAs/SM)
+constexpr int HS = BX + 1;               // row stride of the horizontal results: conflict-light stores
 
-__host__ __device__ inline int rup8(int v) { return (v + 7) & ~7; }
 
 __device__ __forceinline__ bool in_focus(uint16_t d, const int* lo, const int* hi, int n) {
   for (int i = 0; i < n; ++i)
@@ -32,9 +33,33 @@ __device__ __forceinline__ bool in_focus(uint16_t d, const int* lo, const int* h
 // exact u8 -> float: 2^23 + b as a float, minus 2^23
 __device__ __forceinline__ float u8f(uint8_t b) { return __int_as_float(0x4B000000 | b) - 8388608.0f; }
 
-// acc[o] += sum_t tap[t] * x[o + t] for o < OB, t < nt (nt a multiple of 8),
-// where x(j) loads input j.  The window win holds x[t + (o..o+15)] rotated so
-// that every index is static: full blocks of 16 taps, then at most one half block.
+// One tap of the register-window convolution at rotation offset OFF + u:
+// win[(OFF + u + o) % OB] holds x[t + u + o]; afterwards the freed slot takes
+// x[t + u + OB].
+template <int OFF, int U, class LOAD>
+__device__ __forceinline__ void conv_tap(float (&acc)[OB], float (&win)[OB], float tp, int t, LOAD x) {
+#pragma unroll
+  for (int o = 0; o < OB; ++o) acc[o] = fmaf(tp, win[(OFF + U + o) % OB], acc[o]);
+  win[(OFF + U) % OB] = x(t + U + OB);
+}
+
+// at most 7 single taps t .. t+rem-1 at rotation offset OFF
+template <int OFF, class LOAD>
+__device__ __forceinline__ void conv_tail(float (&acc)[OB], float (&win)[OB], const float* tap, int t, int rem,
+                                          LOAD x) {
+  if (rem > 0) conv_tap<OFF, 0>(acc, win, tap[t], t, x);
+  if (rem > 1) conv_tap<OFF, 1>(acc, win, tap[t + 1], t, x);
+  if (rem > 2) conv_tap<OFF, 2>(acc, win, tap[t + 2], t, x);
+  if (rem > 3) conv_tap<OFF, 3>(acc, win, tap[t + 3], t, x);
+  if (rem > 4) conv_tap<OFF, 4>(acc, win, tap[t + 4], t, x);
+  if (rem > 5) conv_tap<OFF, 5>(acc, win, tap[t + 5], t, x);
+  if (rem > 6) conv_tap<OFF, 6>(acc, win, tap[t + 6], t, x);
+}
+
+// acc[o] = sum_{t < nt} tap[t] * x[o + t] for o < OB, where x(j) loads input
+// j (inputs up to index nt - 1 + OB are loaded; the last OB - 1 of them only
+// refill the window).  Whole blocks of 16 taps keep every window index static
+// by rotating the slots; the remainder is at most one half block and 7 taps.
 template <class LOAD>
 __device__ __forceinline__ void conv16(float (&acc)[OB], const float* tap, int nt, LOAD x) {
   float win[OB];
@@ -50,7 +75,8 @@ __device__ __forceinline__ void conv16(float (&acc)[OB], const float* tap, int n
       win[u] = x(t + u + OB);
     }
   }
-  if (t < nt) {  // half block of 8 taps
+  const int rem = nt - t;
+  if (rem >= 8) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const float tp = tap[t + u];
@@ -58,29 +84,48 @@ __device__ __forceinline__ void conv16(float (&acc)[OB], const float* tap, int n
       for (int o = 0; o < OB; ++o) acc[o] = fmaf(tp, win[(u + o) % OB], acc[o]);
       win[u] = x(t + u + OB);
     }
+    conv_tail<8>(acc, win, tap, t + 8, rem - 8, x);
+  } else {
+    conv_tail<0>(acc, win, tap, t, rem, x);
   }
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src));
+}
+
+struct BlurGeo {
+  int nt, ih, hrows, iw, sr, base, all3, bytes;
+};
+
+// Shared-memory layout for radius R: taps [nt] (16-byte padded), horizontal
+// results float [hrows = BY + 2R + 1][HS] (the last row is only read as a
+// window refill), the blur mask [BY][BX], then the input tile: three
+// interleaved channels, rows of sr bytes that start at a per-row offset of
+// 0..15 bytes (the cp.async source alignment), or one channel [ih][iw].
+__host__ __device__ inline BlurGeo blur_geo(int R) {
+  BlurGeo g;
+  g.nt = 2 * R + 1;
+  g.ih = BY + 2 * R;
+  g.hrows = g.ih + 1;
+  g.iw = BX + 2 * R + 1;
+  g.sr = ((g.iw * 3 + 15 + 15) / 16) * 16;
+  g.base = ((((g.nt + 3) & ~3) * 4 + g.hrows * HS * 4 + BY * BX) + 15) & ~15;
+  const int three = g.base + g.ih * g.sr;
+  g.all3 = three <= kAll3Limit;
+  g.bytes = g.all3 ? three : g.base + g.ih * g.iw;
+  return g;
 }
 }  // namespace
 
-// shared memory: taps (2R+1 padded with zeros to nt = a multiple of 8), the
-// horizontal results as float [(BY + nt)][BX], the tile's blur mask
-// [BY][BX], then the input tile as bytes [(BY + nt)][(BX + nt)] x (3 channels
-// interleaved, or 1 channel when three do not fit).
-__host__ __device__ int blur_smem_bytes(int R, int* all3) {
-  const int nt = rup8(2 * R + 1);
-  const int iw = BX + nt, ih = BY + nt;  // the windows read input indices up to nt + 15
-  const int base = (nt + ih * BX) * 4 + BY * BX + 16;
-  const int three = base + iw * ih * 3;
-  if (three <= kAll3Limit) { if (all3) *all3 = 1; return three; }
-  if (all3) *all3 = 0;
-  return base + iw * ih;
-}
-__host__ __device__ int blur_smem_bytes(int R) { return blur_smem_bytes(R, nullptr); }
+__host__ __device__ int blur_smem_bytes(int R) { return blur_geo(R).bytes; }
 
 __global__ void __launch_bounds__(kBlurThreads) k_blur(const BlurJob* __restrict__ jobs) {
   extern __shared__ __align__(16) float fsm[];
   __shared__ int s_any;
   __shared__ int s_lo[8], s_hi[8];
+  __shared__ uint8_t s_off[BY + 2 * 96];   // per input row: byte offset of its run (R <= 96)
   const BlurJob J = jobs[blockIdx.z];
   const int w = J.w, h = J.h, R = J.R;
   const int tx0 = blockIdx.x * BX, ty0 = blockIdx.y * BY;
@@ -88,20 +133,44 @@ __global__ void __launch_bounds__(kBlurThreads) k_blur(const BlurJob* __restrict
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ox = min(BX, w - tx0), oy = min(BY, h - ty0);
   const int nr = J.n_ranges;
-  int all3;
-  blur_smem_bytes(R, &all3);
-  const int nt = rup8(2 * R + 1);
-  const int iw = BX + nt, ih = BY + nt;
-  const int nch = all3 ? 3 : 1;
+  const BlurGeo G = blur_geo(R);
+  const int nt = G.nt, iw = G.iw, ih = G.ih, sr = G.sr;
+  const int nch = G.all3 ? 3 : 1;
   float* s_tap = fsm;
-  float* s_h = s_tap + nt;
-  uint8_t* s_mask = reinterpret_cast<uint8_t*>(s_h + ih * BX);
-  uint8_t* s_in = s_mask + BY * BX;
-  if (tid < 8) { s_lo[tid] = J.lo[tid]; s_hi[tid] = J.hi[tid]; }
+  float* s_h = fsm + ((nt + 3) & ~3);
+  uint8_t* s_mask = reinterpret_cast<uint8_t*>(s_h + G.hrows * HS);
+  uint8_t* s_in = reinterpret_cast<uint8_t*>(fsm) + G.base;
+  const int xs = tx0 - R;
+  const bool interior = xs >= 0 && xs + iw <= w;
+  const int64_t nbytes = (int64_t)w * h * 3;
+  const bool fast = interior && G.all3 && ((reinterpret_cast<uintptr_t>(J.rgb) & 15) == 0);
+  if (tid < 8) { s_lo[tid] = jobs[blockIdx.z].lo[tid]; s_hi[tid] = jobs[blockIdx.z].hi[tid]; }
   if (tid == 0) s_any = 0;
+  // three channels, interior tile: each input row is one run of iw*3 bytes,
+  // copied as the 16-byte chunks that cover it (issued before the mask so the
+  // copies overlap the mask loads)
+  if (fast) {
+    const int nchunk = (iw * 3 + 15 + 15) / 16;
+    for (int i = warp; i < ih; i += kBlurThreads / 32) {
+      const int y = min(max(ty0 - R + i, 0), h - 1);
+      const int64_t s0 = ((int64_t)y * w + xs) * 3, a16 = s0 & ~(int64_t)15;
+      if (lane == 0) s_off[i] = (uint8_t)(s0 - a16);
+      uint8_t* dst = s_in + i * sr;
+      for (int c = lane; c < nchunk; c += 32) {
+        const int64_t src = a16 + 16 * c;
+        if (src + 16 <= nbytes) {
+          cp_async16(dst + 16 * c, J.rgb + src);
+        } else {
+          for (int k = 0; k < 16; ++k) dst[16 * c + k] = J.rgb[min(src + k, nbytes - 1)];
+        }
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  }
   __syncthreads();
   // blur mask of the tile (1 = blurred: the disparity is in no range of interest)
   int any = 0;
+#pragma unroll 7
   for (int t = tid; t < BY * BX; t += kBlurThreads) {
     const int i = t / BX, j = t % BX;  // BX is a power of two
     uint8_t m = 0;
@@ -110,54 +179,56 @@ __global__ void __launch_bounds__(kBlurThreads) k_blur(const BlurJob* __restrict
     any |= m;
   }
   if (any) s_any = 1;
+  if (fast) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
-  if (!s_any) {
+  if (!s_any) {  // nothing to blur: copy the tile (from the staged rows when there are any)
     for (int i = warp; i < oy; i += kBlurThreads / 32) {
       const int64_t row = ((int64_t)(ty0 + i) * w + tx0) * 3;
-      for (int b = lane; b < ox * 3; b += 32) J.out[row + b] = J.rgb[row + b];
+      if (fast) {
+        const uint8_t* src = s_in + (i + R) * sr + s_off[i + R] + R * 3;
+        for (int b = lane; b < ox * 3; b += 32) J.out[row + b] = src[b];
+      } else {
+        for (int b = lane; b < ox * 3; b += 32) J.out[row + b] = J.rgb[row + b];
+      }
     }
     return;
   }
-  for (int t = tid; t < nt; t += kBlurThreads) s_tap[t] = t <= 2 * R ? J.taps[t] : 0.0f;
-  // stage channels c0 .. c0+nch-1 of the input tile (edges replicated): rows that
-  // lie inside the image columns are one contiguous run of bytes
+  for (int t = tid; t < nt; t += kBlurThreads) s_tap[t] = J.taps[t];
+  // byte-wise staging (edge tiles, unaligned images, or one channel at a
+  // time): channels c0 .. c0+nch-1, edges replicated, row offset 0
   auto stage = [&](int c0) {
+    const int stride = nch == 3 ? sr : iw;
     for (int i = warp; i < ih; i += kBlurThreads / 32) {
       const int y = min(max(ty0 - R + i, 0), h - 1);
-      const int xs = tx0 - R;
-      uint8_t* dst = s_in + i * iw * nch;
+      uint8_t* dst = s_in + i * stride;
       const uint8_t* src_row = J.rgb + (int64_t)y * w * 3;
-      if (nch == 3 && xs >= 0 && xs + iw <= w) {
-        const uint8_t* src = src_row + (int64_t)xs * 3;
-        for (int b = lane; b < iw * 3; b += 32) dst[b] = src[b];
-      } else {
-        for (int b = lane; b < iw * nch; b += 32) {
-          const int j = nch == 3 ? b / 3 : b, c = nch == 3 ? b - 3 * j : 0;
-          const int x = min(max(xs + j, 0), w - 1);
-          dst[b] = src_row[x * 3 + c0 + c];
-        }
+      if (lane == 0) s_off[i] = 0;
+      for (int b = lane; b < iw * nch; b += 32) {
+        const int j = nch == 3 ? b / 3 : b, c = nch == 3 ? b - 3 * j : 0;
+        const int x = min(max(xs + j, 0), w - 1);
+        dst[b] = src_row[x * 3 + c0 + c];
       }
     }
   };
-  if (all3) stage(0);
+  if (G.all3 && !fast) stage(0);
+  const int stride = nch == 3 ? sr : iw;
   for (int ch = 0; ch < 3; ++ch) {
-    const int c = all3 ? ch : 0;
-    if (!all3) {
+    const int c = G.all3 ? ch : 0;
+    if (!G.all3) {
       __syncthreads();
       stage(ch);
     }
     __syncthreads();
-    // horizontal pass: rows 0 .. BY+nt-1, 16 outputs per task
+    // horizontal pass: input rows 0 .. BY+2R-1, 16 outputs per task
     {
       const int tasks_per_row = BX / OB;
-      const int rows = BY + nt;
-      for (int task = tid; task < rows * tasks_per_row; task += kBlurThreads) {
+      for (int task = tid; task < ih * tasks_per_row; task += kBlurThreads) {
         const int i = task / tasks_per_row, j0 = (task % tasks_per_row) * OB;
-        const uint8_t* in = s_in + ((i * iw) + j0) * nch + c;  // output j0+o uses in[o .. o+2R]
+        const uint8_t* in = s_in + i * stride + s_off[i] + j0 * nch + c;  // output j0+o uses in[o .. o+2R]
         float acc[OB];
-        conv16(acc, s_tap, nt, [&](int j) { return u8f(in[j * nch]); });
+        conv16(acc, s_tap, nt, [in, nch](int j) { return u8f(in[j * nch]); });
 #pragma unroll
-        for (int o = 0; o < OB; ++o) s_h[i * BX + j0 + o] = acc[o];
+        for (int o = 0; o < OB; ++o) s_h[i * HS + j0 + o] = acc[o];
       }
     }
     __syncthreads();
@@ -166,9 +237,9 @@ __global__ void __launch_bounds__(kBlurThreads) k_blur(const BlurJob* __restrict
       const int tasks = BX * (BY / OB);
       for (int task = tid; task < tasks; task += kBlurThreads) {
         const int col = task % BX, i0 = (task / BX) * OB;
-        const float* hc = s_h + i0 * BX + col;  // output row i0+o uses hc rows o .. o+2R
+        const float* hc = s_h + i0 * HS + col;  // output row i0+o uses hc rows o .. o+2R
         float acc[OB];
-        conv16(acc, s_tap, nt, [&](int j) { return hc[j * BX]; });
+        conv16(acc, s_tap, nt, [hc](int j) { return hc[j * HS]; });
         if (col < ox) {
 #pragma unroll
           for (int o = 0; o < OB; ++o) {
@@ -179,7 +250,7 @@ __global__ void __launch_bounds__(kBlurThreads) k_blur(const BlurJob* __restrict
                 const int q = __float2int_rd(acc[o] + 0.5f);
                 v = (uint8_t)min(max(q, 0), 255);
               } else {
-                v = s_in[((i + R) * iw + col + R) * nch + c];  // the original pixel
+                v = s_in[(i + R) * stride + s_off[i + R] + (col + R) * nch + c];  // the original pixel
               }
               J.out[((int64_t)(ty0 + i) * w + tx0 + col) * 3 + ch] = v;
             }

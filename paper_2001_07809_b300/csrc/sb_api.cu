@@ -341,17 +341,11 @@ bool params_ok(sb_context* ctx, int w, int h, const sb_params& p, sb_status* st)
 }
 
 // --------------------------------------------------------------- tuner
-// Box sums cost about kBoxNsPerPxD per (domain pixel, disparity); direct
-// window sums about kDirectNsPerCell per (anchor, disparity, window cell).
-// With N_b boundary pixels in the image, the direct variant is the cheaper
-// one iff N_b |Omega|/(w h) B^2 c_direct < |Omega| c_box, i.e. N_b below
-// w h c_box / (B^2 c_direct).  The count is only known on the device once
-// the boundary map exists, so the host passes that limit with each job and
+// The direct kernel pays off only when N_b B^2 is small against |Omega| (the
+// cost model is sad_direct_limit).  The count N_b exists only on the device
+// once the boundary map does, so the host passes the limit with each job and
 // the kernels compare it with the pair's own count (no read-back, and a
 // replayed graph re-decides for every new frame).
-constexpr double kBoxNsPerPxD = 0.0012;
-constexpr double kDirectNsPerCell = 0.00009;
-
 // (nb, nb_direct_max) of a job; *direct_possible / *box_possible say which
 // kernels may serve it.
 void sad_choice(const Geo& g, const int64_t* nb, SadJob* j, bool* direct_possible, bool* box_possible) {
@@ -363,9 +357,7 @@ void sad_choice(const Geo& g, const int64_t* nb, SadJob* j, bool* direct_possibl
     *box_possible = !dir;
     return;
   }
-  const double B = g.p.block;
-  const double lim = (double)g.w * g.h * kBoxNsPerPxD / (B * B * kDirectNsPerCell);
-  const int64_t m = (int64_t)std::ceil(lim) - 1;   // N_b <= m  <=>  N_b < lim
+  const int64_t m = sad_direct_limit(g.w, g.h, g.p.max_disp, g.p.block);
   j->nb = m >= 0 ? nb : nullptr;
   j->nb_direct_max = m;
   *direct_possible = m >= 0;

@@ -8,6 +8,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cmath>
 #include <stdint.h>
 
 #define SB_UNDET16 0xFFFFu
@@ -95,6 +96,25 @@ struct SadJob {
 
 __device__ __forceinline__ bool sad_use_direct(const SadJob& J) {
   return J.nb ? (*J.nb <= J.nb_direct_max) : (J.nb_direct_max >= 0);
+}
+
+// Cost model of the automatic SAD choice.  The direct kernel spends about
+// 1/kDirectVsBox box-sum (domain pixel, disparity) steps per (anchor,
+// disparity, window cell), disparities rounded up to whole 32-lane chunks
+// (fitted on B300 timings of both kernels over 65 pairs of mixed size,
+// disparity range, block and density).  Anchors are estimated from the
+// boundary count N_b of the whole image as N_b |Omega| / (w h) plus the two
+// domain-edge columns.  Returns the largest N_b for which the direct kernel
+// is the cheaper one, or -1 when it never is.
+constexpr double kDirectVsBox = 0.3;
+inline int64_t sad_direct_limit(int w, int h, int D, int B) {
+  const int r = (B - 1) / 2;
+  const double omega = (double)(w - D - 2 * r) * (double)(h - 2 * r);
+  const double chunks = 32.0 * ((D + 32) / 32);
+  const double anchors = kDirectVsBox * omega * (D + 1) / (chunks * (double)B * B) - 2.0 * (h - 2 * r);
+  if (!(anchors > 0.0)) return -1;
+  const double lim = anchors * (double)w * h / omega;   // N_b < lim
+  return (int64_t)std::ceil(lim) - 1;
 }
 // Box-sum variant: items = (job, column strip, disparity chunk, row band)
 struct SadItem {

@@ -104,8 +104,7 @@ extern "C" sb_status sb_boundary_sad_static(const uint8_t* L_left, const uint8_t
   SadJob job{L_left, L_right, boundary, key, disp, cost, w, h, max_disp, r, nullptr, -1};
   bool run_direct = variant == SB_SAD_DIRECT, run_box = variant == SB_SAD_BOXSUM;
   if (variant == SB_SAD_AUTO) {   // same cost model as the context path, decided from the map's own count
-    const double lim = (double)w * h * 0.0012 / ((double)block * block * 0.00009);
-    job.nb_direct_max = (int64_t)std::ceil(lim) - 1;
+    job.nb_direct_max = sad_direct_limit(w, h, max_disp, block);
     job.nb = job.nb_direct_max >= 0 ? (const int64_t*)(desc + kCountOff + 16) : nullptr;
     run_direct = job.nb_direct_max >= 0;
     run_box = true;

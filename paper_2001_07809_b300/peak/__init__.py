@@ -1,0 +1,26 @@
+"""Measured instruction rates of the current GPU (see int_peak.cu).
+
+``measure()`` returns thread-instructions per second for add.u32,
+vabsdiff4 (four byte cells each), fma.f32 and prmt, measured with CUDA
+events over a full grid.  Used by bench.py beside the derived peaks."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB = os.path.join(HERE, "libsb_peak.so")
+
+
+def measure() -> dict:
+    if not os.path.exists(LIB):
+        raise RuntimeError("libsb_peak.so is not built: run paper_2001_07809_b300.build.build()")
+    lib = ctypes.CDLL(LIB)
+    lib.sb_peak_measure.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    lib.sb_peak_measure.restype = ctypes.c_int
+    rates = (ctypes.c_double * 4)()
+    if lib.sb_peak_measure(rates) != 0:
+        raise RuntimeError("sb_peak_measure failed")
+    return {"iadd_tops": rates[0] / 1e12, "vabsdiff4_tinstr_s": rates[1] / 1e12,
+            "vabsdiff4_tcell_s": 4 * rates[1] / 1e12, "ffma_tflops": 2 * rates[2] / 1e12,
+            "prmt_tinstr_s": rates[3] / 1e12}

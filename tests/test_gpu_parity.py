@@ -178,7 +178,7 @@ def test_sad_extreme_costs(ctx):
         assert np.all(oc[anchor] == 63 * 63 * 255) and np.all(od[anchor] == 0)
 
 
-@pytest.mark.parametrize("density,B", [(0.0, 9), (0.01, 3), (0.5, 25), (0.2, 41)])
+@pytest.mark.parametrize("density,B", [(0.0, 1), (0.0, 9), (0.01, 3), (0.03, 3), (0.5, 25), (0.2, 41)])
 def test_sad_auto_choice_is_exact(ctx, density, B):
     # the automatic choice is taken on the device from the map's own count;
     # whichever kernel serves the map, the result is the oracle's
@@ -197,7 +197,7 @@ def test_batched_auto_mixes_variants_per_pair(ctx):
     # them): every pair equals its forced-variant result and the oracle
     items = []
     flat = np.full((96, 300, 3), 90, np.uint8)
-    items.append((flat, flat.copy(), synth.Params(k=4, max_disp=40, block=9, sigma=2.0, ranges=[(10, 20)])))
+    items.append((flat, flat.copy(), synth.Params(k=4, max_disp=40, block=3, sigma=2.0, ranges=[(10, 20)])))
     for i in range(2):
         r = synth.Rng(700 + i)
         sc = synth.Scene(320, 120, synth._c2_style_layers(r, 320, 120, 48, contrast=50), noise_q8=512,
@@ -254,6 +254,25 @@ def test_blur_within_one_level(ctx, sigma):
     assert diff.max() <= 1
     keep = ((disp >= 10) & (disp <= 20)) | ((disp >= 30) & (disp <= 31))
     assert np.array_equal(out[keep], rgb[keep])
+
+
+@pytest.mark.parametrize("sigma", [2.0, 8.0, 8.6, 9.0])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_blur_interior_tiles(ctx, sigma, offset):
+    # wide enough for tiles whose input run lies inside the image (staged with
+    # 16-byte copies at per-row offsets: 3*517 bytes per row is not a multiple
+    # of 16); offset 1 makes the RGB base unaligned, which takes the byte path
+    h, w = 150, 517
+    rgb = RNG.integers(0, 256, (h, w, 3)).astype(np.uint8)
+    disp = RNG.integers(0, 40, (h, w)).astype(np.uint16)
+    ranges = [(10, 20)]
+    buf = torch.empty(h * w * 3 + 16, dtype=torch.uint8, device="cuda")
+    d_rgb = buf[offset:offset + h * w * 3].view(h, w, 3)
+    d_rgb.copy_(torch.from_numpy(rgb))
+    out = torch.empty((h, w, 3), dtype=torch.uint8, device="cuda")
+    sb.sb_selective_blur(ctx, d_rgb, dev(disp), ranges, sigma, out)
+    want = oracle.selective_blur(rgb, disp, ranges, sigma)
+    assert np.abs(host(out).astype(int) - want.astype(int)).max() <= 1
 
 
 def test_blur_constant_image_unchanged(ctx):
