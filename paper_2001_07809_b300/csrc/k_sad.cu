@@ -70,196 +70,207 @@ __device__ __forceinline__ void stage_chunk(uint8_t* dst, const uint8_t* img, in
 
 __host__ __device__ int sad_boxsum_strip(int r) { return (kVsCols - 1 - 2 * r) & ~15; }
 
+// Persistent: each CTA takes the next work item from the queue counter (zero
+// before the launch) until the list is exhausted; items come in the order of
+// the list, which the host sorts largest first.
 __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __restrict__ jobs,
-                                                            const SadItem* __restrict__ items) {
+                                                            const SadItem* __restrict__ items, int n_items,
+                                                            unsigned* __restrict__ queue) {
   extern __shared__ __align__(16) uint8_t smem[];
-  const SadItem it = items[blockIdx.x];
-  const SadJob J = jobs[it.job];
-  if (sad_use_direct(J)) return;                          // the direct kernel serves this pair
-  const int r = J.r, D = J.D, w = J.w;
-  const int64_t npx = (int64_t)w * J.h;
-  const int ring = 2 * r + 1 + 2 * kGroup;                // + one group staged ahead
-  uint8_t* s_ring = smem;                                 // ring rows: [L | R]
-  uint8_t* s_zero = s_ring + ring * kRowBytes;            // zero row (warm-up leaving rows)
-  uint8_t* s_bm = s_zero + kRowBytes;                     // 2 x kGroup boundary-map rows
-  uint8_t* s_vs = s_bm + 2 * kGroup * kBBytes;            // kGroup x kVsCols x kVsStride
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int TX = sad_boxsum_strip(r);
-  const int NC = TX + 2 * r;
-  const int x0 = it.x0, d0 = it.d0;
-  const int xo0 = D + r, xo1 = w - 1 - r;                 // Omega columns
-  const int cstart = x0 - r;                              // strip column 0
-  const int rstart = cstart - d0 - 31;                    // first R byte any thread needs
-  const int y_first = it.y0, y_last = it.y1;              // output rows of the band
-  const bool fast = (((uintptr_t)J.Ll | (uintptr_t)J.Lr | (uintptr_t)J.bmap) & 15) == 0;
-  const int nchL = (15 + NC + 15) / 16, nchR = (15 + NC + 31 + 4 + 15) / 16, nchB = (15 + TX + 15) / 16;
-
-  for (int i = tid; i < kRowBytes / 4; i += kThreads) reinterpret_cast<uint32_t*>(s_zero)[i] = 0u;
-  for (int i = tid; i < kGroup * (kVsStride / 4); i += kThreads)   // column 0 of every row slot is zero
-    reinterpret_cast<uint32_t*>(s_vs + (i / (kVsStride / 4)) * kVsCols * kVsStride)[i % (kVsStride / 4)] = 0u;
-
-  // stage the entering rows of the group starting at virtual output row yg, and
-  // the boundary-map rows of its real output rows, into buffer `buf`; thread
-  // tid copies chunk (tid & 63) of ring row (tid >> 6) and chunk (tid & 15) of
-  // boundary row (tid >> 4): at most 35 chunks per ring row, 16 per map row
-  const int per = nchL + nchR;
-  auto stage = [&](int yg, int slot_first, int buf) {
-    const int ng = min(kGroup, y_last - yg + 1);
-    {
-      const int k = tid >> 6, ch = tid & 63;
-      if (k < ng && ch < per) {
-        const int yin = yg + k + r;
-        const int sl = slot_first + k < ring ? slot_first + k : slot_first + k - ring;
-        uint8_t* row = s_ring + sl * kRowBytes;
-        const int64_t ro = (int64_t)yin * w;
-        if (ch < nchL) stage_chunk(row, J.Ll, npx, (ro + cstart) & ~(int64_t)15, ch, fast);
-        else stage_chunk(row + kLBytes, J.Lr, npx, (ro + rstart) & ~(int64_t)15, ch - nchL, fast);
-      }
-    }
-    {
-      const int k = tid >> 4, ch = tid & 15;
-      const int y = yg + k;
-      if (k < ng && ch < nchB && y >= y_first)
-        stage_chunk(s_bm + (buf * kGroup + k) * kBBytes, J.bmap, npx, ((int64_t)y * w + x0) & ~(int64_t)15, ch, fast);
-    }
-    cp_async_commit();
-  };
-
-  // Stage A state: 32 vertical window sums as 16 packed u16 pairs.  For word g,
-  // Ve[g] holds disparities (d0+31-4g | d0+29-4g) and Vo[g] (d0+30-4g | d0+28-4g).
-  uint32_t Ve[8], Vo[8];
-#pragma unroll
-  for (int g = 0; g < 8; ++g) Ve[g] = Vo[g] = 0u;
-
-  // Stage B: where lane (disparity d0 + lane) finds its u16 in a column
-  int lanepos;
-  {
-    const int u = 31 - lane, g = u >> 2, b = u & 3;
-    lanepos = 4 * g + 2 * (b & 1) + (b >> 1);
-  }
-
-  // ring slot and 16-byte alignment offsets of the first entering row of the
-  // current group, advanced incrementally (no division in the row loop).  The
-  // leaving row y - r - 1 is 2r + 1 rows before the entering row y + r, which
-  // is 2*kGroup slots ahead in the ring.
-  const int wm = w & 15, back = ((2 * r + 1) * w) & 15;
-  int slot = (y_first - r) % ring;                            // entering row of the first group
-  int offL = (int)(((int64_t)(y_first - r) * w + cstart) & 15);
-  int offR = (int)(((int64_t)(y_first - r) * w + rstart) & 15);
-  int k_iter = 0;
-  stage(y_first - 2 * r, slot, 0);
-  // virtual output rows run from y_first - 2r (warm-up) to y_last
-  for (int yg = y_first - 2 * r; yg <= y_last; yg += kGroup, ++k_iter) {
-    const int ng = min(kGroup, y_last - yg + 1);
-    const int buf = k_iter & 1;
-    cp_async_wait_all();
-    __syncthreads();  // this group's rows have landed; the previous Stage B is done
-    const int slot_next = slot + kGroup < ring ? slot + kGroup : slot + kGroup - ring;
-    if (yg + kGroup <= y_last) stage(yg + kGroup, slot_next, buf ^ 1);
-    // Stage A: ng row steps
-    if (tid < NC) {
-      int sin = slot, offLi = offL, offRi = offR;
-#pragma unroll 1
-      for (int k = 0; k < ng; ++k) {
-        const int y = yg + k;
-        const bool real_out = y - r - 1 >= y_first - r;
-        int sout = sin + 2 * kGroup;
-        if (sout >= ring) sout -= ring;
-        const uint8_t* rin = s_ring + sin * kRowBytes;
-        const uint8_t* rout = real_out ? s_ring + sout * kRowBytes : s_zero;
-        const int offLo = real_out ? ((offLi - back) & 15) : 0, offRo = real_out ? ((offRi - back) & 15) : 0;
-        const uint32_t Lin = (uint32_t)rin[offLi + tid] * 0x01010101u;
-        const uint32_t Lout = (uint32_t)rout[offLo + tid] * 0x01010101u;
-        const int ji = tid + offRi, jo = tid + offRo;
-        const uint32_t* Ri = reinterpret_cast<const uint32_t*>(rin + kLBytes) + (ji >> 2);
-        const uint32_t* Ro = reinterpret_cast<const uint32_t*>(rout + kLBytes) + (jo >> 2);
-        const int shi = (ji & 3) * 8, sho = (jo & 3) * 8;
-        uint32_t wi = Ri[0], wo = Ro[0];
-#pragma unroll
-        for (int g = 0; g < 8; ++g) {
-          const uint32_t wi2 = Ri[g + 1], wo2 = Ro[g + 1];
-          const uint32_t ri = __funnelshift_r(wi, wi2, shi), ro = __funnelshift_r(wo, wo2, sho);
-          wi = wi2;
-          wo = wo2;
-          // byte b of ri/ro is disparity d0 + 31 - 4g - b
-          const uint32_t ai = __vabsdiffu4(Lin, ri), ao = __vabsdiffu4(Lout, ro);
-          // lane-wise u16 updates: sums stay in [0, 63*255], so no carry or
-          // borrow crosses the 16-bit lanes
-          Ve[g] = Ve[g] + (ai & 0x00FF00FFu) - (ao & 0x00FF00FFu);
-          Vo[g] = Vo[g] + __byte_perm(ai, 0u, 0x4341) - __byte_perm(ao, 0u, 0x4341);
-        }
-        if (y >= y_first) {
-          uint4* dst = reinterpret_cast<uint4*>(s_vs + (k * kVsCols + tid + 1) * kVsStride);
-#pragma unroll
-          for (int m = 0; m < 4; ++m) dst[m] = make_uint4(Ve[2 * m], Vo[2 * m], Ve[2 * m + 1], Vo[2 * m + 1]);
-        }
-        sin = sin + 1 < ring ? sin + 1 : 0;
-        offLi = (offLi + wm) & 15;
-        offRi = (offRi + wm) & 15;
-      }
-    }
-    slot = slot_next;
-    offL = (offL + kGroup * wm) & 15;
-    offR = (offR + kGroup * wm) & 15;
-    if (yg + ng - 1 < y_first) continue;  // still warming up
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();  // every thread is done with the previous item (and has read s_item)
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);
     __syncthreads();
-    // Stage B: warp -> (row slot, half strip); lane -> disparity.  The warp
-    // slides the horizontal window along its half strip, 8 outputs per block.
+    if (s_item >= n_items) break;
+    const SadItem it = items[s_item];
+    const SadJob J = jobs[it.job];
+    if (sad_use_direct(J)) continue;                        // the direct kernel serves this pair
+    const int r = J.r, D = J.D, w = J.w;
+    const int64_t npx = (int64_t)w * J.h;
+    const int ring = 2 * r + 1 + 2 * kGroup;                // + one group staged ahead
+    uint8_t* s_ring = smem;                                 // ring rows: [L | R]
+    uint8_t* s_zero = s_ring + ring * kRowBytes;            // zero row (warm-up leaving rows)
+    uint8_t* s_bm = s_zero + kRowBytes;                     // 2 x kGroup boundary-map rows
+    uint8_t* s_vs = s_bm + 2 * kGroup * kBBytes;            // kGroup x kVsCols x kVsStride
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int TX = sad_boxsum_strip(r);
+    const int NC = TX + 2 * r;
+    const int x0 = it.x0, d0 = it.d0;
+    const int xo0 = D + r, xo1 = w - 1 - r;                 // Omega columns
+    const int cstart = x0 - r;                              // strip column 0
+    const int rstart = cstart - d0 - 31;                    // first R byte any thread needs
+    const int y_first = it.y0, y_last = it.y1;              // output rows of the band
+    const bool fast = (((uintptr_t)J.Ll | (uintptr_t)J.Lr | (uintptr_t)J.bmap) & 15) == 0;
+    const int nchL = (15 + NC + 15) / 16, nchR = (15 + NC + 31 + 4 + 15) / 16, nchB = (15 + TX + 15) / 16;
+
+    for (int i = tid; i < kRowBytes / 4; i += kThreads) reinterpret_cast<uint32_t*>(s_zero)[i] = 0u;
+    for (int i = tid; i < kGroup * (kVsStride / 4); i += kThreads)   // column 0 of every row slot is zero
+      reinterpret_cast<uint32_t*>(s_vs + (i / (kVsStride / 4)) * kVsCols * kVsStride)[i % (kVsStride / 4)] = 0u;
+
+    // stage the entering rows of the group starting at virtual output row yg, and
+    // the boundary-map rows of its real output rows, into buffer `buf`; thread
+    // tid copies chunk (tid & 63) of ring row (tid >> 6) and chunk (tid & 15) of
+    // boundary row (tid >> 4): at most 35 chunks per ring row, 16 per map row
+    const int per = nchL + nchR;
+    auto stage = [&](int yg, int slot_first, int buf) {
+      const int ng = min(kGroup, y_last - yg + 1);
+      {
+        const int k = tid >> 6, ch = tid & 63;
+        if (k < ng && ch < per) {
+          const int yin = yg + k + r;
+          const int sl = slot_first + k < ring ? slot_first + k : slot_first + k - ring;
+          uint8_t* row = s_ring + sl * kRowBytes;
+          const int64_t ro = (int64_t)yin * w;
+          if (ch < nchL) stage_chunk(row, J.Ll, npx, (ro + cstart) & ~(int64_t)15, ch, fast);
+          else stage_chunk(row + kLBytes, J.Lr, npx, (ro + rstart) & ~(int64_t)15, ch - nchL, fast);
+        }
+      }
+      {
+        const int k = tid >> 4, ch = tid & 15;
+        const int y = yg + k;
+        if (k < ng && ch < nchB && y >= y_first)
+          stage_chunk(s_bm + (buf * kGroup + k) * kBBytes, J.bmap, npx, ((int64_t)y * w + x0) & ~(int64_t)15, ch, fast);
+      }
+      cp_async_commit();
+    };
+
+    // Stage A state: 32 vertical window sums as 16 packed u16 pairs.  For word g,
+    // Ve[g] holds disparities (d0+31-4g | d0+29-4g) and Vo[g] (d0+30-4g | d0+28-4g).
+    uint32_t Ve[8], Vo[8];
+  #pragma unroll
+    for (int g = 0; g < 8; ++g) Ve[g] = Vo[g] = 0u;
+
+    // Stage B: where lane (disparity d0 + lane) finds its u16 in a column
+    int lanepos;
     {
-      const int g = warp >> 1, half = warp & 1;
-      const int y = yg + g;
-      if (g < ng && y >= y_first) {
-        const int HW = TX / 2;
-        const int xa = half * HW, xb = min(half * HW + HW, TX);
-        const int d = d0 + lane;
-        const uint32_t dbits = d <= D ? (uint32_t)d : 0xFFFFFFFFu;  // invalid lanes never win
-        const uint16_t* vcol = reinterpret_cast<const uint16_t*>(s_vs + g * kVsCols * kVsStride) + lanepos;
-        constexpr int CS = kVsStride / 2;                              // u16 per column
-        const uint8_t* bm = s_bm + (buf * kGroup + g) * kBBytes + (int)(((int64_t)y * w + x0) & 15);
-        uint32_t* krow = J.key + (int64_t)y * w + x0;
-        auto anchor = [&](int xi) -> bool {  // strip-relative output column
-          const int xl = x0 + xi;
-          return xi < xb && xl >= xo0 && xl <= xo1 && (xl == xo0 || xl == xo1 || bm[xi]);
-        };
-        auto emit = [&](uint32_t S, int xi) {
-          const uint32_t key = dbits == 0xFFFFFFFFu ? 0xFFFFFFFFu : ((S << SB_KEY_DBITS) | dbits);
-          const uint32_t kmin = __reduce_min_sync(0xffffffffu, key);
-          if (lane == 0) atomicMin(&krow[xi], kmin);
-        };
-        // S starts as the window of output xa - 1 (column xa - 1 + j, shifted by
-        // the zero column: slot column xa + j), then every output adds its
-        // entering column and drops its leaving one; HW is a multiple of 8.
-        uint32_t S = 0;
-        for (int j = 0; j <= 2 * r; ++j) S += vcol[(xa + j) * CS];
-        for (int xbase = xa; xbase < xb; xbase += 32) {
-          const unsigned mask = __ballot_sync(0xffffffffu, anchor(xbase + lane));
-          const int n = min(32, xb - xbase);
-          const uint16_t* pin = vcol + (xbase + 2 * r + 1) * CS;  // slot column of strip column x + 2r
-          const uint16_t* pout = vcol + xbase * CS;             // slot column of x - 1
-#pragma unroll 1
-          for (int i = 0; i < n; i += 8) {
-            uint32_t Sv[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              S += (uint32_t)pin[(i + k) * CS] - (uint32_t)pout[(i + k) * CS];
-              Sv[k] = S;
-            }
-            const unsigned bits = (mask >> i) & 0xFFu;
-            if (bits & 0x0Fu) {
-#pragma unroll
-              for (int k = 0; k < 4; ++k)
-                if (bits & (1u << k)) emit(Sv[k], xbase + i + k);
-            }
-            if (bits & 0xF0u) {
-#pragma unroll
-              for (int k = 4; k < 8; ++k)
-                if (bits & (1u << k)) emit(Sv[k], xbase + i + k);
+      const int u = 31 - lane, g = u >> 2, b = u & 3;
+      lanepos = 4 * g + 2 * (b & 1) + (b >> 1);
+    }
+
+    // ring slot and 16-byte alignment offsets of the first entering row of the
+    // current group, advanced incrementally (no division in the row loop).  The
+    // leaving row y - r - 1 is 2r + 1 rows before the entering row y + r, which
+    // is 2*kGroup slots ahead in the ring.
+    const int wm = w & 15, back = ((2 * r + 1) * w) & 15;
+    int slot = (y_first - r) % ring;                            // entering row of the first group
+    int offL = (int)(((int64_t)(y_first - r) * w + cstart) & 15);
+    int offR = (int)(((int64_t)(y_first - r) * w + rstart) & 15);
+    int k_iter = 0;
+    stage(y_first - 2 * r, slot, 0);
+    // virtual output rows run from y_first - 2r (warm-up) to y_last
+    for (int yg = y_first - 2 * r; yg <= y_last; yg += kGroup, ++k_iter) {
+      const int ng = min(kGroup, y_last - yg + 1);
+      const int buf = k_iter & 1;
+      cp_async_wait_all();
+      __syncthreads();  // this group's rows have landed; the previous Stage B is done
+      const int slot_next = slot + kGroup < ring ? slot + kGroup : slot + kGroup - ring;
+      if (yg + kGroup <= y_last) stage(yg + kGroup, slot_next, buf ^ 1);
+      // Stage A: ng row steps
+      if (tid < NC) {
+        int sin = slot, offLi = offL, offRi = offR;
+  #pragma unroll 1
+        for (int k = 0; k < ng; ++k) {
+          const int y = yg + k;
+          const bool real_out = y - r - 1 >= y_first - r;
+          int sout = sin + 2 * kGroup;
+          if (sout >= ring) sout -= ring;
+          const uint8_t* rin = s_ring + sin * kRowBytes;
+          const uint8_t* rout = real_out ? s_ring + sout * kRowBytes : s_zero;
+          const int offLo = real_out ? ((offLi - back) & 15) : 0, offRo = real_out ? ((offRi - back) & 15) : 0;
+          const uint32_t Lin = (uint32_t)rin[offLi + tid] * 0x01010101u;
+          const uint32_t Lout = (uint32_t)rout[offLo + tid] * 0x01010101u;
+          const int ji = tid + offRi, jo = tid + offRo;
+          const uint32_t* Ri = reinterpret_cast<const uint32_t*>(rin + kLBytes) + (ji >> 2);
+          const uint32_t* Ro = reinterpret_cast<const uint32_t*>(rout + kLBytes) + (jo >> 2);
+          const int shi = (ji & 3) * 8, sho = (jo & 3) * 8;
+          uint32_t wi = Ri[0], wo = Ro[0];
+  #pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            const uint32_t wi2 = Ri[g + 1], wo2 = Ro[g + 1];
+            const uint32_t ri = __funnelshift_r(wi, wi2, shi), ro = __funnelshift_r(wo, wo2, sho);
+            wi = wi2;
+            wo = wo2;
+            // byte b of ri/ro is disparity d0 + 31 - 4g - b
+            const uint32_t ai = __vabsdiffu4(Lin, ri), ao = __vabsdiffu4(Lout, ro);
+            // lane-wise u16 updates: sums stay in [0, 63*255], so no carry or
+            // borrow crosses the 16-bit lanes
+            Ve[g] = Ve[g] + (ai & 0x00FF00FFu) - (ao & 0x00FF00FFu);
+            Vo[g] = Vo[g] + __byte_perm(ai, 0u, 0x4341) - __byte_perm(ao, 0u, 0x4341);
+          }
+          if (y >= y_first) {
+            uint4* dst = reinterpret_cast<uint4*>(s_vs + (k * kVsCols + tid + 1) * kVsStride);
+  #pragma unroll
+            for (int m = 0; m < 4; ++m) dst[m] = make_uint4(Ve[2 * m], Vo[2 * m], Ve[2 * m + 1], Vo[2 * m + 1]);
+          }
+          sin = sin + 1 < ring ? sin + 1 : 0;
+          offLi = (offLi + wm) & 15;
+          offRi = (offRi + wm) & 15;
+        }
+      }
+      slot = slot_next;
+      offL = (offL + kGroup * wm) & 15;
+      offR = (offR + kGroup * wm) & 15;
+      if (yg + ng - 1 < y_first) continue;  // still warming up
+      __syncthreads();
+      // Stage B: warp -> (row slot, half strip); lane -> disparity.  The warp
+      // slides the horizontal window along its half strip, 8 outputs per block.
+      {
+        const int g = warp >> 1, half = warp & 1;
+        const int y = yg + g;
+        if (g < ng && y >= y_first) {
+          const int HW = TX / 2;
+          const int xa = half * HW, xb = min(half * HW + HW, TX);
+          const int d = d0 + lane;
+          const uint32_t dbits = d <= D ? (uint32_t)d : 0xFFFFFFFFu;  // invalid lanes never win
+          const uint16_t* vcol = reinterpret_cast<const uint16_t*>(s_vs + g * kVsCols * kVsStride) + lanepos;
+          constexpr int CS = kVsStride / 2;                              // u16 per column
+          const uint8_t* bm = s_bm + (buf * kGroup + g) * kBBytes + (int)(((int64_t)y * w + x0) & 15);
+          uint32_t* krow = J.key + (int64_t)y * w + x0;
+          auto anchor = [&](int xi) -> bool {  // strip-relative output column
+            const int xl = x0 + xi;
+            return xi < xb && xl >= xo0 && xl <= xo1 && (xl == xo0 || xl == xo1 || bm[xi]);
+          };
+          auto emit = [&](uint32_t S, int xi) {
+            const uint32_t key = dbits == 0xFFFFFFFFu ? 0xFFFFFFFFu : ((S << SB_KEY_DBITS) | dbits);
+            const uint32_t kmin = __reduce_min_sync(0xffffffffu, key);
+            if (lane == 0) atomicMin(&krow[xi], kmin);
+          };
+          // S starts as the window of output xa - 1 (column xa - 1 + j, shifted by
+          // the zero column: slot column xa + j), then every output adds its
+          // entering column and drops its leaving one; HW is a multiple of 8.
+          uint32_t S = 0;
+          for (int j = 0; j <= 2 * r; ++j) S += vcol[(xa + j) * CS];
+          for (int xbase = xa; xbase < xb; xbase += 32) {
+            const unsigned mask = __ballot_sync(0xffffffffu, anchor(xbase + lane));
+            const int n = min(32, xb - xbase);
+            const uint16_t* pin = vcol + (xbase + 2 * r + 1) * CS;  // slot column of strip column x + 2r
+            const uint16_t* pout = vcol + xbase * CS;             // slot column of x - 1
+  #pragma unroll 1
+            for (int i = 0; i < n; i += 8) {
+              uint32_t Sv[8];
+  #pragma unroll
+              for (int k = 0; k < 8; ++k) {
+                S += (uint32_t)pin[(i + k) * CS] - (uint32_t)pout[(i + k) * CS];
+                Sv[k] = S;
+              }
+              const unsigned bits = (mask >> i) & 0xFFu;
+              if (bits & 0x0Fu) {
+  #pragma unroll
+                for (int k = 0; k < 4; ++k)
+                  if (bits & (1u << k)) emit(Sv[k], xbase + i + k);
+              }
+              if (bits & 0xF0u) {
+  #pragma unroll
+                for (int k = 4; k < 8; ++k)
+                  if (bits & (1u << k)) emit(Sv[k], xbase + i + k);
+              }
             }
           }
         }
       }
     }
-  }
+  }  // next work item
 }
 
 int sad_boxsum_smem_bytes(int r) {
@@ -267,11 +278,17 @@ int sad_boxsum_smem_bytes(int r) {
   return (ring + 1) * kRowBytes + 2 * kGroup * kBBytes + kGroup * kVsCols * kVsStride;
 }
 
-void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, cudaStream_t s) {
+void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, unsigned* queue,
+                       cudaStream_t s) {
   if (n_items <= 0) return;
   const int smem = sad_boxsum_smem_bytes(max_r);
   cudaFuncSetAttribute(k_sad_boxsum, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_sad_boxsum<<<n_items, kThreads, smem, s>>>(jobs, items);
+  int dev = 0, sms = 148, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sad_boxsum, kThreads, smem);
+  const int grid = std::min(n_items, sms * std::max(1, per_sm));
+  k_sad_boxsum<<<grid, kThreads, smem, s>>>(jobs, items, n_items, queue);
 }
 
 // ----------------------------------------------------------------- direct

@@ -167,6 +167,7 @@ struct sb_context {
   uint64_t launches = 0;
   uint8_t* tables = nullptr;  // lin (512 B) | coarse (4096 B) | thr (257 x 4 B)
   uint32_t* dev_err = nullptr;
+  unsigned* sad_queue = nullptr;  // work-item cursor of the box-sum SAD kernel
   uint8_t* ws = nullptr;
   size_t ws_bytes = 0;
   Uploader up;
@@ -376,6 +377,8 @@ void sad_items(const std::vector<std::pair<int, Geo>>& pairs, std::vector<SadIte
     base += (int64_t)((ncols + TX - 1) / TX) * ((D + 1 + kSadChunk - 1) / kSadChunk);
   }
   const int64_t target = 148 * 2 * 3;
+  // (cost, item): cost = rows including the 2r warm-up rows x the strip's columns
+  std::vector<std::pair<int64_t, SadItem>> list;
   for (auto& pg : pairs) {
     const Geo& g = pg.second;
     const int r = (g.p.block - 1) / 2, D = g.p.max_disp;
@@ -387,10 +390,14 @@ void sad_items(const std::vector<std::pair<int, Geo>>& pairs, std::vector<SadIte
     for (int b = 0; b < bands; ++b) {
       const int ya = yo0 + (int)((int64_t)rows * b / bands), yb = yo0 + (int)((int64_t)rows * (b + 1) / bands) - 1;
       if (ya > yb) continue;
+      const int64_t cost = (int64_t)(yb - ya + 1 + 2 * r) * (TX + 2 * r);
       for (int x0 = xo0; x0 <= xo1; x0 += TX)
-        for (int d0 = 0; d0 <= D; d0 += kSadChunk) items->push_back(SadItem{pg.first, x0, d0, ya, yb});
+        for (int d0 = 0; d0 <= D; d0 += kSadChunk) list.push_back({cost, SadItem{pg.first, x0, d0, ya, yb}});
     }
   }
+  // largest first, so the persistent kernel ends on short items (ties keep generation order)
+  std::stable_sort(list.begin(), list.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  for (auto& c : list) items->push_back(c.second);
 }
 
 // Stage boundary marks for sb_profile_read (external records inside captures).
@@ -536,8 +543,9 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
       if (!di) return st;
       int max_r = 0;
       for (auto& b : box) max_r = std::max(max_r, (b.second.p.block - 1) / 2);
+      SB_MEMSET(ctx, (ctx->sad_queue, 0, 4, s));
       if (!ctx->dry) {
-        launch_sad_boxsum(d, di, (int)items.size(), max_r, s);
+        launch_sad_boxsum(d, di, (int)items.size(), max_r, ctx->sad_queue, s);
         SB_LAUNCHED(ctx, 1);
       }
     }
@@ -635,6 +643,7 @@ sb_status sb_create(int device, size_t mem_budget_bytes, void* cuda_stream, sb_c
   if (cudaSetDevice(device) != cudaSuccess) return SB_ERR_CUDA;
   if (build_tables(ctx.get()) != SB_OK) return SB_ERR_CUDA;
   if (cudaMalloc(&ctx->dev_err, 4) != cudaSuccess || cudaMemset(ctx->dev_err, 0, 4) != cudaSuccess) return SB_ERR_CUDA;
+  if (cudaMalloc(&ctx->sad_queue, 4) != cudaSuccess) return SB_ERR_CUDA;
   if (ctx->up.init(8 << 20) != cudaSuccess) return SB_ERR_OOM;
   *out = ctx.release();
   return SB_OK;
@@ -654,6 +663,7 @@ void sb_destroy(sb_context* ctx) {
     if (ctx->prof_ev[i]) cudaEventDestroy(ctx->prof_ev[i]);
   if (ctx->tables) cudaFree(ctx->tables);
   if (ctx->dev_err) cudaFree(ctx->dev_err);
+  if (ctx->sad_queue) cudaFree(ctx->sad_queue);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->stage) cudaFree(ctx->stage);
   if (ctx->s_in) cudaStreamDestroy(ctx->s_in);
@@ -838,7 +848,8 @@ sb_status sb_boundary_sad(sb_context* ctx, const uint8_t* L_left, const uint8_t*
     sad_items({{0, g}}, &items);
     const SadItem* di = upload(ctx, items, &st);
     if (!di) return st;
-    launch_sad_boxsum(d, di, (int)items.size(), (block - 1) / 2, s);
+    SB_CUDA(ctx, cudaMemsetAsync(ctx->sad_queue, 0, 4, s));
+    launch_sad_boxsum(d, di, (int)items.size(), (block - 1) / 2, ctx->sad_queue, s);
     SB_LAUNCHED(ctx, 1);
   }
   if (dp) {

@@ -121,7 +121,9 @@ struct SadItem {
   int32_t job, x0, d0, y0, y1;  // output rows y0..y1 inclusive, inside Omega
 };
 // max_r: the largest block radius among the items (sizes shared memory)
-void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, cudaStream_t s);
+// queue: one device counter, zero before the launch (the kernel's work-item cursor)
+void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, unsigned* queue,
+                       cudaStream_t s);
 void launch_sad_direct(const SadJob* jobs, int n_jobs, cudaStream_t s);
 void launch_count_nonzero(const uint8_t* const* maps, const int64_t* n, int64_t* out, int n_maps, cudaStream_t s);
 int sad_boxsum_smem_bytes(int r);

@@ -96,10 +96,11 @@ extern "C" sb_status sb_boundary_sad_static(const uint8_t* L_left, const uint8_t
   uint8_t* desc = base + kKeyBytes;
 
   // descriptors: one job (and, at kCountOff, the boundary map, its size and a
-  // zeroed count for the device-side variant choice), then the box-sum work
-  // items (strip x disparity chunk x row band)
+  // zeroed count for the device-side variant choice; at kQueueOff the zeroed
+  // work cursor of the box-sum kernel), then the box-sum work items (strip x
+  // disparity chunk x row band)
   const int r = (block - 1) / 2;
-  constexpr size_t kCountOff = 192;
+  constexpr size_t kCountOff = 192, kQueueOff = 224;   // count block: map, size, count; queue: work cursor
   static_assert(sizeof(SadJob) <= kCountOff, "job descriptor overlaps the count block");
   SadJob job{L_left, L_right, boundary, key, disp, cost, w, h, max_disp, r, nullptr, -1};
   bool run_direct = variant == SB_SAD_DIRECT, run_box = variant == SB_SAD_BOXSUM;
@@ -151,7 +152,7 @@ extern "C" sb_status sb_boundary_sad_static(const uint8_t* L_left, const uint8_t
   if (run_direct && run_box)
     launch_count_nonzero((const uint8_t* const*)(desc + kCountOff), (const int64_t*)(desc + kCountOff + 8),
                          (int64_t*)(desc + kCountOff + 16), 1, s);
-  if (run_box) launch_sad_boxsum(djob, (const SadItem*)(desc + 256), n_items, r, s);
+  if (run_box) launch_sad_boxsum(djob, (const SadItem*)(desc + 256), n_items, r, (unsigned*)(desc + kQueueOff), s);
   if (run_direct) launch_sad_direct(djob, 1, s);
   launch_sad_finalize(djob, 1, w, h, s);
   e = cudaGetLastError();
