@@ -293,86 +293,243 @@ void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, in
 
 // ----------------------------------------------------------------- direct
 namespace {
-// 4 bytes at byte offset off (a multiple of 4) of an image of n bytes; bytes
-// past the end read as 0, a base that is not 4-byte aligned uses byte loads.
-__device__ __forceinline__ uint32_t load_word(const uint8_t* base, int64_t off, int64_t n) {
-  if (off + 3 < n && ((reinterpret_cast<uintptr_t>(base) & 3) == 0))
-    return __ldg(reinterpret_cast<const uint32_t*>(base + off));
-  uint32_t v = 0;
-  for (int b = 0; b < 4; ++b) v |= (off + b < n ? (uint32_t)__ldg(base + off + b) : 0u) << (8 * b);
-  return v;
+// Direct window sums (the paper's own formulation).  A CTA takes a tile of
+// kDirRows output rows x kDirCols output columns of one pair and stages, with
+// cp.async, the rows its windows read: the left image over the tile's columns
+// plus the window margin, the right image over the same columns shifted left
+// by up to D.  Warps then take the tile's anchors, one warp per anchor.  For
+// each window row the warp realigns the anchor's B left-image bytes once
+// (funnel shifts of aligned words, L' below) and reuses them for every
+// disparity.  Lane (c, g) = (lane & 3, lane >> 2) takes the disparity pair
+// d, d + 4 with d = 64p + c + 8g in pass p (64 disparities per pass); both
+// start at the same alignment within a 4-byte word, so NW + 1 aligned words
+// of the right image serve both: d + 4 uses the same words one position
+// earlier.  Bytes outside the window are masked to zero in both operands, so
+// every vabsdiff4.add adds only window cells.  A last pass of one disparity
+// per lane covers a remainder of at most 32 disparities.  Passes run in
+// groups of four with the window rows re-read per group.  NW = (B + 6) / 4
+// is the number of words a B-byte window spans at any alignment.  The argmin
+// over the warp is one redux.sync.
+constexpr int kPassGroup = 4;   // 64-disparity passes accumulated together (D < 256: one group)
+constexpr int kDirRows = 8;     // output rows per tile
+constexpr int kDirCols = 256;   // output columns per tile (8 warps x 32)
+
+// staged bytes per row of the left and right image for window radius r and max disparity D
+__host__ __device__ inline int dir_lbytes(int r) { return ((kDirCols + 2 * r + 16 + 15) + 15) & ~15; }
+__host__ __device__ inline int dir_rbytes(int r, int D) { return ((kDirCols + 2 * r + D + 13 + 15) + 15) & ~15; }
+__host__ __device__ inline int dir_smem_bytes(int r, int D) {
+  return (kDirRows + 2 * r) * (dir_lbytes(r) + dir_rbytes(r, D));
 }
-}  // namespace
-// One warp per (row, 32-column chunk); every anchor of the chunk is matched
-// by the whole warp, lanes = disparities d0 + lane for d0 = 0, 32, ...  A
-// persistent grid walks the jobs in order; a job served by the box-sum kernel
-// costs each CTA one descriptor read.
-__global__ void __launch_bounds__(256) k_sad_direct(const SadJob* __restrict__ jobs, int n_jobs) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int j = 0; j < n_jobs; ++j) {
-    const SadJob J = jobs[j];
-    if (!sad_use_direct(J)) continue;
-    const int r = J.r, D = J.D, w = J.w, B = 2 * r + 1;
-    const int xo0 = D + r, xo1 = w - 1 - r;
-    const int xblocks = (xo1 - xo0 + 256) / 256;          // 256-column blocks of Omega
-    const int64_t units = (int64_t)(J.h - 2 * r) * xblocks;
-    const int nw = (B + 3) >> 2;                           // words per window row
-    const int64_t nimg = (int64_t)w * J.h;
-    const uint32_t lastmask = (B & 3) ? (0xFFFFFFFFu >> (8 * (4 - (B & 3)))) : 0xFFFFFFFFu;
-    for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-      const int y = r + (int)(u / xblocks);
-      const int x = xo0 + ((int)(u % xblocks) * 8 + wid) * 32 + lane;
-      bool anc = false;
-      if (x <= xo1) anc = (x == xo0) || (x == xo1) || J.bmap[(int64_t)y * w + x];
-      uint32_t mask = __ballot_sync(0xffffffffu, anc);
-      while (mask) {
-        const int i = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const int xa = x - lane + i;                        // the anchor
-        uint32_t best = 0xFFFFFFFFu;
-        for (int d0 = 0; d0 <= D; d0 += 32) {
-          const int d = d0 + lane;
-          const bool dv = d <= D;
-          const int dd = dv ? d : D;                        // keep addresses inside the image
-          uint32_t acc = 0;
-          const int lstart = xa - r, rstart = xa - r - dd;
-          for (int iy = -r; iy <= r; ++iy) {
-            // word-aligned absolute offsets of the window starts in this row
-            const int64_t row = (int64_t)(y + iy) * w;
-            const int64_t labs = row + lstart, rabs = row + rstart;
-            const int64_t la = labs & ~(int64_t)3, ra = rabs & ~(int64_t)3;
-            const int lsh = (int)(labs & 3) * 8, rsh = (int)(rabs & 3) * 8;
-            uint32_t lp = load_word(J.Ll, la, nimg), rp = load_word(J.Lr, ra, nimg);
-            for (int k = 0; k < nw; ++k) {
-              const uint32_t ln = load_word(J.Ll, la + 4 * k + 4, nimg);
-              const uint32_t rn = load_word(J.Lr, ra + 4 * k + 4, nimg);
-              uint32_t lw = __funnelshift_r(lp, ln, lsh), rw = __funnelshift_r(rp, rn, rsh);
-              lp = ln;
-              rp = rn;
-              if (k == nw - 1) { lw &= lastmask; rw &= lastmask; }
-              asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %0;" : "+r"(acc) : "r"(lw), "r"(rw));
+
+// bytes [0, n) of a word set, n clamped to [0, 4]
+__device__ __forceinline__ uint32_t low_bytes(int n) {
+  return (uint32_t)((1ull << (8 * min(max(n, 0), 4))) - 1ull);
+}
+// valid bytes of word k of a window that starts `off` bytes into word 0 and
+// spans B bytes: [off - 4k, off + B - 4k) within the word
+__device__ __forceinline__ uint32_t win_mask(int k, int off, int B) {
+  return low_bytes(off + B - 4 * k) & ~low_bytes(off - 4 * k);
+}
+
+__device__ __forceinline__ uint32_t lds32(const uint8_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// One anchor (y, xa) of the tile whose first output row is y0 and first output
+// column x0; sL / sR hold staged row t = image row y0 - r + t from absolute
+// byte aL(t) / aR(t) on (multiples of 16, so word alignment is preserved).
+template <int NW>
+__device__ __forceinline__ void direct_anchor(const SadJob& J, int y0, int x0, const uint8_t* sL,
+                                              const uint8_t* sR, int lb, int rbytes, int y, int xa, int lane,
+                                              int n2, bool p1) {
+  const int r = J.r, B = 2 * r + 1, D = J.D, w = J.w;
+  const int c = lane & 3, g = lane >> 2;
+  // largest disparity <= D of this lane's class (d = c mod 4): where a lane
+  // past D reads instead, so that every read stays inside the staged rows
+  const int dcap = D >= c ? D - ((D - c) & 3) : c;
+  const int ngroups = max((n2 + kPassGroup - 1) / kPassGroup, 1);
+  uint32_t best = 0xFFFFFFFFu;
+  for (int gi = 0; gi < ngroups; ++gi) {
+    const bool last = gi == ngroups - 1;
+    uint32_t acc2[kPassGroup][2], acc1 = 0;
+#pragma unroll
+    for (int q = 0; q < kPassGroup; ++q) acc2[q][0] = acc2[q][1] = 0;
+    for (int iy = -r; iy <= r; ++iy) {
+      const int t = y + iy - (y0 - r);                       // staged row
+      const int64_t rb = (int64_t)(y + iy) * w;
+      const int64_t aL = (rb + x0 - r - 6) & ~(int64_t)15, aR = (rb + x0 - r - D - 7) & ~(int64_t)15;
+      const uint8_t* Lrow = sL + t * lb - aL;                  // index by absolute byte
+      const uint8_t* Rrow = sR + t * rbytes - aR;
+      const int off = (int)((rb + xa - r - c) & 3);           // window start within its word, d = c mod 4
+      const int64_t s = rb + xa - r - off;                    // L' starts off bytes before the window
+      const int64_t sa = s & ~(int64_t)3;
+      const int sh = (int)(s - sa) * 8;
+      uint32_t Lp[NW], mk[NW];
+      uint32_t prev = lds32(Lrow + sa);
+#pragma unroll
+      for (int k = 0; k < NW; ++k) {
+        const uint32_t nx = lds32(Lrow + sa + 4 * k + 4);
+        mk[k] = (k == 0 || k >= NW - 2) ? win_mask(k, off, B) : 0xFFFFFFFFu;
+        Lp[k] = __funnelshift_r(prev, nx, sh) & mk[k];
+        prev = nx;
+      }
+#pragma unroll
+      for (int q = 0; q < kPassGroup; ++q) {
+        const int p = gi * kPassGroup + q;
+        if (p < n2) {
+          const int d0 = min(64 * p + c + 8 * g, dcap);
+          const uint8_t* ra = Rrow + (rb + xa - r - d0 - off - 4);  // word-aligned; d0 + 4 starts here
+          uint32_t R[NW + 1];
+#pragma unroll
+          for (int k = 0; k <= NW; ++k) R[k] = lds32(ra + 4 * k);
+          // even and odd words into separate sums: twice the independent chains
+          uint32_t s0 = acc2[q][0], s1 = acc2[q][1], t0 = 0, t1 = 0;
+#pragma unroll
+          for (int k = 0; k < NW; ++k) {
+            const uint32_t r0 = (k == 0 || k >= NW - 2) ? (R[k + 1] & mk[k]) : R[k + 1];
+            const uint32_t r1 = (k == 0 || k >= NW - 2) ? (R[k] & mk[k]) : R[k];
+            if (k & 1) {
+              asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %0;" : "+r"(t0) : "r"(Lp[k]), "r"(r0));
+              asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %0;" : "+r"(t1) : "r"(Lp[k]), "r"(r1));
+            } else {
+              asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %0;" : "+r"(s0) : "r"(Lp[k]), "r"(r0));
+              asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %0;" : "+r"(s1) : "r"(Lp[k]), "r"(r1));
             }
           }
-          const uint32_t key = dv ? ((acc << SB_KEY_DBITS) | (uint32_t)d) : 0xFFFFFFFFu;
-          best = min(best, __reduce_min_sync(0xffffffffu, key));
+          acc2[q][0] = s0 + t0;
+          acc2[q][1] = s1 + t1;
         }
-        if (lane == 0) J.key[(int64_t)y * w + xa] = best;
+      }
+      if (last && p1) {
+        const int d = min(64 * n2 + lane, dcap);
+        const uint8_t* ra = Rrow + (rb + xa - r - d - off);
+        uint32_t s1 = acc1;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+          uint32_t rw = lds32(ra + 4 * k);
+          if (k == 0 || k >= NW - 2) rw &= mk[k];
+          asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %0;" : "+r"(s1) : "r"(Lp[k]), "r"(rw));
+        }
+        acc1 = s1;
+      }
+    }
+    // this group's argmin over the lane's disparities; lanes past D never win
+#pragma unroll
+    for (int q = 0; q < kPassGroup; ++q) {
+      const int p = gi * kPassGroup + q;
+      if (p < n2) {
+        const int d0 = 64 * p + c + 8 * g;
+        if (d0 <= D) best = min(best, (acc2[q][0] << SB_KEY_DBITS) | (uint32_t)d0);
+        if (d0 + 4 <= D) best = min(best, (acc2[q][1] << SB_KEY_DBITS) | (uint32_t)(d0 + 4));
+      }
+    }
+    if (last && p1 && 64 * n2 + lane <= D) best = min(best, (acc1 << SB_KEY_DBITS) | (uint32_t)(64 * n2 + lane));
+  }
+  best = __reduce_min_sync(0xffffffffu, best);
+  if (lane == 0) J.key[(int64_t)y * w + xa] = best;
+}
+
+// Persistent grid over the tiles of the jobs whose window spans NW words and
+// that the direct variant serves.
+template <int NW>
+__global__ void __launch_bounds__(256) k_sad_direct(const SadJob* __restrict__ jobs, int n_jobs) {
+  extern __shared__ __align__(16) uint8_t dsm[];
+  __shared__ uint16_t s_list[kDirRows * kDirCols];   // the tile's anchors: row * kDirCols + column
+  __shared__ int s_na;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int j = 0; j < n_jobs; ++j) {
+    const SadJob J = jobs[j];
+    if ((2 * J.r + 1 + 6) / 4 != NW || !sad_use_direct(J)) continue;
+    const int r = J.r, D = J.D, w = J.w, h = J.h;
+    const int xo0 = D + r, xo1 = w - 1 - r, yo0 = r, yo1 = h - 1 - r;
+    const int tcols = (xo1 - xo0 + kDirCols) / kDirCols, trows = (yo1 - yo0 + kDirRows) / kDirRows;
+    const int64_t npx = (int64_t)w * h;
+    const int n2 = (D + 1) / 64 + ((D + 1) % 64 > 32 ? 1 : 0);
+    const bool p1 = (D + 1) % 64 != 0 && (D + 1) % 64 <= 32;
+    const bool fast = (((uintptr_t)J.Ll | (uintptr_t)J.Lr) & 15) == 0;
+    const int lb = dir_lbytes(r), rbytes = dir_rbytes(r, D), nrows = kDirRows + 2 * r;
+    const int nchL = lb / 16, nchR = rbytes / 16;
+    uint8_t* sL = dsm;
+    uint8_t* sR = dsm + nrows * lb;
+    for (int tile = blockIdx.x; tile < tcols * trows; tile += gridDim.x) {
+      const int y0 = yo0 + (tile / tcols) * kDirRows, x0 = xo0 + (tile % tcols) * kDirCols;
+      __syncthreads();  // the previous tile's windows are done
+      if (tid == 0) s_na = 0;
+      // stage rows y0 - r .. y0 + kDirRows - 1 + r (all inside the image: y0 >= r)
+      const int last_row = min(y0 + kDirRows - 1, yo1) + r;
+      for (int i = tid; i < nrows * (nchL + nchR); i += 256) {
+        const int t = i / (nchL + nchR), ch = i - t * (nchL + nchR);
+        const int yy = y0 - r + t;
+        if (yy > last_row) continue;
+        const int64_t rb = (int64_t)yy * w;
+        if (ch < nchL)
+          stage_chunk(sL + t * lb, J.Ll, npx, (rb + x0 - r - 6) & ~(int64_t)15, ch, fast);
+        else
+          stage_chunk(sR + t * rbytes, J.Lr, npx, (rb + x0 - r - D - 7) & ~(int64_t)15, ch - nchL, fast);
+      }
+      cp_async_commit();
+      cp_async_wait_all();
+      __syncthreads();
+      // the tile's anchors into a shared list (warp wid scans column chunk wid
+      // of every output row), then the warps take them in turn: every anchor
+      // costs the same, so the warps stay balanced even when the anchors
+      // cluster (the domain's edge columns are anchors in every row)
+      for (int i = 0; i < kDirRows; ++i) {
+        const int y = y0 + i;
+        if (y > yo1) break;
+        const int x = x0 + wid * 32 + lane;
+        bool anc = false;
+        if (x <= xo1) anc = (x == xo0) || (x == xo1) || J.bmap[(int64_t)y * w + x];
+        const uint32_t mask = __ballot_sync(0xffffffffu, anc);
+        int base = 0;
+        if (lane == 0 && mask) base = atomicAdd(&s_na, __popc(mask));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (anc) s_list[base + __popc(mask & ((1u << lane) - 1))] = (uint16_t)(i * kDirCols + (x - x0));
+      }
+      __syncthreads();
+      const int na = s_na;
+      for (int a = wid; a < na; a += 8) {
+        const int v = s_list[a];
+        direct_anchor<NW>(J, y0, x0, sL, sR, lb, rbytes, y0 + v / kDirCols, x0 + v % kDirCols, lane, n2, p1);
       }
     }
   }
 }
 
-void launch_sad_direct(const SadJob* jobs, int n_jobs, cudaStream_t s) {
+template <int NW>
+void launch_direct_nw(const SadJob* jobs, int n_jobs, int smem, cudaStream_t s) {
+  cudaFuncSetAttribute(k_sad_direct<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int dev = 0, sms = 148, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sad_direct<NW>, 256, smem);
+  k_sad_direct<NW><<<sms * std::max(1, per_sm), 256, smem, s>>>(jobs, n_jobs);
+}
+}  // namespace
+
+int sad_direct_words(int block) { return (block + 6) / 4; }
+
+void launch_sad_direct(const SadJob* jobs, int n_jobs, int nw, int max_r, int max_D, cudaStream_t s) {
   if (n_jobs <= 0) return;
-  static int grid = 0;
-  if (!grid) {
-    int dev = 0, sms = 148, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sad_direct, 256, 0);
-    grid = sms * std::max(1, per_sm);
+  const int smem = dir_smem_bytes(max_r, max_D);
+  switch (nw) {
+    case 1: launch_direct_nw<1>(jobs, n_jobs, smem, s); break;
+    case 2: launch_direct_nw<2>(jobs, n_jobs, smem, s); break;
+    case 3: launch_direct_nw<3>(jobs, n_jobs, smem, s); break;
+    case 4: launch_direct_nw<4>(jobs, n_jobs, smem, s); break;
+    case 5: launch_direct_nw<5>(jobs, n_jobs, smem, s); break;
+    case 6: launch_direct_nw<6>(jobs, n_jobs, smem, s); break;
+    case 7: launch_direct_nw<7>(jobs, n_jobs, smem, s); break;
+    case 8: launch_direct_nw<8>(jobs, n_jobs, smem, s); break;
+    case 9: launch_direct_nw<9>(jobs, n_jobs, smem, s); break;
+    case 10: launch_direct_nw<10>(jobs, n_jobs, smem, s); break;
+    case 11: launch_direct_nw<11>(jobs, n_jobs, smem, s); break;
+    case 12: launch_direct_nw<12>(jobs, n_jobs, smem, s); break;
+    case 13: launch_direct_nw<13>(jobs, n_jobs, smem, s); break;
+    case 14: launch_direct_nw<14>(jobs, n_jobs, smem, s); break;
+    case 15: launch_direct_nw<15>(jobs, n_jobs, smem, s); break;
+    case 16: launch_direct_nw<16>(jobs, n_jobs, smem, s); break;
+    case 17: launch_direct_nw<17>(jobs, n_jobs, smem, s); break;
+    default: break;
   }
-  k_sad_direct<<<grid, 256, 0, s>>>(jobs, n_jobs);
 }
 
 // Nonzero bytes of each map (the boundary count the variant choice reads);

@@ -520,7 +520,8 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
   {
     std::vector<SadJob> J;
     std::vector<std::pair<int, Geo>> box;
-    bool any_direct = false;
+    uint32_t direct_nw = 0;   // bit k: some pair the direct kernel may serve has a k-word window
+    int dir_r = 0, dir_D = 0;
     for (int i = 0; i < n; ++i) {
       auto& r = runs[i];
       const size_t N = (size_t)r.g.w * r.g.h;
@@ -530,7 +531,11 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
       bool dp = false, bp = true;
       sad_choice(r.g, r.ws.cut, &sj, &dp, &bp);   // cut[0]: boundary pixels of the refined map
       J.push_back(sj);
-      any_direct |= dp;
+      if (dp) {
+        direct_nw |= 1u << sad_direct_words(r.g.p.block);
+        dir_r = std::max(dir_r, (r.g.p.block - 1) / 2);
+        dir_D = std::max(dir_D, r.g.p.max_disp);
+      }
       if (bp) box.push_back({i, r.g});
     }
     const SadJob* d = upload(ctx, J, &st);
@@ -549,10 +554,11 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
         SB_LAUNCHED(ctx, 1);
       }
     }
-    if (any_direct && !ctx->dry) {
-      launch_sad_direct(d, n, s);
-      SB_LAUNCHED(ctx, 1);
-    }
+    for (int nw = 1; nw <= 17 && !ctx->dry; ++nw)
+      if (direct_nw & (1u << nw)) {
+        launch_sad_direct(d, n, nw, dir_r, dir_D, s);
+        SB_LAUNCHED(ctx, 1);
+      }
     SB_MARK(ctx, SB_STAGE_SAD_FINALIZE);
     if (!ctx->dry) {
       launch_sad_finalize(d, n, max_w, max_h, s);
@@ -853,7 +859,7 @@ sb_status sb_boundary_sad(sb_context* ctx, const uint8_t* L_left, const uint8_t*
     SB_LAUNCHED(ctx, 1);
   }
   if (dp) {
-    launch_sad_direct(d, 1, s);
+    launch_sad_direct(d, 1, sad_direct_words(block), (block - 1) / 2, max_disp, s);
     SB_LAUNCHED(ctx, 1);
   }
   launch_sad_finalize(d, 1, w, h, s);

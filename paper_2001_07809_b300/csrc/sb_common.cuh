@@ -100,18 +100,20 @@ __device__ __forceinline__ bool sad_use_direct(const SadJob& J) {
 
 // Cost model of the automatic SAD choice.  The direct kernel spends about
 // 1/kDirectVsBox box-sum (domain pixel, disparity) steps per (anchor,
-// disparity, window cell), disparities rounded up to whole 32-lane chunks
-// (fitted on B300 timings of both kernels over 65 pairs of mixed size,
-// disparity range, block and density).  Anchors are estimated from the
+// computed disparity, window cell); it computes the disparities in passes of
+// 64 plus a last pass of 32 (fitted on B300 timings of both kernels over the
+// 64 pairs of mixed size, disparity range, block and boundary density of the
+// uneven batch and a 4096x2304 frame).  Anchors are estimated from the
 // boundary count N_b of the whole image as N_b |Omega| / (w h) plus the two
 // domain-edge columns.  Returns the largest N_b for which the direct kernel
 // is the cheaper one, or -1 when it never is.
-constexpr double kDirectVsBox = 0.3;
+constexpr double kDirectVsBox = 1.0;
 inline int64_t sad_direct_limit(int w, int h, int D, int B) {
   const int r = (B - 1) / 2;
   const double omega = (double)(w - D - 2 * r) * (double)(h - 2 * r);
-  const double chunks = 32.0 * ((D + 32) / 32);
-  const double anchors = kDirectVsBox * omega * (D + 1) / (chunks * (double)B * B) - 2.0 * (h - 2 * r);
+  const int rem = (D + 1) % 64;
+  const double computed = 64.0 * ((D + 1) / 64 + (rem > 32 ? 1 : 0)) + (rem > 0 && rem <= 32 ? 32.0 : 0.0);
+  const double anchors = kDirectVsBox * omega * (D + 1) / (computed * (double)B * B) - 2.0 * (h - 2 * r);
   if (!(anchors > 0.0)) return -1;
   const double lim = anchors * (double)w * h / omega;   // N_b < lim
   return (int64_t)std::ceil(lim) - 1;
@@ -124,7 +126,10 @@ struct SadItem {
 // queue: one device counter, zero before the launch (the kernel's work-item cursor)
 void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, unsigned* queue,
                        cudaStream_t s);
-void launch_sad_direct(const SadJob* jobs, int n_jobs, cudaStream_t s);
+// the direct kernel for the jobs whose window spans nw = sad_direct_words(block) words
+int sad_direct_words(int block);
+// (shared memory sized for the largest window radius and disparity range among them)
+void launch_sad_direct(const SadJob* jobs, int n_jobs, int nw, int max_r, int max_D, cudaStream_t s);
 void launch_count_nonzero(const uint8_t* const* maps, const int64_t* n, int64_t* out, int n_maps, cudaStream_t s);
 int sad_boxsum_smem_bytes(int r);
 void launch_sad_finalize(const SadJob* jobs, int n_jobs, int max_w, int max_h, cudaStream_t s);

@@ -153,7 +153,7 @@ extern "C" sb_status sb_boundary_sad_static(const uint8_t* L_left, const uint8_t
     launch_count_nonzero((const uint8_t* const*)(desc + kCountOff), (const int64_t*)(desc + kCountOff + 8),
                          (int64_t*)(desc + kCountOff + 16), 1, s);
   if (run_box) launch_sad_boxsum(djob, (const SadItem*)(desc + 256), n_items, r, (unsigned*)(desc + kQueueOff), s);
-  if (run_direct) launch_sad_direct(djob, 1, s);
+  if (run_direct) launch_sad_direct(djob, 1, sad_direct_words(block), r, max_disp, s);
   launch_sad_finalize(djob, 1, w, h, s);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
