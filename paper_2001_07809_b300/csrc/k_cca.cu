@@ -1,17 +1,21 @@
 // Connected components analysis and small-component removal (Section III).
 //
 // Labelling (8-connectivity) is union-find: each 32x32 tile first unites its
-// pixels in shared memory, then pixels on tile borders unite across tiles in
-// global memory, then every pixel jumps to its root.  Unions always hang the
-// larger root under the smaller (atomicMin), so a component's final root is
-// its smallest linear index: the same label a raster-order flood fill gives.
+// pixels in shared memory (at most two unions per pixel, by the decision tree
+// of two-pass labelling), then pixels on tile borders unite across tiles in
+// global memory, then every pixel jumps to its root while the sizes are
+// counted.  Unions always hang the larger root under the smaller (atomicMin),
+// so a component's final root is its smallest linear index: the same label a
+// raster-order flood fill gives.
 //
 // Removal: the components are ordered by (size, label) and the longest
 // prefix holding at most floor(frac * N_b) pixels is removed.  On the device
 // that prefix is "every component smaller than s*, plus the m size-s*
 // components with the smallest labels", with s* and m found from a histogram
-// of component sizes, and the cut label T found from per-row counts.  No
-// host round-trip, so the whole sequence can be captured in a CUDA graph.
+// of component sizes, and the cut label T found from per-row counts; both
+// counts run over the list of roots rather than over every pixel.  No host
+// round-trip, so the whole sequence can be captured in a CUDA graph.
+#include <algorithm>
 #include "sb_common.cuh"
 
 namespace sb {
@@ -64,12 +68,16 @@ __global__ void __launch_bounds__(256) k_cca_local(const CcaJob* __restrict__ jo
   for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) {
     if (s_p[i] < 0) continue;
     const int lx = i & (CT - 1), ly = i >> 5;
-    // previous neighbours inside the tile: W, NW, N, NE
-    if (lx > 0 && s_p[i - 1] >= 0) ok &= unite(s_p, i, i - 1);
-    if (ly > 0) {
-      if (lx > 0 && s_p[i - CT - 1] >= 0) ok &= unite(s_p, i, i - CT - 1);
-      if (s_p[i - CT] >= 0) ok &= unite(s_p, i, i - CT);
-      if (lx < CT - 1 && s_p[i - CT + 1] >= 0) ok &= unite(s_p, i, i - CT + 1);
+    // previous neighbours inside the tile (W, NW, N, NE), by the usual
+    // 8-connectivity decision tree: N alone when it is set (W, NW and NE all
+    // touch N, and their links to N are made when those pixels are visited);
+    // otherwise W or else NW (they touch each other), plus NE
+    if (ly > 0 && s_p[i - CT] >= 0) {
+      ok &= unite(s_p, i, i - CT);
+    } else {
+      if (lx > 0 && s_p[i - 1] >= 0) ok &= unite(s_p, i, i - 1);
+      else if (ly > 0 && lx > 0 && s_p[i - CT - 1] >= 0) ok &= unite(s_p, i, i - CT - 1);
+      if (ly > 0 && lx < CT - 1 && s_p[i - CT + 1] >= 0) ok &= unite(s_p, i, i - CT + 1);
     }
   }
   __syncthreads();
@@ -116,21 +124,13 @@ __global__ void __launch_bounds__(256) k_cca_merge(const CcaJob* __restrict__ jo
   if (!ok) atomicOr(dev_err, DEV_ERR_CCA_ITER);
 }
 
-// Flatten to roots, then count component sizes and the boundary pixels.
-__global__ void __launch_bounds__(256) k_cca_flatten(const CcaJob* __restrict__ jobs) {
-  const CcaJob J = jobs[blockIdx.y];
-  const int64_t n = (int64_t)J.w * J.h;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-    int v = J.lab[p];
-    if (v >= 0 && v != (int)p) J.lab[p] = find_root(J.lab, v);
-  }
-}
-
-// Component sizes: each 32x32 tile first counts its pixels per root in a
-// small shared-memory hash table, then adds one total per (tile, root) to the
-// global size array, so a large component costs one atomic per tile it
-// touches instead of one per pixel.  Also counts the boundary pixels.
+// Final labels and component sizes: every pixel of a 32x32 tile follows its
+// parent chain to the root (and stores it: the label is then the root), the
+// tile counts its pixels per root in a small shared-memory hash table and
+// adds one total per (tile, root) to the global size array, so a large
+// component costs one atomic per tile it touches instead of one per pixel.
+// Roots append themselves to the job's root list, and the tile's boundary
+// pixels are added to N_b.
 __global__ void __launch_bounds__(256) k_cc_count(const CcaJob* __restrict__ jobs) {
   constexpr int HS = 256;  // hash slots (a tile rarely holds more than a few dozen roots)
   __shared__ int s_key[HS];
@@ -146,9 +146,14 @@ __global__ void __launch_bounds__(256) k_cc_count(const CcaJob* __restrict__ job
   for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) {
     const int x = tx0 + (i & (CT - 1)), y = ty0 + (i >> 5);
     if (x >= J.w || y >= J.h) continue;
-    const int v = J.lab[(int64_t)y * J.w + x];
+    const int64_t p = (int64_t)y * J.w + x;
+    int v = J.lab[p];
     if (v < 0) continue;
     ++mine;
+    const int f = find_root(J.lab, v);
+    if (f != v) J.lab[p] = f;   // only shortens paths other tiles may be following
+    if (f == (int)p) J.roots[atomicAdd(reinterpret_cast<unsigned long long*>(&J.cut[5]), 1ull)] = f;
+    v = f;
     unsigned hsh = ((unsigned)v * 2654435761u) >> 24;  // 8 bits
     bool placed = false;
     volatile int* vkey = s_key;
@@ -177,14 +182,12 @@ __device__ __forceinline__ int64_t removal_limit(const CcaJob& J) {
 
 __global__ void __launch_bounds__(256) k_cc_hist(const CcaJob* __restrict__ jobs) {
   const CcaJob J = jobs[blockIdx.y];
-  const int64_t n = (int64_t)J.w * J.h;
+  const int64_t nroots = J.cut[5];
   const int64_t limit = removal_limit(J);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-    if (J.lab[p] == (int)p) {
-      const uint32_t s = J.size[p];
-      if ((int64_t)s <= limit && (int64_t)s < J.shist_len) atomicAdd(&J.shist[s], 1u);
-    }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nroots; i += stride) {
+    const uint32_t s = J.size[J.roots[i]];
+    if ((int64_t)s <= limit && (int64_t)s < J.shist_len) atomicAdd(&J.shist[s], 1u);
   }
 }
 
@@ -234,21 +237,16 @@ __global__ void __launch_bounds__(1024) k_cc_cut(const CcaJob* __restrict__ jobs
   }
 }
 
-// Per row: how many roots have size s* (only when m > 0).
+// Per row: how many roots have size s* (only when m > 0); rowcnt is zero on entry.
 __global__ void __launch_bounds__(256) k_cc_rowcount(const CcaJob* __restrict__ jobs) {
   const CcaJob J = jobs[blockIdx.y];
   if (J.cut[3] <= 0) return;
   const uint32_t sstar = (uint32_t)J.cut[2];
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int y = warp; y < J.h; y += nwarps) {
-    unsigned cnt = 0;
-    for (int x = lane; x < J.w; x += 32) {
-      const int64_t p = (int64_t)y * J.w + x;
-      cnt += (J.lab[p] == (int)p && J.size[p] == sstar) ? 1u : 0u;
-    }
-    for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if (lane == 0) J.rowcnt[y] = cnt;
+  const int64_t nroots = J.cut[5];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nroots; i += stride) {
+    const int v = J.roots[i];
+    if (J.size[v] == sstar) atomicAdd(&J.rowcnt[v / J.w], 1u);
   }
 }
 
@@ -331,11 +329,6 @@ void launch_cca(const CcaJob* jobs, int n_jobs, int max_w, int max_h, uint32_t* 
   dim3 tiles((max_w + CT - 1) / CT, (max_h + CT - 1) / CT, n_jobs);
   k_cca_local<<<tiles, 256, 0, s>>>(jobs, dev_err);
   k_cca_merge<<<tiles, 128, 0, s>>>(jobs, dev_err);
-  const int64_t n = (int64_t)max_w * max_h;
-  int bpj = (int)((n + 256 * 8 - 1) / (256 * 8));
-  if (bpj > 1184) bpj = 1184;
-  if (bpj < 1) bpj = 1;
-  k_cca_flatten<<<dim3(bpj, n_jobs), 256, 0, s>>>(jobs);
 }
 
 void launch_cc_filter(const CcaJob* jobs, int n_jobs, int max_w, int max_h, cudaStream_t s) {
@@ -345,11 +338,10 @@ void launch_cc_filter(const CcaJob* jobs, int n_jobs, int max_w, int max_h, cuda
   if (bpj > 1184) bpj = 1184;
   if (bpj < 1) bpj = 1;
   k_cc_count<<<dim3((max_w + CT - 1) / CT, (max_h + CT - 1) / CT, n_jobs), 256, 0, s>>>(jobs);
-  k_cc_hist<<<dim3(bpj, n_jobs), 256, 0, s>>>(jobs);
+  const int rpj = std::max(1, std::min(bpj, 148));   // root-list passes: roots are few
+  k_cc_hist<<<dim3(rpj, n_jobs), 256, 0, s>>>(jobs);
   k_cc_cut<<<n_jobs, 1024, 0, s>>>(jobs);
-  int rb = (max_h + 7) / 8;
-  if (rb > 592) rb = 592;
-  k_cc_rowcount<<<dim3(rb, n_jobs), 256, 0, s>>>(jobs);
+  k_cc_rowcount<<<dim3(rpj, n_jobs), 256, 0, s>>>(jobs);
   k_cc_select<<<n_jobs, 1024, 0, s>>>(jobs);
   k_cc_filter<<<dim3(bpj, n_jobs), 256, 0, s>>>(jobs);
 }

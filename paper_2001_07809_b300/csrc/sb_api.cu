@@ -85,6 +85,7 @@ struct Uploader {
 struct PairWs {
   uint8_t *Ll, *Lr, *refined, *filtered, *lut;
   uint32_t *hist, *size_key, *shist, *rowcnt;
+  int32_t* roots;   // component roots of the CCA (at most ceil(w/2) ceil(h/2) with 8-connectivity)
   double* centroids;
   int32_t *lab, *iters;
   int64_t* cut;
@@ -106,7 +107,7 @@ size_t pair_ws_bytes(const Geo& g, bool need_disp) {
   b += al(N) * 4;                        // Ll, Lr, refined, filtered
   b += al(256) + al(256 * 4) + al(256 * 8) + al(8) + al(8 * 8);
   b += al(N * 4) * 2;                    // size/key, lab
-  b += al(shist * 4) + al((size_t)g.h * 4);
+  b += al(shist * 4) + al((size_t)g.h * 4) + al(N + g.w + g.h + 1);   // + root list
   b += al(N * 2) * (need_disp ? 3 : 2);  // sparse, filled (+ disp)
   b += al((size_t)nseg * g.w * 2) * 2;
   b += al(200 * 4);
@@ -133,6 +134,7 @@ PairWs carve(uint8_t* base, const Geo& g, bool need_disp) {
   s.lab = (int32_t*)take(N * 4);
   s.shist = (uint32_t*)take(shist * 4);
   s.rowcnt = (uint32_t*)take((size_t)g.h * 4);
+  s.roots = (int32_t*)take(N + g.w + g.h + 1);   // 4 ceil(w/2) ceil(h/2) <= (w+1)(h+1) bytes
   s.sparse = (uint16_t*)take(N * 2);
   s.filled = (uint16_t*)take(N * 2);
   s.disp = need_disp ? (uint16_t*)take(N * 2) : nullptr;
@@ -502,14 +504,15 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
       const size_t N = (size_t)r.g.w * r.g.h;
       SB_MEMSET(ctx, (r.ws.size_key, 0, N * 4, s));
       SB_MEMSET(ctx, (r.ws.shist, 0, (size_t)r.ws.shist_len * 4, s));
+      SB_MEMSET(ctx, (r.ws.rowcnt, 0, (size_t)r.g.h * 4, s));
       J.push_back(CcaJob{r.ws.refined, r.ws.lab, r.ws.size_key, r.ws.shist, r.ws.rowcnt, r.ws.cut, r.ws.filtered,
-                         r.g.w, r.g.h, r.ws.shist_len, r.g.p.cc_remove_fraction});
+                         r.ws.roots, r.g.w, r.g.h, r.ws.shist_len, r.g.p.cc_remove_fraction});
     }
     const CcaJob* d = upload(ctx, J, &st);
     if (!d) return st;
     if (!ctx->dry) {
       launch_cca(d, n, max_w, max_h, ctx->dev_err, s);
-      SB_LAUNCHED(ctx, 3);
+      SB_LAUNCHED(ctx, 2);
     }
     if (!ctx->dry) {
       launch_cc_filter(d, n, max_w, max_h, s);
@@ -781,7 +784,7 @@ sb_status sb_refine_boundaries(sb_context* ctx, const uint8_t* labels, int32_t w
   if ((int64_t)w * h >= (int64_t)1 << 31) return fail(ctx, SB_ERR_INVALID_ARG, "image too large");
   const size_t N = (size_t)w * h;
   const size_t shist = (size_t)floor(cc_remove_fraction * (double)N) + 2;
-  const size_t need = al(N) + al(N * 4) * 2 + al(shist * 4) + al((size_t)h * 4) + al(64);
+  const size_t need = al(N) + al(N * 4) * 2 + al(shist * 4) + al((size_t)h * 4) + al(64) + al(N + w + h + 1);
   sb_status st = ensure_ws(ctx, need);
   if (st != SB_OK) return st;
   uint8_t* o = ctx->ws;
@@ -796,6 +799,8 @@ sb_status sb_refine_boundaries(sb_context* ctx, const uint8_t* labels, int32_t w
   uint32_t* rowcnt = (uint32_t*)o;
   o += al((size_t)h * 4);
   int64_t* cut = (int64_t*)o;
+  o += al(64);
+  int32_t* roots = (int32_t*)o;
   cudaStream_t s = ctx->stream;
   std::vector<MorphJob> MJ{MorphJob{labels, nullptr, ref, w, h, morph_mode}};
   const MorphJob* dm = upload(ctx, MJ, &st);
@@ -805,11 +810,13 @@ sb_status sb_refine_boundaries(sb_context* ctx, const uint8_t* labels, int32_t w
   SB_CUDA(ctx, cudaMemsetAsync(size, 0, N * 4, s));
   SB_CUDA(ctx, cudaMemsetAsync(sh, 0, shist * 4, s));
   SB_CUDA(ctx, cudaMemsetAsync(cut, 0, 64, s));
-  std::vector<CcaJob> CJ{CcaJob{ref, lab, size, sh, rowcnt, cut, boundary, w, h, (int32_t)shist, cc_remove_fraction}};
+  SB_CUDA(ctx, cudaMemsetAsync(rowcnt, 0, (size_t)h * 4, s));
+  std::vector<CcaJob> CJ{CcaJob{ref, lab, size, sh, rowcnt, cut, boundary, roots, w, h, (int32_t)shist,
+                                cc_remove_fraction}};
   const CcaJob* dc = upload(ctx, CJ, &st);
   if (!dc) return st;
   launch_cca(dc, 1, w, h, ctx->dev_err, s);
-  SB_LAUNCHED(ctx, 3);
+  SB_LAUNCHED(ctx, 2);
   launch_cc_filter(dc, 1, w, h, s);
   SB_LAUNCHED(ctx, 6);
   return SB_OK;

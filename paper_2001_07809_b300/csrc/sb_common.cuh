@@ -69,8 +69,9 @@ struct CcaJob {
   uint32_t* size;        // per-root sizes (zeroed before k_cc_count)
   uint32_t* shist;       // size histogram, shist_len entries (zeroed)
   uint32_t* rowcnt;      // h entries
-  int64_t* cut;          // [0] N_b, [1] limit, [2] s*, [3] m, [4] T
+  int64_t* cut;          // [0] N_b, [1] limit, [2] s*, [3] m, [4] T, [5] number of roots
   uint8_t* out;          // filtered boundary map
+  int32_t* roots;        // component roots, appended by k_cc_count (count in cut[5]); room for ceil(w/2) ceil(h/2)
   int32_t w, h;
   int32_t shist_len;
   double frac;
