@@ -17,7 +17,8 @@ are stated in ``sb_oracle.c``):
 * ``cca`` / ``cc_filter``   connected components, 4 % removal (Section III)
 * ``anchor_mask`` / ``boundary_sad``  SAD at boundary pixels (Section III)
 * ``recon_fill``            Algorithm 1
-* ``recon_peek``            Algorithm 2
+* ``recon_peek``            Algorithm 2 (estimates from the map after Algorithm 1)
+* ``recon_peek_inplace``    Algorithm 2, in-place top-down reading
 * ``selective_blur``        Eq. 1 and Eq. 2
 * ``run``                   the whole pipeline in the paper's order
 * ``disp_at_points``        final disparity at chosen pixels, evaluated from
@@ -83,6 +84,7 @@ def lib():
             "or_boundary_sad": ([V, V, V, I, I, I, I, V, V], None),
             "or_recon_fill": ([V, V, I, I], None),
             "or_recon_peek": ([V, I, I, I, I, I, V], None),
+            "or_recon_peek_inplace": ([V, I, I, I, I, I, V], None),
             "or_blur_radius": ([ctypes.c_float], I),
             "or_selective_blur": ([V, V, I, I, V, I, ctypes.c_float, V], None),
             "or_blur_at": ([V, I, I, I, I, ctypes.c_float, V], None),
@@ -231,6 +233,15 @@ def recon_peek(det: np.ndarray, max_disp: int, block: int, threshold: int) -> np
     return out
 
 
+def recon_peek_inplace(det: np.ndarray, max_disp: int, block: int, threshold: int) -> np.ndarray:
+    """Algorithm 2, in-place top-down reading (estimates feed the pixel below)."""
+    det = np.ascontiguousarray(det, np.uint16)
+    h, w = det.shape
+    out = np.empty_like(det)
+    lib().or_recon_peek_inplace(_p(det), w, h, max_disp, block, threshold, _p(out))
+    return out
+
+
 def blur_radius(sigma: float) -> int:
     return int(lib().or_blur_radius(float(sigma)))
 
@@ -308,7 +319,8 @@ def run(left_rgb, right_rgb, p, with_blur: bool = True) -> Result:
     res = run_front(left_rgb, right_rgb, p)
     res.disp_sparse, res.cost = boundary_sad(res.L_left, res.L_right, res.anchor, p.max_disp, p.block)
     res.disp_filled = recon_fill(res.disp_sparse, res.anchor)
-    res.disp = recon_peek(res.disp_filled, p.max_disp, p.block, p.disp_threshold)
+    peek = recon_peek_inplace if getattr(p, "peek_mode", 0) == 1 else recon_peek
+    res.disp = peek(res.disp_filled, p.max_disp, p.block, p.disp_threshold)
     if with_blur:
         res.out_rgb = selective_blur(left_rgb, res.disp, p.ranges, p.sigma)
     return res
@@ -324,6 +336,9 @@ def disp_at_points(front: Result, p, points: Iterable[Tuple[int, int]],
     have equal disparity; Algorithm 2 then needs, per column, the nearest
     pixel above and below that is an anchor or filled.  Both are evaluated
     lazily here with a memo of anchor disparities."""
+    if getattr(p, "peek_mode", 0) != 0:
+        raise NotImplementedError("disp_at_points follows the Algorithm 2 reading that uses the map after "
+                                  "Algorithm 1 (peek_mode 0)")
     Ll, Lr, anc = front.L_left, front.L_right, front.anchor
     h, w = anc.shape
     r = (p.block - 1) // 2

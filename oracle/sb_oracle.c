@@ -410,6 +410,40 @@ void or_recon_peek(const uint16_t* det, int w, int h, int max_disp, int block, i
     }
 }
 
+/* Algorithm 2 ("Peek"), in-place reading: each column of Omega is swept top
+ * down and an estimate is written back before the next pixel is visited, so
+ * the nearest determined pixel above an undetermined one is the pixel just
+ * above it (an anchor, a Fill output or an estimate of this sweep); the
+ * nearest below is the nearest anchor or Fill output below (nothing below
+ * has been estimated yet).  The range test, the floor mean, the single
+ * neighbour and no-neighbour cases and the pixels outside Omega are as in
+ * or_recon_peek. */
+void or_recon_peek_inplace(const uint16_t* det, int w, int h, int max_disp, int block, int threshold,
+                           uint16_t* out) {
+  int r = (block - 1) / 2, x0 = max_disp + r, x1 = w - 1 - r, y0 = r, y1 = h - 1 - r;
+  for (int64_t p = 0; p < (int64_t)w * h; ++p) out[p] = 0;
+  for (int x = x0; x <= x1; ++x) {
+    int above = -1;                       /* the output just above, once there is one */
+    for (int y = y0; y <= y1; ++y) {
+      int64_t p = (int64_t)y * w + x;
+      if (det[p] != OR_UNDET) { out[p] = det[p]; above = det[p]; continue; }
+      int below = -1;
+      for (int yy = y + 1; yy <= y1; ++yy)
+        if (det[(int64_t)yy * w + x] != OR_UNDET) { below = det[(int64_t)yy * w + x]; break; }
+      int v;
+      if (above < 0 && below < 0) v = 0;
+      else if (above < 0) v = below;
+      else if (below < 0) v = above;
+      else {
+        int range = above > below ? above - below : below - above;
+        v = range > threshold ? (above < below ? above : below) : (above + below) / 2;
+      }
+      out[p] = (uint16_t)v;
+      above = v;
+    }
+  }
+}
+
 /* ------------------------------------------------------------------------
  * Depth-based selective blurring (Section III, Eq. 1 and Eq. 2).  The blur
  * map marks every pixel whose disparity lies in no range of interest; those

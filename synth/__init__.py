@@ -220,6 +220,7 @@ class Params:
     morph_mode: int = 0                     # 0 Fill+Remove (paper), 1 open/close
     kmeans_max_iter: int = 100
     cc_remove_fraction: float = 0.04
+    peek_mode: int = 0                      # Algorithm 2: 0 from the map after Algorithm 1, 1 in place
 
 
 def _tint(r: Rng) -> Tuple[int, int, int]:

@@ -360,6 +360,54 @@ def test_algorithm2_hand_columns(golden_dir):
         assert np.array_equal(got, e), tag
 
 
+def test_algorithm2_inplace_paper_columns(golden_dir):
+    for tag, rows in _blocks(os.path.join(golden_dir, "alg2_inplace_columns.txt")):
+        T = int(tag.split("T=")[1])
+        d = dict(rows)
+        col = np.array(_parse_row(d["column"]), np.uint16).reshape(-1, 1)
+        e = np.array(_parse_row(d["expected"]), np.uint16).reshape(-1, 1)
+        got = oracle.recon_peek_inplace(col, 0, 1, T)
+        assert np.array_equal(got, e), tag
+
+
+def test_algorithm2_inplace_properties():
+    # T = -1 (always the minimum): an estimate equals min(above, below) of the
+    # snapshot reading, so both readings agree; for any T the in-place
+    # estimates between two determined pixels move monotonically from the
+    # upper value towards the lower one and stay between them, and the first
+    # one equals the snapshot estimate
+    h, w, D, B = 60, 30, 4, 5
+    r = (B - 1) // 2
+    for trial in range(20):
+        det = np.full((h, w), oracle.UNDET, np.uint16)
+        for x in range(w):
+            k = int(RNG.integers(0, 8))
+            ys = RNG.choice(h, k, replace=False)
+            det[ys, x] = RNG.integers(0, 200, k)
+        assert np.array_equal(oracle.recon_peek_inplace(det, D, B, -1), oracle.recon_peek(det, D, B, -1))
+        T = int(RNG.integers(0, 40))
+        ip, sn = oracle.recon_peek_inplace(det, D, B, T), oracle.recon_peek(det, D, B, T)
+        for x in range(D + r, w - r):
+            ys = [y for y in range(r, h - r) if det[y, x] != oracle.UNDET]
+            for y0, y1 in zip(ys, ys[1:]):
+                a, b = int(det[y0, x]), int(det[y1, x])
+                run = [int(v) for v in ip[y0 + 1:y1, x]]
+                if not run:
+                    continue
+                assert run[0] == int(sn[y0 + 1, x])
+                lo, hi = min(a, b), max(a, b)
+                assert all(lo <= v <= hi for v in run)
+                prev = a
+                for v in run:
+                    assert abs(b - v) <= abs(b - prev)
+                    prev = v
+        outside = np.ones((h, w), bool)
+        outside[r:h - r, D + r:w - r] = False
+        assert np.all(ip[outside] == 0)
+        inside = ~outside & (det != oracle.UNDET)
+        assert np.array_equal(ip[inside], det[inside])
+
+
 def test_algorithm2_threshold_extremes():
     det = np.full((40, 9), oracle.UNDET, np.uint16)
     for x in range(9):
