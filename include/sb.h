@@ -64,6 +64,14 @@ typedef struct {
  * 3x3 opening followed by a 3x3 closing. */
 enum { SB_MORPH_FILL_REMOVE = 0, SB_MORPH_OPEN_CLOSE = 1 };
 
+/* Algorithm 2 (Section III): an undetermined pixel is estimated from the map
+ * after Algorithm 1 (SNAPSHOT, estimates do not feed each other; columns are
+ * independent), or each column is swept top down writing every estimate
+ * back at once (INPLACE: the pixel just above is the "nearest determined
+ * pixel above"; the nearest below is the nearest one determined before the
+ * step).  The paper's wording allows both. */
+enum { SB_PEEK_SNAPSHOT = 0, SB_PEEK_INPLACE = 1 };
+
 /* SAD implementation: chosen per pair on the device from the pair's own
  * boundary-pixel count N_b and a cost model (direct iff N_b * B^2 is small
  * against w * h), exhaustive window sums at each boundary pixel, or running
@@ -83,6 +91,7 @@ typedef struct {
   int32_t n_ranges;           /* 0..SB_MAX_RANGES                                    */
   sb_range ranges[SB_MAX_RANGES];
   int32_t sad_variant;        /* SB_SAD_*                                            */
+  int32_t peek_mode;          /* SB_PEEK_*: reading of Algorithm 2                    */
 } sb_params;
 
 /* Fills p with the defaults: K=10, block 9, threshold 1 (Table 3), Fill/Remove,
@@ -153,10 +162,12 @@ sb_status sb_boundary_sad(sb_context* ctx, const uint8_t* L_left, const uint8_t*
  * undetermined takes, from the nearest determined pixels above and below in
  * its column (inside Omega), the smaller if they differ by more than
  * disp_threshold, else floor of their mean; one neighbour: its value; none: 0.
+ * peek_mode SB_PEEK_SNAPSHOT or SB_PEEK_INPLACE selects the reading of
+ * "nearest determined pixel above" (see the enum).
  * Out: every pixel set; pixels outside Omega are 0.
  * filled: NULL or uint16 h*w out, the map after Algorithm 1 only. */
 sb_status sb_reconstruct_disparity(sb_context* ctx, uint16_t* disp, int32_t w, int32_t h, int32_t max_disp,
-                                   int32_t block, int32_t disp_threshold, uint16_t* filled);
+                                   int32_t block, int32_t disp_threshold, int32_t peek_mode, uint16_t* filled);
 
 /* Depth-based selective blurring (Section III, Eq. 1 and 2): pixels whose
  * disparity lies in none of the ranges get the normalised Gaussian of

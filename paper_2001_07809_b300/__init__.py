@@ -25,6 +25,7 @@ __all__ = [
 SB_OK, SB_ERR_INVALID_ARG, SB_ERR_CUDA, SB_ERR_OOM, SB_ERR_TIMEOUT, SB_ERR_UNSUPPORTED = range(6)
 SB_MORPH_FILL_REMOVE, SB_MORPH_OPEN_CLOSE = 0, 1
 SB_SAD_AUTO, SB_SAD_DIRECT, SB_SAD_BOXSUM = 0, 1, 2
+SB_PEEK_SNAPSHOT, SB_PEEK_INPLACE = 0, 1
 SB_RUN_PLAIN, SB_RUN_BATCHED, SB_RUN_GRAPH, SB_RUN_HOST_IO = 0, 1, 2, 4
 SB_MAX_RANGES = 8
 UNDETERMINED = 0xFFFF
@@ -47,7 +48,7 @@ class sb_params(ctypes.Structure):
                 ("disp_threshold", ctypes.c_int32), ("morph_mode", ctypes.c_int32),
                 ("kmeans_max_iter", ctypes.c_int32), ("cc_remove_fraction", ctypes.c_double),
                 ("sigma", ctypes.c_float), ("n_ranges", ctypes.c_int32), ("ranges", sb_range * SB_MAX_RANGES),
-                ("sad_variant", ctypes.c_int32)]
+                ("sad_variant", ctypes.c_int32), ("peek_mode", ctypes.c_int32)]
 
 
 class sb_pair(ctypes.Structure):
@@ -82,7 +83,7 @@ def _load():
         "sb_kmeans_segment": ([V, V, I32, I32, I32, I32, V, V, V, V], ctypes.c_int),
         "sb_refine_boundaries": ([V, V, I32, I32, I32, ctypes.c_double, V, V, V], ctypes.c_int),
         "sb_boundary_sad": ([V, V, V, V, I32, I32, I32, I32, I32, V, V], ctypes.c_int),
-        "sb_reconstruct_disparity": ([V, V, I32, I32, I32, I32, I32, V], ctypes.c_int),
+        "sb_reconstruct_disparity": ([V, V, I32, I32, I32, I32, I32, I32, V], ctypes.c_int),
         "sb_selective_blur": ([V, V, V, I32, I32, V, I32, ctypes.c_float, V], ctypes.c_int),
         "sb_run": ([V, ctypes.POINTER(sb_pair), I32, U32], ctypes.c_int),
         "sb_profile_enable": ([V, ctypes.c_int], ctypes.c_int),
@@ -119,7 +120,8 @@ def sb_default_params() -> sb_params:
 
 def make_params(k=10, max_disp=64, block=9, disp_threshold=1, morph_mode=SB_MORPH_FILL_REMOVE,
                 kmeans_max_iter=100, cc_remove_fraction=0.04, sigma=3.0,
-                ranges: Sequence[Tuple[int, int]] = (), sad_variant=SB_SAD_AUTO) -> sb_params:
+                ranges: Sequence[Tuple[int, int]] = (), sad_variant=SB_SAD_AUTO,
+                peek_mode=SB_PEEK_SNAPSHOT) -> sb_params:
     p = sb_default_params()
     p.k, p.max_disp, p.block, p.disp_threshold = k, max_disp, block, disp_threshold
     p.morph_mode, p.kmeans_max_iter, p.cc_remove_fraction, p.sigma = morph_mode, kmeans_max_iter, cc_remove_fraction, sigma
@@ -129,6 +131,7 @@ def make_params(k=10, max_disp=64, block=9, disp_threshold=1, morph_mode=SB_MORP
     for i, (lo, hi) in enumerate(ranges):
         p.ranges[i] = sb_range(int(lo), int(hi))
     p.sad_variant = sad_variant
+    p.peek_mode = peek_mode
     return p
 
 
@@ -235,10 +238,11 @@ def sb_boundary_sad(ctx: Context, L_left, L_right, boundary, max_disp: int, bloc
                                      variant, _ptr(disp), _ptr(cost)))
 
 
-def sb_reconstruct_disparity(ctx: Context, disp, max_disp: int, block: int, disp_threshold: int, filled=None):
+def sb_reconstruct_disparity(ctx: Context, disp, max_disp: int, block: int, disp_threshold: int, filled=None,
+                             peek_mode: int = 0):
     h, w = _hw(disp)
     _check(ctx, _lib.sb_reconstruct_disparity(ctx.handle, _ptr(disp), w, h, max_disp, block, disp_threshold,
-                                              _ptr(filled)))
+                                              peek_mode, _ptr(filled)))
 
 
 def sb_selective_blur(ctx: Context, rgb, disp, ranges: Sequence[Tuple[int, int]], sigma: float, out_rgb):

@@ -15,6 +15,11 @@
 // column is cut into segments of seg_rows rows whose first/last determined
 // values are summarised first, so a segment can start its sweeps knowing the
 // nearest determined value beyond each of its ends.
+//
+// Algorithm 2, in-place reading: each column is swept top down and every
+// estimate is written back before the next pixel, so the value above an
+// undetermined pixel is the output just above it; the nearest determined
+// value below is found by an upward pass first.  A thread per column.
 #include "sb_common.cuh"
 
 namespace sb {
@@ -68,6 +73,7 @@ __global__ void __launch_bounds__(256) k_recon_fill(const ReconJob* __restrict__
 // first / last determined value of each (segment, column) inside Omega
 __global__ void __launch_bounds__(128) k_recon_peek_summary(const ReconJob* __restrict__ jobs) {
   const ReconJob J = jobs[blockIdx.z];
+  if (J.inplace) return;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int seg = blockIdx.y;
   const int oy0 = J.r, oy1 = J.h - 1 - J.r;
@@ -88,6 +94,7 @@ __global__ void __launch_bounds__(128) k_recon_peek_summary(const ReconJob* __re
 
 __global__ void __launch_bounds__(128) k_recon_peek_apply(const ReconJob* __restrict__ jobs) {
   const ReconJob J = jobs[blockIdx.z];
+  if (J.inplace) return;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int seg = blockIdx.y;
   const int w = J.w;
@@ -139,12 +146,60 @@ __global__ void __launch_bounds__(128) k_recon_peek_apply(const ReconJob* __rest
   }
 }
 
-void launch_recon(const ReconJob* jobs, int n_jobs, int max_w, int max_h, int max_nseg, cudaStream_t s) {
+__global__ void __launch_bounds__(128) k_recon_peek_inplace(const ReconJob* __restrict__ jobs) {
+  const ReconJob J = jobs[blockIdx.y];
+  if (!J.inplace) return;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = J.w, h = J.h;
+  if (x >= w) return;
+  const int oy0 = J.r, oy1 = h - 1 - J.r, ox0 = J.D + J.r, ox1 = w - 1 - J.r;
+  const bool colin = x >= ox0 && x <= ox1;
+  for (int y = 0; y < h; ++y)
+    if (!colin || y < oy0 || y > oy1) J.out[(int64_t)y * w + x] = 0;
+  if (!colin) return;
+  // upward: the nearest value determined before the step at or below each pixel
+  uint16_t nb = NONE;
+  for (int y = oy1; y >= oy0; --y) {
+    const int64_t p = (int64_t)y * w + x;
+    const uint16_t v = J.filled[p];
+    if (v != NONE) nb = v;
+    J.out[p] = nb;
+  }
+  // downward, in place: the output just above is the value above
+  uint16_t na = NONE;
+  const int T = J.threshold;
+  for (int y = oy0; y <= oy1; ++y) {
+    const int64_t p = (int64_t)y * w + x;
+    const uint16_t v = J.filled[p];
+    if (v != NONE) { na = v; continue; }   // out[p] already holds v
+    const uint16_t b = J.out[p];
+    uint16_t o;
+    if (na == NONE && b == NONE) o = 0;
+    else if (na == NONE) o = b;
+    else if (b == NONE) o = na;
+    else {
+      const int a = na, c = b;
+      const int range = a > c ? a - c : c - a;
+      o = (uint16_t)(range > T ? min(a, c) : (a + c) / 2);
+    }
+    J.out[p] = o;
+    na = o;
+  }
+}
+
+void launch_recon(const ReconJob* jobs, int n_jobs, int max_w, int max_h, int max_nseg, int peek_modes,
+                  cudaStream_t s) {
   if (n_jobs <= 0) return;
   k_recon_fill<<<dim3((max_h + 7) / 8, n_jobs), 256, 0, s>>>(jobs);
-  dim3 g((max_w + 127) / 128, max_nseg, n_jobs);
-  k_recon_peek_summary<<<g, 128, 0, s>>>(jobs);
-  k_recon_peek_apply<<<g, 128, 0, s>>>(jobs);
+  if (peek_modes & 1) {
+    dim3 g((max_w + 127) / 128, max_nseg, n_jobs);
+    k_recon_peek_summary<<<g, 128, 0, s>>>(jobs);
+    k_recon_peek_apply<<<g, 128, 0, s>>>(jobs);
+  }
+  if (peek_modes & 2) k_recon_peek_inplace<<<dim3((max_w + 127) / 128, n_jobs), 128, 0, s>>>(jobs);
 }
+
+// kernels launch_recon issues for the given peek_modes
+int recon_launches(int peek_modes) { return 1 + ((peek_modes & 1) ? 2 : 0) + ((peek_modes & 2) ? 1 : 0); }
 
 }  // namespace sb

@@ -340,6 +340,7 @@ bool params_ok(sb_context* ctx, int w, int h, const sb_params& p, sb_status* st)
   if (!(p.cc_remove_fraction >= 0.0 && p.cc_remove_fraction <= 1.0)) { *st = fail(ctx, SB_ERR_INVALID_ARG, "cc_remove_fraction must be in [0, 1]"); return false; }
   if (p.kmeans_max_iter < 0 || p.kmeans_max_iter > 100000) { *st = fail(ctx, SB_ERR_INVALID_ARG, "kmeans_max_iter must be in [0, 100000]"); return false; }
   if (p.sad_variant < SB_SAD_AUTO || p.sad_variant > SB_SAD_BOXSUM) { *st = fail(ctx, SB_ERR_INVALID_ARG, "unknown sad_variant %d", p.sad_variant); return false; }
+  if (p.peek_mode != SB_PEEK_SNAPSHOT && p.peek_mode != SB_PEEK_INPLACE) { *st = fail(ctx, SB_ERR_INVALID_ARG, "unknown peek_mode %d", p.peek_mode); return false; }
   return true;
 }
 
@@ -572,16 +573,19 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
   // 6. reconstruction (Algorithms 1 and 2)
   {
     std::vector<ReconJob> J;
+    int modes = 0;
     for (auto& r : runs) {
       uint16_t* out = r.out_disp ? r.out_disp : r.ws.disp;
+      const int inplace = r.g.p.peek_mode == SB_PEEK_INPLACE;
+      modes |= inplace ? 2 : 1;
       J.push_back(ReconJob{r.ws.sparse, r.ws.filled, out, r.ws.seg_top, r.ws.seg_bot, r.g.w, r.g.h, r.g.p.max_disp,
-                           (r.g.p.block - 1) / 2, r.g.p.disp_threshold, kSegRows});
+                           (r.g.p.block - 1) / 2, r.g.p.disp_threshold, kSegRows, inplace});
     }
     const ReconJob* d = upload(ctx, J, &st);
     if (!d) return st;
     if (!ctx->dry) {
-      launch_recon(d, n, max_w, max_h, max_nseg, s);
-      SB_LAUNCHED(ctx, 3);
+      launch_recon(d, n, max_w, max_h, max_nseg, modes, s);
+      SB_LAUNCHED(ctx, recon_launches(modes));
     }
   }
   SB_MARK(ctx, SB_STAGE_BLUR);
@@ -635,6 +639,7 @@ void sb_default_params(sb_params* p) {
   p->sigma = 3.0f;
   p->n_ranges = 0;
   p->sad_variant = SB_SAD_AUTO;
+  p->peek_mode = SB_PEEK_SNAPSHOT;
 }
 
 sb_status sb_create(int device, size_t mem_budget_bytes, void* cuda_stream, sb_context** out) {
@@ -875,9 +880,11 @@ sb_status sb_boundary_sad(sb_context* ctx, const uint8_t* L_left, const uint8_t*
 }
 
 sb_status sb_reconstruct_disparity(sb_context* ctx, uint16_t* disp, int32_t w, int32_t h, int32_t max_disp,
-                                   int32_t block, int32_t disp_threshold, uint16_t* filled) {
+                                   int32_t block, int32_t disp_threshold, int32_t peek_mode, uint16_t* filled) {
   if (!ctx) return SB_ERR_INVALID_ARG;
   if (!disp) return fail(ctx, SB_ERR_INVALID_ARG, "reconstruct_disparity: null pointer");
+  if (peek_mode != SB_PEEK_SNAPSHOT && peek_mode != SB_PEEK_INPLACE)
+    return fail(ctx, SB_ERR_INVALID_ARG, "unknown peek_mode %d", peek_mode);
   sb_status st = SB_OK;
   if (!geometry_ok(ctx, w, h, max_disp, block, &st)) return st;
   const size_t N = (size_t)w * h;
@@ -887,11 +894,13 @@ sb_status sb_reconstruct_disparity(sb_context* ctx, uint16_t* disp, int32_t w, i
   uint16_t* fl = filled ? filled : (uint16_t*)ctx->ws;
   uint16_t* top = (uint16_t*)(ctx->ws + al(N * 2));
   uint16_t* bot = (uint16_t*)(ctx->ws + al(N * 2) + al((size_t)nseg * w * 2));
-  std::vector<ReconJob> J{ReconJob{disp, fl, disp, top, bot, w, h, max_disp, (block - 1) / 2, disp_threshold, kSegRows}};
+  const int inplace = peek_mode == SB_PEEK_INPLACE;
+  std::vector<ReconJob> J{ReconJob{disp, fl, disp, top, bot, w, h, max_disp, (block - 1) / 2, disp_threshold, kSegRows,
+                                   inplace}};
   const ReconJob* d = upload(ctx, J, &st);
   if (!d) return st;
-  launch_recon(d, 1, w, h, nseg, ctx->stream);
-  SB_LAUNCHED(ctx, 3);
+  launch_recon(d, 1, w, h, nseg, inplace ? 2 : 1, ctx->stream);
+  SB_LAUNCHED(ctx, recon_launches(inplace ? 2 : 1));
   return SB_OK;
 }
 

@@ -146,8 +146,12 @@ struct ReconJob {
   uint16_t* seg_top;       // nseg * w
   uint16_t* seg_bot;       // nseg * w
   int32_t w, h, D, r, threshold, seg_rows;
+  int32_t inplace;         // Algorithm 2 reading: 0 snapshot, 1 in-place top-down sweep
 };
-void launch_recon(const ReconJob* jobs, int n_jobs, int max_w, int max_h, int max_nseg, cudaStream_t s);
+// peek_modes: bit 0 = some job uses the snapshot reading, bit 1 = some job the in-place one
+void launch_recon(const ReconJob* jobs, int n_jobs, int max_w, int max_h, int max_nseg, int peek_modes,
+                  cudaStream_t s);
+int recon_launches(int peek_modes);
 
 // --------------------------------------------------------------------- blur
 struct BlurJob {

@@ -61,11 +61,11 @@ def sad(ctx, Ll, Lr, bmap, D, B, variant):
     return host(disp, np.uint16), host(cost, np.uint32)
 
 
-def recon(ctx, sparse: np.ndarray, D, B, T):
+def recon(ctx, sparse: np.ndarray, D, B, T, peek_mode=0):
     h, w = sparse.shape
     d = dev(sparse.astype(np.uint16))
     filled = empty((h, w), np.uint16)
-    sb.sb_reconstruct_disparity(ctx, d, D, B, T, filled)
+    sb.sb_reconstruct_disparity(ctx, d, D, B, T, filled, peek_mode)
     return host(filled, np.uint16), host(d, np.uint16)
 
 
@@ -79,7 +79,7 @@ def params_of(p, sad_variant=sb.SB_SAD_AUTO):
     return sb.make_params(k=p.k, max_disp=p.max_disp, block=p.block, disp_threshold=p.disp_threshold,
                           morph_mode=p.morph_mode, kmeans_max_iter=p.kmeans_max_iter,
                           cc_remove_fraction=p.cc_remove_fraction, sigma=p.sigma, ranges=p.ranges,
-                          sad_variant=sad_variant)
+                          sad_variant=sad_variant, peek_mode=getattr(p, "peek_mode", 0))
 
 
 def run_pairs(ctx, items, flags, sad_variant=sb.SB_SAD_AUTO):

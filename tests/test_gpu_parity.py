@@ -216,17 +216,36 @@ def test_batched_auto_mixes_variants_per_pair(ctx):
 # ------------------------------------------------------------ reconstruction
 @pytest.mark.parametrize("h,w,D,B,T", [(50, 80, 4, 3, 1), (130, 140, 10, 5, 0), (200, 333, 20, 9, 3),
                                        (257, 64, 0, 1, -1), (300, 50, 8, 7, 1000)])
-def test_recon_bit_exact(ctx, h, w, D, B, T):
+@pytest.mark.parametrize("peek_mode", [sb.SB_PEEK_SNAPSHOT, sb.SB_PEEK_INPLACE])
+def test_recon_bit_exact(ctx, h, w, D, B, T, peek_mode):
     bmap = (RNG.random((h, w)) < 0.15).astype(np.uint8)
     anchor = oracle.anchor_mask(bmap, D, B)
     sparse = np.full((h, w), oracle.UNDET, np.uint16)
-    vals = RNG.integers(0, 6, (h, w)).astype(np.uint16)      # few values -> many equal neighbours
+    vals = RNG.integers(0, 6 if T < 100 else 200, (h, w)).astype(np.uint16)   # few values: many equal neighbours
     sparse[anchor == 1] = vals[anchor == 1]
-    filled, final = recon(ctx, sparse, D, B, T)
+    filled, final = recon(ctx, sparse, D, B, T, peek_mode)
     o_filled = oracle.recon_fill(sparse, anchor)
-    o_final = oracle.recon_peek(o_filled, D, B, T)
+    peek = oracle.recon_peek_inplace if peek_mode == sb.SB_PEEK_INPLACE else oracle.recon_peek
+    o_final = peek(o_filled, D, B, T)
     assert np.array_equal(filled, o_filled)
     assert np.array_equal(final, o_final)
+
+
+def test_recon_inplace_golden_columns(ctx, golden_dir):
+    import os
+    from test_oracle_pins import _blocks, _parse_row
+    for tag, rows in _blocks(os.path.join(golden_dir, "alg2_inplace_columns.txt")):
+        T = int(tag.split("T=")[1])
+        d = dict(rows)
+        col = np.array(_parse_row(d["column"]), np.uint16)
+        e = np.array(_parse_row(d["expected"]), np.uint16)
+        # D = 0, block 1: Omega is the whole image; the column sits beside an
+        # empty one (the smallest legal width), so Algorithm 1 changes nothing
+        img = np.full((len(col), 2), oracle.UNDET, np.uint16)
+        img[:, 0] = col
+        _, final = recon(ctx, img, 0, 1, T, sb.SB_PEEK_INPLACE)
+        assert np.array_equal(final[:, 0], e), tag
+        assert np.all(final[:, 1] == 0), tag
 
 
 def test_recon_paper_rows_and_columns(ctx, golden_dir):
@@ -312,6 +331,21 @@ def test_pipeline_ragged_and_open_close(ctx):
                          morph_mode=mode)
         (o_rgb, o_disp), = run_pairs(ctx, [(left, right, p)], sb.SB_RUN_PLAIN)
         _compare_full(o_rgb, o_disp, left, right, p)
+
+
+def test_pipeline_inplace_peek_and_mixed_batch(ctx):
+    # the in-place reading of Algorithm 2 through the whole pipeline, and a
+    # batch mixing both readings (one launch per kernel, each job picks its own)
+    sc, p, _ = synth.workload("c1")
+    left, right, _ = sc.render()
+    import dataclasses
+    p_ip = dataclasses.replace(p, peek_mode=1)
+    (rgb_ip, disp_ip), = run_pairs(ctx, [(left, right, p_ip)], sb.SB_RUN_PLAIN)
+    _compare_full(rgb_ip, disp_ip, left, right, p_ip)
+    mixed = run_pairs(ctx, [(left, right, p), (left, right, p_ip)], sb.SB_RUN_BATCHED | sb.SB_RUN_GRAPH)
+    (rgb_sn, disp_sn), = run_pairs(ctx, [(left, right, p)], sb.SB_RUN_PLAIN)
+    assert np.array_equal(mixed[0][1], disp_sn) and np.array_equal(mixed[0][0], rgb_sn)
+    assert np.array_equal(mixed[1][1], disp_ip) and np.array_equal(mixed[1][0], rgb_ip)
 
 
 def test_batched_and_graph_equal_plain_on_uneven_batch(ctx):
