@@ -527,6 +527,67 @@ def run_ours(args):
     return 0
 
 
+def bad_pixel_percent(disp, gt, mask, delta=1.0):
+    """Eq. 3: the percentage of pixels inside ``mask`` whose disparity differs
+    from the ground truth by more than delta (the evaluation, not the method)."""
+    import numpy as np
+    err = np.abs(disp.astype(np.float64) - gt.astype(np.float64)) > delta
+    return 100.0 * float(err[mask].sum()) / max(int(mask.sum()), 1)
+
+
+def run_accuracy(args):
+    """Eq. 3 bad-pixel % against the generator's ground truth over the domain,
+    for the readings the paper leaves open, one at a time from the defaults:
+    Algorithm 2's threshold T and its in-place reading, the share of boundary
+    pixels dropped as small components, the refinement mode and K.  The GPU
+    pipeline computes every map; one JSON line with the table."""
+    import dataclasses
+    import numpy as np
+    import torch
+    import synth
+    import paper_2001_07809_b300 as sb
+    torch.cuda.set_device(0)
+    ctx = sb.Context(0)
+    cases = [("c1", 0), ("c2", 0), ("c3", 0)]
+    variants = [("default", {}), ("T=0", {"disp_threshold": 0}), ("T=4", {"disp_threshold": 4}),
+                ("T=16", {"disp_threshold": 16}), ("peek in place", {"peek_mode": 1}),
+                ("T=16, peek in place", {"disp_threshold": 16, "peek_mode": 1}),
+                ("no small-component removal", {"cc_remove_fraction": 0.0}),
+                ("remove 10 %", {"cc_remove_fraction": 0.10}), ("open/close", {"morph_mode": 1}),
+                ("K-2", "k-2"), ("K+4", "k+4")]
+    table = {}
+    for name, index in cases:
+        sc, p0, frame = synth.workload(name, index)
+        left, right, gt = sc.render(frame=frame)
+        r = (p0.block - 1) // 2
+        h, w = gt.shape
+        mask = np.zeros((h, w), bool)
+        mask[r:h - r, p0.max_disp + r:w - r] = True
+        dl, dr = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+        row = {}
+        for vname, ch in variants:
+            if ch == "k-2":
+                p = dataclasses.replace(p0, k=max(2, p0.k - 2))
+            elif ch == "k+4":
+                p = dataclasses.replace(p0, k=p0.k + 4)
+            else:
+                p = dataclasses.replace(p0, **ch)
+            params = sb.make_params(k=p.k, max_disp=p.max_disp, block=p.block, disp_threshold=p.disp_threshold,
+                                    morph_mode=p.morph_mode, cc_remove_fraction=p.cc_remove_fraction,
+                                    sigma=p.sigma, ranges=p.ranges, peek_mode=p.peek_mode)
+            o = torch.empty_like(dl)
+            d = torch.empty((h, w), dtype=torch.int16, device="cuda")
+            sb.sb_run(ctx, [sb.Pair(dl, dr, params, o, d)], sb.SB_RUN_PLAIN)
+            ctx.synchronize()
+            disp = d.cpu().numpy().view(np.uint16)
+            row[vname] = round(bad_pixel_percent(disp, gt, mask), 3)
+        table["%s %dx%d D=%d B=%d K=%d" % (name, w, h, p0.max_disp, p0.block, p0.k)] = row
+    ctx.close()
+    print(json.dumps({"study": "Eq. 3 bad-pixel % (|d - gt| > 1) over the domain, synthetic ground truth",
+                      "data": "synthetic", "table": table}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -537,7 +598,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--accuracy", action="store_true", help="Eq. 3 study of the open readings, then exit")
     args = ap.parse_args()
+    if args.accuracy:
+        return run_accuracy(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
