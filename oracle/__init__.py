@@ -85,6 +85,8 @@ def lib():
             "or_recon_fill": ([V, V, I, I], None),
             "or_recon_peek": ([V, I, I, I, I, I, V], None),
             "or_recon_peek_inplace": ([V, I, I, I, I, I, V], None),
+            "or_sad_argmin_right": ([V, V, I, I, I, I, I, V], ctypes.c_int),
+            "or_lr_consistency": ([V, V, I, I, I, V], ctypes.c_int64),
             "or_blur_radius": ([ctypes.c_float], I),
             "or_selective_blur": ([V, V, I, I, V, I, ctypes.c_float, V], None),
             "or_blur_at": ([V, I, I, I, I, ctypes.c_float, V], None),
@@ -205,6 +207,25 @@ def sad_argmin(Ll: np.ndarray, Lr: np.ndarray, x: int, y: int, max_disp: int, bl
     return int(d), int(c.value)
 
 
+def sad_argmin_right(Ll: np.ndarray, Lr: np.ndarray, x: int, y: int, max_disp: int, block: int) -> Tuple[int, int]:
+    """Right-referenced SAD argmin at right-image pixel (x, y), written out directly."""
+    Ll = np.ascontiguousarray(Ll, np.uint8)
+    Lr = np.ascontiguousarray(Lr, np.uint8)
+    c = ctypes.c_uint32(0)
+    d = lib().or_sad_argmin_right(_p(Ll), _p(Lr), Ll.shape[1], x, y, max_disp, block, ctypes.byref(c))
+    return int(d), int(c.value)
+
+
+def lr_consistency(dL: np.ndarray, dR: np.ndarray, tol: int = 1):
+    """-> (ok uint8 map, number of consistent pixels) of a left- and a right-referenced map."""
+    dL = np.ascontiguousarray(dL, np.uint16)
+    dR = np.ascontiguousarray(dR, np.uint16)
+    h, w = dL.shape
+    ok = np.empty((h, w), np.uint8)
+    n = lib().or_lr_consistency(_p(dL), _p(dR), w, h, tol, _p(ok))
+    return ok, int(n)
+
+
 def boundary_sad(Ll, Lr, anchor, max_disp: int, block: int):
     """-> (disp uint16 with UNDET off the anchors, cost uint32 (0 off anchors))."""
     Ll = np.ascontiguousarray(Ll, np.uint8)
@@ -315,7 +336,24 @@ def run_front(left_rgb, right_rgb, p) -> Result:
 
 
 def run(left_rgb, right_rgb, p, with_blur: bool = True) -> Result:
-    """The whole pipeline of Section III in the paper's order."""
+    """The whole pipeline of Section III in the paper's order.  With
+    ``p.view == 1`` the right image is the reference: the method runs on the
+    horizontally mirrored pair with the roles swapped (the mirrored right
+    image matched against the mirrored left one, disparities still >= 0), and
+    ``disp`` / ``out_rgb`` are mirrored back: the right image's disparity map
+    and its selectively blurred copy.  The intermediate maps stay mirrored."""
+    if getattr(p, "view", 0) == 1:
+        left_m = np.ascontiguousarray(left_rgb[:, ::-1])
+        right_m = np.ascontiguousarray(right_rgb[:, ::-1])
+        res = _run_left(right_m, left_m, p, with_blur=False)
+        res.disp = np.ascontiguousarray(res.disp[:, ::-1])
+        if with_blur:
+            res.out_rgb = selective_blur(right_rgb, res.disp, p.ranges, p.sigma)
+        return res
+    return _run_left(left_rgb, right_rgb, p, with_blur)
+
+
+def _run_left(left_rgb, right_rgb, p, with_blur: bool = True) -> Result:
     res = run_front(left_rgb, right_rgb, p)
     res.disp_sparse, res.cost = boundary_sad(res.L_left, res.L_right, res.anchor, p.max_disp, p.block)
     res.disp_filled = recon_fill(res.disp_sparse, res.anchor)
@@ -336,6 +374,8 @@ def disp_at_points(front: Result, p, points: Iterable[Tuple[int, int]],
     have equal disparity; Algorithm 2 then needs, per column, the nearest
     pixel above and below that is an anchor or filled.  Both are evaluated
     lazily here with a memo of anchor disparities."""
+    if getattr(p, "view", 0) != 0:
+        raise NotImplementedError("disp_at_points evaluates the left view")
     if getattr(p, "peek_mode", 0) != 0:
         raise NotImplementedError("disp_at_points follows the Algorithm 2 reading that uses the map after "
                                   "Algorithm 1 (peek_mode 0)")

@@ -345,6 +345,48 @@ int or_sad_argmin(const uint8_t* Ll, const uint8_t* Lr, int w, int x, int y, int
   return best;
 }
 
+/* Right-referenced SAD at right-image pixel (x, y), written out directly:
+ * argmin over d of sum |L_R(y+i, x+j) - L_L(y+i, x+j+d)|, ties to the
+ * smallest d (Section III states the method for either image of the pair).
+ * Used to check the mirrored right view. */
+int or_sad_argmin_right(const uint8_t* Ll, const uint8_t* Lr, int w, int x, int y, int max_disp, int block,
+                        uint32_t* cost) {
+  int r = (block - 1) / 2, best = 0;
+  uint32_t bc = 0xFFFFFFFFu;
+  for (int d = 0; d <= max_disp; ++d) {
+    uint32_t c = 0;
+    for (int i = -r; i <= r; ++i)
+      for (int j = -r; j <= r; ++j) {
+        int a = Lr[(int64_t)(y + i) * w + (x + j)], b = Ll[(int64_t)(y + i) * w + (x + j + d)];
+        c += (uint32_t)(a > b ? a - b : b - a);
+      }
+    if (c < bc) { bc = c; best = d; }
+  }
+  if (cost) *cost = bc;
+  return best;
+}
+
+/* Left-right consistency of a left-referenced map dL and a right-referenced
+ * map dR (both as the pipeline outputs them): left pixel (x, y) is consistent
+ * when its match x - dL lies inside the image and the right map's disparity
+ * there differs from dL by at most tol.  ok[p] = 1 or 0; returns the number
+ * of consistent pixels. */
+int64_t or_lr_consistency(const uint16_t* dL, const uint16_t* dR, int w, int h, int tol, uint8_t* ok) {
+  int64_t n = 0;
+  for (int y = 0; y < h; ++y)
+    for (int x = 0; x < w; ++x) {
+      int64_t p = (int64_t)y * w + x;
+      int dl = dL[p], xr = x - dl, v = 0;
+      if (xr >= 0) {
+        int dr = dR[(int64_t)y * w + xr];
+        v = (dl > dr ? dl - dr : dr - dl) <= tol;
+      }
+      ok[p] = (uint8_t)v;
+      n += v;
+    }
+  return n;
+}
+
 /* Partial disparity map: d* at every anchor, OR_UNDET elsewhere.  cost may be NULL. */
 void or_boundary_sad(const uint8_t* Ll, const uint8_t* Lr, const uint8_t* anchor, int w, int h, int max_disp,
                      int block, uint16_t* disp, uint32_t* cost) {

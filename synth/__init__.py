@@ -221,6 +221,7 @@ class Params:
     kmeans_max_iter: int = 100
     cc_remove_fraction: float = 0.04
     peek_mode: int = 0                      # Algorithm 2: 0 from the map after Algorithm 1, 1 in place
+    view: int = 0                           # reference image: 0 left (paper's figures), 1 right
 
 
 def _tint(r: Rng) -> Tuple[int, int, int]:

@@ -14,6 +14,7 @@ import pytest
 import scipy.ndimage as ndi
 
 import oracle
+import synth
 
 RNG = np.random.default_rng(12345)
 
@@ -493,3 +494,35 @@ def test_blur_impulse_response_is_kernel():
     assert np.array_equal(out[c - R:c + R + 1, c - R:c + R + 1, 0], want.astype(np.uint8))
     for y, x in ((c, c), (c - 3, c + 1)):
         assert np.array_equal(oracle.blur_at(img, x, y, sigma), out[y, x])
+
+
+def test_right_view_matches_direct_right_referenced_sad():
+    # the right view runs the method on the mirrored, swapped pair; its SAD
+    # at every anchor must equal the right-referenced SAD written out directly
+    # (argmin_d sum |R(x+j) - L(x+j+d)|) at the mirrored position
+    import dataclasses
+    sc, p, _ = synth.workload("c1")
+    left, right, _ = sc.render()
+    left, right = left[:64, :160].copy(), right[:64, :160].copy()
+    p = dataclasses.replace(p, max_disp=12, block=5, view=1)
+    res = oracle.run(left, right, p, with_blur=False)
+    Ll, Lr = oracle.rgb_to_lightness(left), oracle.rgb_to_lightness(right)
+    h, w = Ll.shape
+    ys, xs = np.nonzero(res.anchor)
+    assert len(ys) > 50
+    for i in RNG.choice(len(ys), 60, replace=False):
+        y, xm = int(ys[i]), int(xs[i])
+        d, c = oracle.sad_argmin_right(Ll, Lr, w - 1 - xm, y, p.max_disp, p.block)
+        assert (int(res.disp_sparse[y, xm]), int(res.cost[y, xm])) == (d, c)
+    assert res.disp.shape == (h, w) and np.all(res.disp[:, w - p.max_disp - 2:] == 0)
+
+
+def test_lr_consistency_hand_worked_row():
+    # one row, worked by hand: left pixel x matches right pixel x - dL[x]
+    dL = np.array([[0, 1, 2, 2, 5, 1]], np.uint16)
+    dR = np.array([[0, 1, 2, 1, 0, 0]], np.uint16)
+    ok0, n0 = oracle.lr_consistency(dL, dR, 0)
+    ok1, n1 = oracle.lr_consistency(dL, dR, 1)
+    assert ok0.tolist() == [[1, 0, 0, 0, 0, 0]] and n0 == 1
+    assert ok1.tolist() == [[1, 1, 0, 1, 0, 1]] and n1 == 4
+
