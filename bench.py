@@ -581,6 +581,23 @@ def run_accuracy(args):
             ctx.synchronize()
             disp = d.cpu().numpy().view(np.uint16)
             row[vname] = round(bad_pixel_percent(disp, gt, mask), 3)
+            if vname == "default":
+                disp_left = d
+        # both views and the left-right check: the share of the domain that is
+        # consistent, and the bad-pixel % inside and outside that share
+        params_r = sb.make_params(k=p0.k, max_disp=p0.max_disp, block=p0.block, disp_threshold=p0.disp_threshold,
+                                  sigma=p0.sigma, ranges=p0.ranges, view=sb.SB_VIEW_RIGHT)
+        o = torch.empty_like(dl)
+        d_r = torch.empty((h, w), dtype=torch.int16, device="cuda")
+        sb.sb_run(ctx, [sb.Pair(dl, dr, params_r, o, d_r)], sb.SB_RUN_PLAIN)
+        ok = torch.empty((h, w), dtype=torch.uint8, device="cuda")
+        sb.sb_lr_consistency(ctx, disp_left, d_r, ok, 1)
+        ctx.synchronize()
+        okm = ok.cpu().numpy().astype(bool) & mask
+        dleft = disp_left.cpu().numpy().view(np.uint16)
+        row["LR-consistent share of the domain (tol 1)"] = round(100.0 * okm.sum() / mask.sum(), 3)
+        row["bad % where consistent"] = round(bad_pixel_percent(dleft, gt, okm), 3)
+        row["bad % where inconsistent"] = round(bad_pixel_percent(dleft, gt, mask & ~okm), 3)
         table["%s %dx%d D=%d B=%d K=%d" % (name, w, h, p0.max_disp, p0.block, p0.k)] = row
     ctx.close()
     print(json.dumps({"study": "Eq. 3 bad-pixel % (|d - gt| > 1) over the domain, synthetic ground truth",

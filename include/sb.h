@@ -72,6 +72,13 @@ enum { SB_MORPH_FILL_REMOVE = 0, SB_MORPH_OPEN_CLOSE = 1 };
  * step).  The paper's wording allows both. */
 enum { SB_PEEK_SNAPSHOT = 0, SB_PEEK_INPLACE = 1 };
 
+/* Reference image (Section III states the method for the left or the right
+ * image).  RIGHT: the disparity map and the blurred output are the right
+ * image's; pixel (x, y) of the right image is matched against (x + d, y) of
+ * the left one, and the domain is rows [r, h-1-r] x columns [r, w-1-r-D].
+ * The library runs the method on the mirrored pair with the roles swapped. */
+enum { SB_VIEW_LEFT = 0, SB_VIEW_RIGHT = 1 };
+
 /* SAD implementation: chosen per pair on the device from the pair's own
  * boundary-pixel count N_b and a cost model (direct iff N_b * B^2 is small
  * against w * h), exhaustive window sums at each boundary pixel, or running
@@ -92,6 +99,7 @@ typedef struct {
   sb_range ranges[SB_MAX_RANGES];
   int32_t sad_variant;        /* SB_SAD_*                                            */
   int32_t peek_mode;          /* SB_PEEK_*: reading of Algorithm 2                    */
+  int32_t view;               /* SB_VIEW_*: the reference image of the pair           */
 } sb_params;
 
 /* Fills p with the defaults: K=10, block 9, threshold 1 (Table 3), Fill/Remove,
@@ -218,6 +226,16 @@ sb_status sb_run(sb_context* ctx, const sb_pair* pairs, int32_t n_pairs, uint32_
 sb_status sb_boundary_sad_static(const uint8_t* L_left, const uint8_t* L_right, const uint8_t* boundary, int32_t w,
                                  int32_t h, int32_t max_disp, int32_t block, int32_t variant, uint16_t* disp,
                                  uint32_t* cost, void* cuda_stream, char* errbuf, size_t errbuf_len);
+
+/* Left-right consistency of a left-view disparity map dL and a right-view map
+ * dR of the same pair (both uint16 h*w device arrays as sb_run writes them):
+ * ok[p] = 1 when left pixel p = (x, y) matches x - dL[p] inside the image and
+ * |dL[p] - dR[y][x - dL[p]]| <= tol, else 0 (ok: uint8 h*w device array).
+ * count: NULL or one device int64 that receives the number of consistent
+ * pixels (overwritten).  The method itself has no occlusion handling; this
+ * only reports agreement. */
+sb_status sb_lr_consistency(sb_context* ctx, const uint16_t* dL, const uint16_t* dR, int32_t w, int32_t h,
+                            int32_t tol, uint8_t* ok, int64_t* count);
 
 /* Number of kernel launches the library has issued on this context so far
  * (a graph replay counts every kernel node it runs). */

@@ -18,6 +18,7 @@ __all__ = [
     "SbError", "Context", "Pair", "sb_default_params", "make_params", "sb_create", "sb_destroy",
     "sb_rgb_to_lightness", "sb_kmeans_segment", "sb_refine_boundaries", "sb_boundary_sad",
     "sb_reconstruct_disparity", "sb_selective_blur", "sb_run", "sb_synchronize", "sb_launch_count",
+    "sb_lr_consistency", "SB_PEEK_SNAPSHOT", "SB_PEEK_INPLACE", "SB_VIEW_LEFT", "SB_VIEW_RIGHT",
     "SB_RUN_PLAIN", "SB_RUN_BATCHED", "SB_RUN_GRAPH", "SB_RUN_HOST_IO", "SB_SAD_AUTO", "SB_SAD_DIRECT",
     "SB_SAD_BOXSUM", "SB_MORPH_FILL_REMOVE", "SB_MORPH_OPEN_CLOSE", "UNDETERMINED", "library_path",
 ]
@@ -26,6 +27,7 @@ SB_OK, SB_ERR_INVALID_ARG, SB_ERR_CUDA, SB_ERR_OOM, SB_ERR_TIMEOUT, SB_ERR_UNSUP
 SB_MORPH_FILL_REMOVE, SB_MORPH_OPEN_CLOSE = 0, 1
 SB_SAD_AUTO, SB_SAD_DIRECT, SB_SAD_BOXSUM = 0, 1, 2
 SB_PEEK_SNAPSHOT, SB_PEEK_INPLACE = 0, 1
+SB_VIEW_LEFT, SB_VIEW_RIGHT = 0, 1
 SB_RUN_PLAIN, SB_RUN_BATCHED, SB_RUN_GRAPH, SB_RUN_HOST_IO = 0, 1, 2, 4
 SB_MAX_RANGES = 8
 UNDETERMINED = 0xFFFF
@@ -48,7 +50,7 @@ class sb_params(ctypes.Structure):
                 ("disp_threshold", ctypes.c_int32), ("morph_mode", ctypes.c_int32),
                 ("kmeans_max_iter", ctypes.c_int32), ("cc_remove_fraction", ctypes.c_double),
                 ("sigma", ctypes.c_float), ("n_ranges", ctypes.c_int32), ("ranges", sb_range * SB_MAX_RANGES),
-                ("sad_variant", ctypes.c_int32), ("peek_mode", ctypes.c_int32)]
+                ("sad_variant", ctypes.c_int32), ("peek_mode", ctypes.c_int32), ("view", ctypes.c_int32)]
 
 
 class sb_pair(ctypes.Structure):
@@ -84,6 +86,7 @@ def _load():
         "sb_refine_boundaries": ([V, V, I32, I32, I32, ctypes.c_double, V, V, V], ctypes.c_int),
         "sb_boundary_sad": ([V, V, V, V, I32, I32, I32, I32, I32, V, V], ctypes.c_int),
         "sb_reconstruct_disparity": ([V, V, I32, I32, I32, I32, I32, I32, V], ctypes.c_int),
+        "sb_lr_consistency": ([V, V, V, I32, I32, I32, V, V], ctypes.c_int),
         "sb_selective_blur": ([V, V, V, I32, I32, V, I32, ctypes.c_float, V], ctypes.c_int),
         "sb_run": ([V, ctypes.POINTER(sb_pair), I32, U32], ctypes.c_int),
         "sb_profile_enable": ([V, ctypes.c_int], ctypes.c_int),
@@ -121,7 +124,7 @@ def sb_default_params() -> sb_params:
 def make_params(k=10, max_disp=64, block=9, disp_threshold=1, morph_mode=SB_MORPH_FILL_REMOVE,
                 kmeans_max_iter=100, cc_remove_fraction=0.04, sigma=3.0,
                 ranges: Sequence[Tuple[int, int]] = (), sad_variant=SB_SAD_AUTO,
-                peek_mode=SB_PEEK_SNAPSHOT) -> sb_params:
+                peek_mode=SB_PEEK_SNAPSHOT, view=SB_VIEW_LEFT) -> sb_params:
     p = sb_default_params()
     p.k, p.max_disp, p.block, p.disp_threshold = k, max_disp, block, disp_threshold
     p.morph_mode, p.kmeans_max_iter, p.cc_remove_fraction, p.sigma = morph_mode, kmeans_max_iter, cc_remove_fraction, sigma
@@ -132,6 +135,7 @@ def make_params(k=10, max_disp=64, block=9, disp_threshold=1, morph_mode=SB_MORP
         p.ranges[i] = sb_range(int(lo), int(hi))
     p.sad_variant = sad_variant
     p.peek_mode = peek_mode
+    p.view = view
     return p
 
 
@@ -243,6 +247,15 @@ def sb_reconstruct_disparity(ctx: Context, disp, max_disp: int, block: int, disp
     h, w = _hw(disp)
     _check(ctx, _lib.sb_reconstruct_disparity(ctx.handle, _ptr(disp), w, h, max_disp, block, disp_threshold,
                                               peek_mode, _ptr(filled)))
+
+
+def sb_lr_consistency(ctx: Context, disp_left, disp_right, ok, tol: int = 1, count=None):
+    """Left-right consistency of a left-view and a right-view disparity map
+    (device uint16/int16 [h, w]); ok: device uint8 [h, w]; count: None or a
+    device int64 tensor of one element."""
+    h, w = _hw(disp_left)
+    _check(ctx, _lib.sb_lr_consistency(ctx.handle, _ptr(disp_left), _ptr(disp_right), w, h, tol, _ptr(ok),
+                                       _ptr(count)))
 
 
 def sb_selective_blur(ctx: Context, rgb, disp, ranges: Sequence[Tuple[int, int]], sigma: float, out_rgb):

@@ -20,12 +20,17 @@
 // estimate is written back before the next pixel, so the value above an
 // undetermined pixel is the output just above it; the nearest determined
 // value below is found by an upward pass first.  A thread per column.
+#include <algorithm>
 #include "sb_common.cuh"
 
 namespace sb {
 
 namespace {
 constexpr uint16_t NONE = SB_UNDET16;
+// the final map's entry for (y, x) of the working orientation
+__device__ __forceinline__ uint16_t& out_at(const ReconJob& J, int y, int x) {
+  return J.out[(int64_t)y * J.w + (J.mirror ? J.w - 1 - x : x)];
+}
 }
 
 __global__ void __launch_bounds__(256) k_recon_fill(const ReconJob* __restrict__ jobs) {
@@ -106,7 +111,7 @@ __global__ void __launch_bounds__(128) k_recon_peek_apply(const ReconJob* __rest
   const int ya = max(sa, oy0), yb = min(sb, oy1);
   // rows of the segment outside Omega (or whole column outside) are 0
   for (int y = sa; y <= sb; ++y)
-    if (!colin || y < oy0 || y > oy1) J.out[(int64_t)y * w + x] = 0;
+    if (!colin || y < oy0 || y > oy1) out_at(J, y, x) = 0;
   if (!colin || ya > yb) return;
   uint16_t above = NONE, below = NONE;
   for (int s = seg - 1; s >= 0; --s) {
@@ -123,7 +128,7 @@ __global__ void __launch_bounds__(128) k_recon_peek_apply(const ReconJob* __rest
     const int64_t p = (int64_t)y * w + x;
     const uint16_t v = J.filled[p];
     if (v != NONE) nb = v;
-    J.out[p] = v != NONE ? v : nb;
+    out_at(J, y, x) = v != NONE ? v : nb;
   }
   // downward sweep: combine with the nearest determined value above
   uint16_t na = above;
@@ -132,7 +137,7 @@ __global__ void __launch_bounds__(128) k_recon_peek_apply(const ReconJob* __rest
     const int64_t p = (int64_t)y * w + x;
     const uint16_t v = J.filled[p];
     if (v != NONE) { na = v; continue; }
-    const uint16_t b = J.out[p];
+    const uint16_t b = out_at(J, y, x);
     uint16_t o;
     if (na == NONE && b == NONE) o = 0;
     else if (na == NONE) o = b;
@@ -142,7 +147,7 @@ __global__ void __launch_bounds__(128) k_recon_peek_apply(const ReconJob* __rest
       const int range = a > c ? a - c : c - a;
       o = (uint16_t)(range > T ? min(a, c) : (a + c) / 2);
     }
-    J.out[p] = o;
+    out_at(J, y, x) = o;
   }
 }
 
@@ -155,7 +160,7 @@ __global__ void __launch_bounds__(128) k_recon_peek_inplace(const ReconJob* __re
   const int oy0 = J.r, oy1 = h - 1 - J.r, ox0 = J.D + J.r, ox1 = w - 1 - J.r;
   const bool colin = x >= ox0 && x <= ox1;
   for (int y = 0; y < h; ++y)
-    if (!colin || y < oy0 || y > oy1) J.out[(int64_t)y * w + x] = 0;
+    if (!colin || y < oy0 || y > oy1) out_at(J, y, x) = 0;
   if (!colin) return;
   // upward: the nearest value determined before the step at or below each pixel
   uint16_t nb = NONE;
@@ -163,7 +168,7 @@ __global__ void __launch_bounds__(128) k_recon_peek_inplace(const ReconJob* __re
     const int64_t p = (int64_t)y * w + x;
     const uint16_t v = J.filled[p];
     if (v != NONE) nb = v;
-    J.out[p] = nb;
+    out_at(J, y, x) = nb;
   }
   // downward, in place: the output just above is the value above
   uint16_t na = NONE;
@@ -171,8 +176,8 @@ __global__ void __launch_bounds__(128) k_recon_peek_inplace(const ReconJob* __re
   for (int y = oy0; y <= oy1; ++y) {
     const int64_t p = (int64_t)y * w + x;
     const uint16_t v = J.filled[p];
-    if (v != NONE) { na = v; continue; }   // out[p] already holds v
-    const uint16_t b = J.out[p];
+    if (v != NONE) { na = v; continue; }   // the output already holds v
+    const uint16_t b = out_at(J, y, x);
     uint16_t o;
     if (na == NONE && b == NONE) o = 0;
     else if (na == NONE) o = b;
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(128) k_recon_peek_inplace(const ReconJob* __re
       const int range = a > c ? a - c : c - a;
       o = (uint16_t)(range > T ? min(a, c) : (a + c) / 2);
     }
-    J.out[p] = o;
+    out_at(J, y, x) = o;
     na = o;
   }
 }
@@ -197,6 +202,35 @@ void launch_recon(const ReconJob* jobs, int n_jobs, int max_w, int max_h, int ma
     k_recon_peek_apply<<<g, 128, 0, s>>>(jobs);
   }
   if (peek_modes & 2) k_recon_peek_inplace<<<dim3((max_w + 127) / 128, n_jobs), 128, 0, s>>>(jobs);
+}
+
+__global__ void __launch_bounds__(256) k_lr_consistency(const uint16_t* __restrict__ dL, const uint16_t* __restrict__ dR,
+                                                        int w, int h, int tol, uint8_t* __restrict__ ok,
+                                                        unsigned long long* count) {
+  const int64_t n = (int64_t)w * h;
+  unsigned long long mine = 0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t y = p / w;
+    const int x = (int)(p - y * w), dl = dL[p], xr = x - dl;
+    int v = 0;
+    if (xr >= 0) {
+      const int dr = dR[y * w + xr];
+      v = (dl > dr ? dl - dr : dr - dl) <= tol;
+    }
+    ok[p] = (uint8_t)v;
+    mine += v;
+  }
+  if (count) {
+    for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(count, mine);
+  }
+}
+
+void launch_lr_consistency(const uint16_t* dL, const uint16_t* dR, int w, int h, int tol, uint8_t* ok,
+                           unsigned long long* count, cudaStream_t s) {
+  const int64_t n = (int64_t)w * h;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 148 * 8);
+  k_lr_consistency<<<std::max(grid, 1), 256, 0, s>>>(dL, dR, w, h, tol, ok, count);
 }
 
 // kernels launch_recon issues for the given peek_modes

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) k_lightness(const LightJob* __restrict__ 
   __syncthreads();
 
   const bool want_hist = J.hist != nullptr;
-  const bool vec = ((reinterpret_cast<uintptr_t>(J.rgb) | reinterpret_cast<uintptr_t>(J.L)) & 15) == 0;
+  const bool vec = !J.mirror && ((reinterpret_cast<uintptr_t>(J.rgb) | reinterpret_cast<uintptr_t>(J.L)) & 15) == 0;
   const int64_t n = J.n_px;
   const int64_t n16 = vec ? n / 16 : 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -63,11 +63,17 @@ __global__ void __launch_bounds__(256) k_lightness(const LightJob* __restrict__ 
     }
     __stcs(reinterpret_cast<uint4*>(J.L) + c, make_uint4(o[0], o[1], o[2], o[3]));
   }
-  // scalar tail (and the whole image when the pointers are not 16-byte aligned)
+  // scalar tail (and the whole image when the pointers are not 16-byte aligned,
+  // or when the rows are written mirrored)
   for (int64_t p = n16 * 16 + (int64_t)blockIdx.x * blockDim.x + tid; p < n; p += stride) {
     uint32_t l = lightness_px(J.rgb[3 * p], J.rgb[3 * p + 1], J.rgb[3 * p + 2], s_lin, s_coarse, s_thr);
     if (want_hist) atomicAdd(&s_hist[warp][l], 1u);
-    J.L[p] = (uint8_t)l;
+    int64_t q = p;
+    if (J.mirror) {   // pixel x of row y goes to w-1-x
+      const int64_t y = p / J.w;
+      q = y * J.w + (J.w - 1 - (p - y * J.w));
+    }
+    J.L[q] = (uint8_t)l;
   }
   if (want_hist) {
     __syncthreads();

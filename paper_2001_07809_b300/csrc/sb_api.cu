@@ -341,6 +341,7 @@ bool params_ok(sb_context* ctx, int w, int h, const sb_params& p, sb_status* st)
   if (p.kmeans_max_iter < 0 || p.kmeans_max_iter > 100000) { *st = fail(ctx, SB_ERR_INVALID_ARG, "kmeans_max_iter must be in [0, 100000]"); return false; }
   if (p.sad_variant < SB_SAD_AUTO || p.sad_variant > SB_SAD_BOXSUM) { *st = fail(ctx, SB_ERR_INVALID_ARG, "unknown sad_variant %d", p.sad_variant); return false; }
   if (p.peek_mode != SB_PEEK_SNAPSHOT && p.peek_mode != SB_PEEK_INPLACE) { *st = fail(ctx, SB_ERR_INVALID_ARG, "unknown peek_mode %d", p.peek_mode); return false; }
+  if (p.view != SB_VIEW_LEFT && p.view != SB_VIEW_RIGHT) { *st = fail(ctx, SB_ERR_INVALID_ARG, "unknown view %d", p.view); return false; }
   return true;
 }
 
@@ -456,8 +457,10 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
     std::vector<LightJob> J;
     for (auto& r : runs) {
       const int64_t N = (int64_t)r.g.w * r.g.h;
-      J.push_back(LightJob{r.left, r.ws.Ll, r.ws.hist, N});
-      J.push_back(LightJob{r.right, r.ws.Lr, nullptr, N});
+      // right view: the mirrored right image is the reference, the mirrored left the search image
+      const bool rv = r.g.p.view == SB_VIEW_RIGHT;
+      J.push_back(LightJob{rv ? r.right : r.left, r.ws.Ll, r.ws.hist, N, r.g.w, rv ? 1 : 0});
+      J.push_back(LightJob{rv ? r.left : r.right, r.ws.Lr, nullptr, N, r.g.w, rv ? 1 : 0});
     }
     const LightJob* d = upload(ctx, J, &st);
     if (!d) return st;
@@ -579,7 +582,8 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
       const int inplace = r.g.p.peek_mode == SB_PEEK_INPLACE;
       modes |= inplace ? 2 : 1;
       J.push_back(ReconJob{r.ws.sparse, r.ws.filled, out, r.ws.seg_top, r.ws.seg_bot, r.g.w, r.g.h, r.g.p.max_disp,
-                           (r.g.p.block - 1) / 2, r.g.p.disp_threshold, kSegRows, inplace});
+                           (r.g.p.block - 1) / 2, r.g.p.disp_threshold, kSegRows, inplace,
+                           r.g.p.view == SB_VIEW_RIGHT ? 1 : 0});
     }
     const ReconJob* d = upload(ctx, J, &st);
     if (!d) return st;
@@ -599,7 +603,7 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
       const float* dtaps = upload(ctx, taps, &st);
       if (!dtaps) return st;
       BlurJob b{};
-      b.rgb = r.left;
+      b.rgb = r.g.p.view == SB_VIEW_RIGHT ? r.right : r.left;   // the reference image
       b.disp = r.out_disp ? r.out_disp : r.ws.disp;
       b.out = r.out_rgb;
       b.taps = dtaps;
@@ -640,6 +644,7 @@ void sb_default_params(sb_params* p) {
   p->n_ranges = 0;
   p->sad_variant = SB_SAD_AUTO;
   p->peek_mode = SB_PEEK_SNAPSHOT;
+  p->view = SB_VIEW_LEFT;
 }
 
 sb_status sb_create(int device, size_t mem_budget_bytes, void* cuda_stream, sb_context** out) {
@@ -740,7 +745,7 @@ sb_status sb_rgb_to_lightness(sb_context* ctx, const uint8_t* rgb, int32_t w, in
   if (!rgb || !L || w <= 0 || h <= 0) return fail(ctx, SB_ERR_INVALID_ARG, "rgb_to_lightness: null pointer or empty image");
   sb_status st;
   if (hist) SB_CUDA(ctx, cudaMemsetAsync(hist, 0, 256 * 4, ctx->stream));
-  std::vector<LightJob> J{LightJob{rgb, L, hist, (int64_t)w * h}};
+  std::vector<LightJob> J{LightJob{rgb, L, hist, (int64_t)w * h, w, 0}};
   const LightJob* d = upload(ctx, J, &st);
   if (!d) return st;
   const int bpj = (int)std::min<int64_t>(std::max<int64_t>(1, (int64_t)w * h / (256 * 16)), 592);
@@ -896,11 +901,24 @@ sb_status sb_reconstruct_disparity(sb_context* ctx, uint16_t* disp, int32_t w, i
   uint16_t* bot = (uint16_t*)(ctx->ws + al(N * 2) + al((size_t)nseg * w * 2));
   const int inplace = peek_mode == SB_PEEK_INPLACE;
   std::vector<ReconJob> J{ReconJob{disp, fl, disp, top, bot, w, h, max_disp, (block - 1) / 2, disp_threshold, kSegRows,
-                                   inplace}};
+                                   inplace, 0}};
   const ReconJob* d = upload(ctx, J, &st);
   if (!d) return st;
   launch_recon(d, 1, w, h, nseg, inplace ? 2 : 1, ctx->stream);
   SB_LAUNCHED(ctx, recon_launches(inplace ? 2 : 1));
+  return SB_OK;
+}
+
+sb_status sb_lr_consistency(sb_context* ctx, const uint16_t* dL, const uint16_t* dR, int32_t w, int32_t h,
+                            int32_t tol, uint8_t* ok, int64_t* count) {
+  if (!ctx) return SB_ERR_INVALID_ARG;
+  if (!dL || !dR || !ok) return fail(ctx, SB_ERR_INVALID_ARG, "lr_consistency: null pointer");
+  if (w < 1 || h < 1 || (int64_t)w * h >= (int64_t)1 << 31) return fail(ctx, SB_ERR_INVALID_ARG, "bad image size %dx%d", w, h);
+  cudaSetDevice(ctx->device);
+  if (count) SB_CUDA(ctx, cudaMemsetAsync(count, 0, 8, ctx->stream));
+  launch_lr_consistency(dL, dR, w, h, tol, ok, reinterpret_cast<unsigned long long*>(count), ctx->stream);
+  SB_LAUNCHED(ctx, 1);
+  SB_CUDA(ctx, cudaGetLastError());
   return SB_OK;
 }
 

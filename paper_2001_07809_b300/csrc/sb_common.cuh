@@ -25,6 +25,8 @@ struct LightJob {
   uint8_t* L;          // n_px
   uint32_t* hist;      // 256 or nullptr (must be zeroed before the launch)
   int64_t n_px;
+  int32_t w;           // row length (used when mirror is set)
+  int32_t mirror;      // 1: write each row mirrored (pixel x of a row to w-1-x)
 };
 // lin: uint16[256] linear sRGB x 65535; coarse: uint8[4096] L of Y>>4; thr: uint32[257]
 // first Y with L >= l.  Both built on the host from FP64 libm.
@@ -147,11 +149,18 @@ struct ReconJob {
   uint16_t* seg_bot;       // nseg * w
   int32_t w, h, D, r, threshold, seg_rows;
   int32_t inplace;         // Algorithm 2 reading: 0 snapshot, 1 in-place top-down sweep
+  int32_t mirror;          // 1: the final map is written mirrored (column x to w-1-x)
 };
 // peek_modes: bit 0 = some job uses the snapshot reading, bit 1 = some job the in-place one
 void launch_recon(const ReconJob* jobs, int n_jobs, int max_w, int max_h, int max_nseg, int peek_modes,
                   cudaStream_t s);
 int recon_launches(int peek_modes);
+
+// left-right consistency: ok[p] = 1 when left pixel p's match x - dL lies in
+// the image and |dL - dR there| <= tol; *count (zero on entry, or null) adds
+// the consistent pixels
+void launch_lr_consistency(const uint16_t* dL, const uint16_t* dR, int w, int h, int tol, uint8_t* ok,
+                           unsigned long long* count, cudaStream_t s);
 
 // --------------------------------------------------------------------- blur
 struct BlurJob {

@@ -79,7 +79,8 @@ def params_of(p, sad_variant=sb.SB_SAD_AUTO):
     return sb.make_params(k=p.k, max_disp=p.max_disp, block=p.block, disp_threshold=p.disp_threshold,
                           morph_mode=p.morph_mode, kmeans_max_iter=p.kmeans_max_iter,
                           cc_remove_fraction=p.cc_remove_fraction, sigma=p.sigma, ranges=p.ranges,
-                          sad_variant=sad_variant, peek_mode=getattr(p, "peek_mode", 0))
+                          sad_variant=sad_variant, peek_mode=getattr(p, "peek_mode", 0),
+                          view=getattr(p, "view", 0))
 
 
 def run_pairs(ctx, items, flags, sad_variant=sb.SB_SAD_AUTO):

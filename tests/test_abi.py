@@ -39,10 +39,10 @@ def test_binding_struct_layout_matches_header():
         c = os.path.join(d, "t.c")
         open(c, "w").write('#include <stdio.h>\n#include <stddef.h>\n#include "sb.h"\nint main(void){'
                            'printf("%zu %zu %zu %zu %zu\\n", sizeof(sb_params), sizeof(sb_pair), offsetof(sb_params, sigma),'
-                           ' offsetof(sb_params, peek_mode), offsetof(sb_pair, out_rgb)); return 0;}\n')
+                           ' offsetof(sb_params, view), offsetof(sb_pair, out_rgb)); return 0;}\n')
         exe = os.path.join(d, "t")
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         got = [int(v) for v in subprocess.check_output([exe]).split()]
     want = [ctypes.sizeof(sb.sb_params), ctypes.sizeof(sb.sb_pair), sb.sb_params.sigma.offset,
-            sb.sb_params.peek_mode.offset, sb.sb_pair.out_rgb.offset]
+            sb.sb_params.view.offset, sb.sb_pair.out_rgb.offset]
     assert got == want

@@ -348,6 +348,31 @@ def test_pipeline_inplace_peek_and_mixed_batch(ctx):
     assert np.array_equal(mixed[1][1], disp_ip) and np.array_equal(mixed[1][0], rgb_ip)
 
 
+def test_right_view_pipeline_and_lr_consistency(ctx):
+    # the right image as the reference: disparity map and
+    # blurred right image equal the oracle's; a batch mixing both views equals
+    # the views run alone; the left-right consistency map and count equal the
+    # oracle's on the two maps
+    import dataclasses
+    sc, p, _ = synth.workload("c1")
+    left, right, _ = sc.render()
+    p_r = dataclasses.replace(p, view=1)
+    (rgb_r, disp_r), = run_pairs(ctx, [(left, right, p_r)], sb.SB_RUN_PLAIN)
+    want = _compare_full(rgb_r, disp_r, left, right, p_r)
+    assert np.abs(rgb_r.astype(int) - want.out_rgb.astype(int)).max() <= 1
+    (rgb_l, disp_l), = run_pairs(ctx, [(left, right, p)], sb.SB_RUN_PLAIN)
+    mixed = run_pairs(ctx, [(left, right, p_r), (left, right, p)], sb.SB_RUN_BATCHED | sb.SB_RUN_GRAPH)
+    assert np.array_equal(mixed[0][1], disp_r) and np.array_equal(mixed[0][0], rgb_r)
+    assert np.array_equal(mixed[1][1], disp_l) and np.array_equal(mixed[1][0], rgb_l)
+    for tol in (0, 1, 3):
+        ok = torch.empty(disp_l.shape, dtype=torch.uint8, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        sb.sb_lr_consistency(ctx, dev(disp_l), dev(disp_r), ok, tol, cnt)
+        ctx.synchronize()
+        o_ok, o_n = oracle.lr_consistency(disp_l, disp_r, tol)
+        assert np.array_equal(host(ok), o_ok) and int(cnt.item()) == o_n
+
+
 def test_batched_and_graph_equal_plain_on_uneven_batch(ctx):
     items = []
     for i, (w, h, D, B, K) in enumerate([(200, 120, 24, 7, 3), (321, 203, 48, 13, 5), (150, 150, 16, 5, 4),
