@@ -67,3 +67,42 @@ def test_budget_rejects_oversized_request_and_keeps_serving():
     out_rgb, out_disp = g.result(timeout=60)
     srv.close()
     assert out_rgb.shape == left.shape
+
+
+@pytest.mark.slow
+def test_c5_sample_alone_and_in_the_mix():
+    # 50 requests of the serving stream (mixed sizes, disparity ranges,
+    # blocks, K; seed 7) submitted in bursts: every served result equals the
+    # same pair run alone, and a few are checked against the oracle
+    import oracle
+    items = []
+    for i in range(50):
+        sc, p, _ = synth.workload("c5", i)
+        left, right, _ = sc.render(want_gt=False)
+        items.append((left, right, p))
+    ctx = sb.Context(0)
+    alone = [run_pairs(ctx, [it], sb.SB_RUN_PLAIN)[0] for it in items]
+    ctx.close()
+    srv = Server(0, mem_budget_bytes=8 << 30, max_batch=16)
+    futs = []
+    for i, (l, r, p) in enumerate(items):
+        futs.append(srv.submit(torch.from_numpy(l).pin_memory(), torch.from_numpy(r).pin_memory(), params_of(p)))
+        if i % 10 == 9:
+            time.sleep(0.01)
+    res = [f.result(timeout=300) for f in futs]
+    batches = srv.batches
+    srv.close()
+    assert batches < len(items)
+    for (o_rgb, o_disp), (a_rgb, a_disp) in zip(res, alone):
+        assert np.array_equal(o_rgb.numpy(), a_rgb)
+        assert np.array_equal(o_disp.numpy().view(np.uint16), a_disp)
+    rng = np.random.default_rng(5)
+    for i in (0, 17, 33):
+        left, right, p = items[i]
+        fr = oracle.run_front(left, right, p)
+        h, w = left.shape[:2]
+        pts = [(int(rng.integers(0, w)), int(rng.integers(0, h))) for _ in range(40)]
+        want = oracle.disp_at_points(fr, p, pts)
+        got = [int(alone[i][1][y, x]) for x, y in pts]
+        assert got == want
+
