@@ -40,9 +40,9 @@ INTEREST_C3 = [(120, 256)]
 # one |L - R|, two vertical running-sum updates, two horizontal, one compare
 BOX_OPS_PER_PXD = 6
 # DRAM bytes of k_sad_boxsum per 4096x2304 pair (D=256, block 41): the ncu capture of one
-# 8-pair launch read 457.97 MB and wrote 170.64 MB (L maps and boundary map in, argmin keys
+# 8-pair launch read 458.19 MB and wrote 170.00 MB (L maps and boundary map in, argmin keys
 # out); a launch over P pairs moves P times that, since each pair's data is its own
-SAD_DRAM_BYTES_PER_PAIR = (457.966080e6 + 170.637824e6) / 8
+SAD_DRAM_BYTES_PER_PAIR = (458.192640e6 + 170.001408e6) / 8
 METRIC = "stereo pairs/s at 4096x2304 (batched vs per-pair), SAD Gcell/s, p99 latency"
 WORKLOAD = ("batched video: %d pairs of 4096x2304 RGB per GPU, 12 drifting layers (seed 2), D=256, block 41, K=8, "
             "sigma 8, interest [120,256]")
