@@ -38,13 +38,21 @@ __global__ void __launch_bounds__(256) k_recon_fill(const ReconJob* __restrict__
   const int y = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (y >= J.h) return;
   const int lane = threadIdx.x & 31, w = J.w;
-  const uint16_t* src = J.sparse + (int64_t)y * w;
+  const uint16_t* srow = J.sparse + (int64_t)y * w;
+  const uint32_t* krow = J.keys ? J.keys + (int64_t)y * w : nullptr;
+  // the anchor's disparity at x, or NONE: from the SAD output, or decoded from
+  // the argmin keys (no real key is all ones: costs stay below 2^22)
+  auto src = [&](int x) -> uint16_t {
+    if (!krow) return srow[x];
+    const uint32_t k = krow[x];
+    return k == 0xFFFFFFFFu ? NONE : (uint16_t)(k & ((1u << SB_KEY_DBITS) - 1u));
+  };
   uint16_t* dst = J.filled + (int64_t)y * w;
   // pass 1: disparity of the nearest anchor strictly to the left (NONE if none)
   uint16_t carry = NONE;
   for (int x0 = 0; x0 < w; x0 += 32) {
     const int x = x0 + lane;
-    const uint16_t v = x < w ? src[x] : NONE;
+    const uint16_t v = x < w ? src(x) : NONE;
     const bool anc = v != NONE;
     const unsigned mask = __ballot_sync(0xffffffffu, anc);
     const unsigned below = mask & ((1u << lane) - 1u);
@@ -60,7 +68,7 @@ __global__ void __launch_bounds__(256) k_recon_fill(const ReconJob* __restrict__
   const int nchunks = (w + 31) / 32;
   for (int ci = nchunks - 1; ci >= 0; --ci) {
     const int x = ci * 32 + lane;
-    const uint16_t v = x < w ? src[x] : NONE;
+    const uint16_t v = x < w ? src(x) : NONE;
     const bool anc = v != NONE;
     const unsigned mask = __ballot_sync(0xffffffffu, anc);
     const unsigned above = lane == 31 ? 0u : (mask & ~((2u << lane) - 1u));

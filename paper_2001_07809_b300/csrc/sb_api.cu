@@ -566,11 +566,9 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
         launch_sad_direct(d, n, nw, dir_r, dir_D, s);
         SB_LAUNCHED(ctx, 1);
       }
+    // the argmin keys go straight to Algorithm 1 (its kernel decodes them), so
+    // the pipeline needs no key-to-disparity pass
     SB_MARK(ctx, SB_STAGE_SAD_FINALIZE);
-    if (!ctx->dry) {
-      launch_sad_finalize(d, n, max_w, max_h, s);
-      SB_LAUNCHED(ctx, 1);
-    }
   }
   SB_MARK(ctx, SB_STAGE_RECON);
   // 6. reconstruction (Algorithms 1 and 2)
@@ -581,8 +579,8 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
       uint16_t* out = r.out_disp ? r.out_disp : r.ws.disp;
       const int inplace = r.g.p.peek_mode == SB_PEEK_INPLACE;
       modes |= inplace ? 2 : 1;
-      J.push_back(ReconJob{r.ws.sparse, r.ws.filled, out, r.ws.seg_top, r.ws.seg_bot, r.g.w, r.g.h, r.g.p.max_disp,
-                           (r.g.p.block - 1) / 2, r.g.p.disp_threshold, kSegRows, inplace,
+      J.push_back(ReconJob{r.ws.sparse, r.ws.size_key, r.ws.filled, out, r.ws.seg_top, r.ws.seg_bot, r.g.w, r.g.h,
+                           r.g.p.max_disp, (r.g.p.block - 1) / 2, r.g.p.disp_threshold, kSegRows, inplace,
                            r.g.p.view == SB_VIEW_RIGHT ? 1 : 0});
     }
     const ReconJob* d = upload(ctx, J, &st);
@@ -900,8 +898,8 @@ sb_status sb_reconstruct_disparity(sb_context* ctx, uint16_t* disp, int32_t w, i
   uint16_t* top = (uint16_t*)(ctx->ws + al(N * 2));
   uint16_t* bot = (uint16_t*)(ctx->ws + al(N * 2) + al((size_t)nseg * w * 2));
   const int inplace = peek_mode == SB_PEEK_INPLACE;
-  std::vector<ReconJob> J{ReconJob{disp, fl, disp, top, bot, w, h, max_disp, (block - 1) / 2, disp_threshold, kSegRows,
-                                   inplace, 0}};
+  std::vector<ReconJob> J{ReconJob{disp, nullptr, fl, disp, top, bot, w, h, max_disp, (block - 1) / 2, disp_threshold,
+                                   kSegRows, inplace, 0}};
   const ReconJob* d = upload(ctx, J, &st);
   if (!d) return st;
   launch_recon(d, 1, w, h, nseg, inplace ? 2 : 1, ctx->stream);

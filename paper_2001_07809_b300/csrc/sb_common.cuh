@@ -142,7 +142,8 @@ constexpr int kSadChunk = 32;
 
 // ----------------------------------------------------------- reconstruction
 struct ReconJob {
-  const uint16_t* sparse;  // SAD output: anchors, UNDET elsewhere
+  const uint16_t* sparse;  // SAD output: anchors, UNDET elsewhere (unused when keys is set)
+  const uint32_t* keys;    // or the SAD argmin keys themselves ((cost << 10) | d, all ones off the anchors)
   uint16_t* filled;        // Algorithm 1 output
   uint16_t* out;           // Algorithm 2 output (final)
   uint16_t* seg_top;       // nseg * w

@@ -349,7 +349,7 @@ def test_pipeline_inplace_peek_and_mixed_batch(ctx):
 
 
 def test_right_view_pipeline_and_lr_consistency(ctx):
-    # the right image as the reference (SURVEY NEXT-4): disparity map and
+    # the right image as the reference: disparity map and
     # blurred right image equal the oracle's; a batch mixing both views equals
     # the views run alone; the left-right consistency map and count equal the
     # oracle's on the two maps
