@@ -1,5 +1,5 @@
 // Segment boundary detection and morphological refinement (Section III),
-// fused into one stencil kernel over 64x16 output tiles with the halo held in
+// fused into one stencil kernel over 64x32 output tiles with the halo held in
 // shared memory: labels (from L through the bin->cluster table, or given) ->
 // 8-neighbour boundary -> Fill -> Remove (halo 3), or -> 3x3 erosion ->
 // dilation (opening) -> dilation -> erosion (closing) (halo 5).  Each
@@ -11,51 +11,47 @@
 namespace sb {
 
 namespace {
-constexpr int TW = 64, TH = 16;
+constexpr int TW = 64, TH = 32;
 
 template <int HALO>
 struct Tile {
   static constexpr int W = TW + 2 * HALO, H = TH + 2 * HALO;
 };
 
-// Evaluate a 3x3 stencil over the sub-region of halo `k` (k <= HALO-1).
+// Evaluate a 3x3 stencil over the sub-region of halo `k` (k <= HALO-1):
+// warps take rows, lanes take columns (no division per pixel).
 template <int HALO, class F>
 __device__ __forceinline__ void region(int k, F f) {
   constexpr int W = Tile<HALO>::W;
   const int i0 = HALO - k, j0 = HALO - k, ni = TH + 2 * k, nj = TW + 2 * k;
-  for (int t = threadIdx.x; t < ni * nj; t += blockDim.x) {
-    const int i = i0 + t / nj, j = j0 + t % nj;
-    f(i, j, i * W + j);
-  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = i0 + warp; i < i0 + ni; i += blockDim.x >> 5)
+    for (int j = j0 + lane; j < j0 + nj; j += 32) f(i, j, i * W + j);
 }
-}  // namespace
 
-template <int MODE>
-__global__ void __launch_bounds__(256) k_boundary_morph(const MorphJob* __restrict__ jobs) {
+// One tile.  INTERIOR: the tile and its halo lie inside the image, so no
+// neighbour test is needed.
+template <int MODE, bool INTERIOR>
+__device__ __forceinline__ void morph_tile(const MorphJob& J, int tx0, int ty0, uint8_t* s_lab, uint8_t* s_a,
+                                           uint8_t* s_b, const uint8_t* s_lut) {
   constexpr int HALO = MODE == 0 ? 3 : 5;
   constexpr int W = Tile<HALO>::W, H = Tile<HALO>::H;
-  __shared__ uint8_t s_lab[H * W];
-  __shared__ uint8_t s_a[H * W];
-  __shared__ uint8_t s_b[H * W];
-  __shared__ uint8_t s_lut[256];
-  const MorphJob J = jobs[blockIdx.z];
-  const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * TH;
-  if (tx0 >= J.w || ty0 >= J.h) return;
   const int w = J.w, h = J.h;
-  if (J.lut) {
-    s_lut[threadIdx.x] = J.lut[threadIdx.x];
-    __syncthreads();
-  }
   const int ox = tx0 - HALO, oy = ty0 - HALO;
-  auto inimg = [&](int i, int j) { return (unsigned)(oy + i) < (unsigned)h && (unsigned)(ox + j) < (unsigned)w; };
-  for (int t = threadIdx.x; t < H * W; t += blockDim.x) {
-    const int i = t / W, j = t % W;
-    uint8_t v = 0;
-    if (inimg(i, j)) {
-      uint8_t s = J.src[(int64_t)(oy + i) * w + (ox + j)];
-      v = J.lut ? s_lut[s] : s;
-    }
-    s_lab[t] = v;
+  auto inimg = [&](int i, int j) {
+    return INTERIOR || ((unsigned)(oy + i) < (unsigned)h && (unsigned)(ox + j) < (unsigned)w);
+  };
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = warp; i < H; i += blockDim.x >> 5)
+      for (int j = lane; j < W; j += 32) {
+        uint8_t v = 0;
+        if (inimg(i, j)) {
+          const uint8_t s = J.src[(int64_t)(oy + i) * w + (ox + j)];
+          v = J.lut ? s_lut[s] : s;
+        }
+        s_lab[i * W + j] = v;
+      }
   }
   __syncthreads();
   // boundary: an in-image 8-neighbour with another label
@@ -140,6 +136,29 @@ __global__ void __launch_bounds__(256) k_boundary_morph(const MorphJob* __restri
       J.out[(int64_t)(oy + i) * w + (ox + j)] = (uint8_t)v;  // closing
     });
   }
+}
+}  // namespace
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_boundary_morph(const MorphJob* __restrict__ jobs) {
+  constexpr int HALO = MODE == 0 ? 3 : 5;
+  constexpr int W = Tile<HALO>::W, H = Tile<HALO>::H;
+  __shared__ uint8_t s_lab[H * W];
+  __shared__ uint8_t s_a[H * W];
+  __shared__ uint8_t s_b[H * W];
+  __shared__ uint8_t s_lut[256];
+  const MorphJob J = jobs[blockIdx.z];
+  const int tx0 = blockIdx.x * TW, ty0 = blockIdx.y * TH;
+  if (tx0 >= J.w || ty0 >= J.h) return;
+  if (J.lut) {
+    s_lut[threadIdx.x] = J.lut[threadIdx.x];
+    __syncthreads();
+  }
+  const bool interior = tx0 >= HALO && ty0 >= HALO && tx0 - HALO + W <= J.w && ty0 - HALO + H <= J.h;
+  if (interior)
+    morph_tile<MODE, true>(J, tx0, ty0, s_lab, s_a, s_b, s_lut);
+  else
+    morph_tile<MODE, false>(J, tx0, ty0, s_lab, s_a, s_b, s_lut);
 }
 
 void launch_boundary_morph(const MorphJob* jobs, int n_jobs, int max_w, int max_h, int mode, cudaStream_t s) {
