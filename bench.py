@@ -247,6 +247,7 @@ def uneven_measure(sb, torch, n_pairs=64, steps=3):
     res = {}
     outs = {}
     for name, flags in (("batched", sb.SB_RUN_BATCHED | sb.SB_RUN_GRAPH), ("per_pair", sb.SB_RUN_PLAIN)):
+        sb.sb_autotune(ctx, pairs, flags)   # untimed
         sb.sb_run(ctx, pairs, flags)
         ctx.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -384,7 +385,10 @@ def run_ours(args):
     pairs = [sb.Pair(lefts[i], rights[i], params, outs[i], disps[i]) for i in range(P)]
     flags = sb.SB_RUN_BATCHED | sb.SB_RUN_GRAPH
 
-    # untimed warm-up (captures the graph)
+    # untimed: the library's autotuner picks the box-sum work split for this
+    # batch shape (it runs the batch once per candidate), then warm-up steps
+    # (the graph is captured by the first)
+    tune_batched = sb.sb_autotune(ctx, pairs, flags)
     for _ in range(args.warmup):
         sb.sb_run(ctx, pairs, flags)
     ctx.synchronize()
@@ -415,8 +419,9 @@ def run_ours(args):
     stage_avg = [statistics.mean(s[i] for s in stage_ms) for i in range(len(sb.STAGES))]
     ctx.profile_enable(False)
 
-    # plain per-pair form on the same pairs
+    # plain per-pair form on the same pairs (work split tuned for one pair, untimed)
     plain_steps = 1
+    tune_plain = sb.sb_autotune(ctx, pairs[:1], sb.SB_RUN_PLAIN)
     sb.sb_run(ctx, pairs[:4], sb.SB_RUN_PLAIN)
     ctx.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -514,6 +519,9 @@ def run_ours(args):
                          "frac_of_measured_iadd": (achieved / rates["iadd_tops"]) if "iadd_tops" in rates else None,
                          "ops_per_launch": ops},
             "e2e": e2e,
+            "autotune": {"box_sum_work_items": {"batched": tune_batched[0], "per_pair": tune_plain[0]},
+                         "candidate_ms": {"batched": tune_batched[1], "per_pair": tune_plain[1]},
+                         "candidates": "1, 2, 3, 6 waves of the persistent box-sum grid"},
             "uneven_batch": uneven,
             "serving": serving,
             "gpu_launches": launches,

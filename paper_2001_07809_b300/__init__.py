@@ -18,7 +18,7 @@ __all__ = [
     "SbError", "Context", "Pair", "sb_default_params", "make_params", "sb_create", "sb_destroy",
     "sb_rgb_to_lightness", "sb_kmeans_segment", "sb_refine_boundaries", "sb_boundary_sad",
     "sb_reconstruct_disparity", "sb_selective_blur", "sb_run", "sb_synchronize", "sb_launch_count",
-    "sb_lr_consistency", "SB_PEEK_SNAPSHOT", "SB_PEEK_INPLACE", "SB_VIEW_LEFT", "SB_VIEW_RIGHT",
+    "sb_lr_consistency", "sb_autotune", "SB_PEEK_SNAPSHOT", "SB_PEEK_INPLACE", "SB_VIEW_LEFT", "SB_VIEW_RIGHT",
     "SB_RUN_PLAIN", "SB_RUN_BATCHED", "SB_RUN_GRAPH", "SB_RUN_HOST_IO", "SB_SAD_AUTO", "SB_SAD_DIRECT",
     "SB_SAD_BOXSUM", "SB_MORPH_FILL_REMOVE", "SB_MORPH_OPEN_CLOSE", "UNDETERMINED", "library_path",
 ]
@@ -87,6 +87,7 @@ def _load():
         "sb_boundary_sad": ([V, V, V, V, I32, I32, I32, I32, I32, V, V], ctypes.c_int),
         "sb_reconstruct_disparity": ([V, V, I32, I32, I32, I32, I32, I32, V], ctypes.c_int),
         "sb_lr_consistency": ([V, V, V, I32, I32, I32, V, V], ctypes.c_int),
+        "sb_autotune": ([V, V, I32, ctypes.c_uint32, V, V], ctypes.c_int),
         "sb_selective_blur": ([V, V, V, I32, I32, V, I32, ctypes.c_float, V], ctypes.c_int),
         "sb_run": ([V, ctypes.POINTER(sb_pair), I32, U32], ctypes.c_int),
         "sb_profile_enable": ([V, ctypes.c_int], ctypes.c_int),
@@ -281,6 +282,17 @@ def _pairs_array(pairs: List[Pair]):
         h, w = _hw(q.left_rgb)
         arr[i] = sb_pair(_ptr(q.left_rgb), _ptr(q.right_rgb), w, h, q.params, _ptr(q.out_rgb), _ptr(q.out_disp))
     return arr
+
+
+def sb_autotune(ctx: Context, pairs: List[Pair], flags: int = SB_RUN_PLAIN):
+    """Times the candidate box-sum work splits on these pairs (running them),
+    keeps the fastest for their shape on this context; -> (items, [ms per
+    candidate])."""
+    arr = _pairs_array(pairs)
+    ms = (ctypes.c_float * 4)()
+    chosen = ctypes.c_int32(0)
+    _check(ctx, _lib.sb_autotune(ctx.handle, arr, len(pairs), flags, ms, ctypes.byref(chosen)))
+    return int(chosen.value), [float(v) for v in ms]
 
 
 def sb_run(ctx: Context, pairs: List[Pair], flags: int = SB_RUN_PLAIN):

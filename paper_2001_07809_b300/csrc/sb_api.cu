@@ -197,6 +197,11 @@ struct sb_context {
   bool prof_recorded = false;
   bool capturing = false;
   uint64_t graph_kernels = 0;
+  // autotune cache: launch-group shape (each pair's w, h, D, block) -> the
+  // box-sum SAD's work-item target chosen by sb_autotune
+  std::map<std::string, int> tuned;
+  int sad_target_override = 0;   // set while sb_autotune times a candidate
+  int sms = 148;
 };
 
 namespace {
@@ -371,7 +376,7 @@ void sad_choice(const Geo& g, const int64_t* nb, SadJob* j, bool* direct_possibl
 
 // Box-sum work items: (pair, strip, disparity chunk, row band); bands are cut
 // so that a small batch still fills the GPU.
-void sad_items(const std::vector<std::pair<int, Geo>>& pairs, std::vector<SadItem>* items) {
+void sad_items(const std::vector<std::pair<int, Geo>>& pairs, int64_t target, std::vector<SadItem>* items) {
   int64_t base = 0;
   for (auto& pg : pairs) {
     const Geo& g = pg.second;
@@ -380,7 +385,6 @@ void sad_items(const std::vector<std::pair<int, Geo>>& pairs, std::vector<SadIte
     const int ncols = g.w - D - 2 * r;
     base += (int64_t)((ncols + TX - 1) / TX) * ((D + 1 + kSadChunk - 1) / kSadChunk);
   }
-  const int64_t target = 148 * 2 * 3;
   // (cost, item): cost = rows including the 2r warm-up rows x the strip's columns
   std::vector<std::pair<int64_t, SadItem>> list;
   for (auto& pg : pairs) {
@@ -428,6 +432,26 @@ struct PairRun {
   Geo g;
   PairWs ws;
 };
+
+// Launch-group shape for the autotune cache: every pair's size, disparity
+// range and block (what the box-sum work split depends on).
+std::string shape_key(const Geo* geos, int n) {
+  std::string key;
+  for (int i = 0; i < n; ++i) {
+    const int32_t v[4] = {geos[i].w, geos[i].h, geos[i].p.max_disp, geos[i].p.block};
+    key.append((const char*)v, sizeof v);
+  }
+  return key;
+}
+
+// Box-sum work items a launch aims for: the candidate being timed, else the
+// tuned value for this shape, else three waves of the persistent grid.
+int64_t sad_target(const sb_context* ctx, const std::string& key) {
+  if (ctx->sad_target_override > 0) return ctx->sad_target_override;
+  auto it = ctx->tuned.find(key);
+  if (it != ctx->tuned.end()) return it->second;
+  return (int64_t)ctx->sms * 2 * 3;
+}
 
 // Enqueues the whole pipeline for `runs` (one launch per stage over all of
 // them).  Job descriptors go to `jobs_dev` when given (graph form), else
@@ -549,8 +573,10 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
     if (!d) return st;
     SB_MARK(ctx, SB_STAGE_SAD);
     if (!box.empty()) {
+      std::vector<Geo> geos;
+      for (auto& r : runs) geos.push_back(r.g);
       std::vector<SadItem> items;
-      sad_items(box, &items);
+      sad_items(box, sad_target(ctx, shape_key(geos.data(), n)), &items);
       const SadItem* di = upload(ctx, items, &st);
       if (!di) return st;
       int max_r = 0;
@@ -661,6 +687,7 @@ sb_status sb_create(int device, size_t mem_budget_bytes, void* cuda_stream, sb_c
   if (build_tables(ctx.get()) != SB_OK) return SB_ERR_CUDA;
   if (cudaMalloc(&ctx->dev_err, 4) != cudaSuccess || cudaMemset(ctx->dev_err, 0, 4) != cudaSuccess) return SB_ERR_CUDA;
   if (cudaMalloc(&ctx->sad_queue, 4) != cudaSuccess) return SB_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) ctx->sms = 148;
   if (ctx->up.init(8 << 20) != cudaSuccess) return SB_ERR_OOM;
   *out = ctx.release();
   return SB_OK;
@@ -866,7 +893,7 @@ sb_status sb_boundary_sad(sb_context* ctx, const uint8_t* L_left, const uint8_t*
   if (!d) return st;
   if (bp) {
     std::vector<SadItem> items;
-    sad_items({{0, g}}, &items);
+    sad_items({{0, g}}, sad_target(ctx, shape_key(&g, 1)), &items);
     const SadItem* di = upload(ctx, items, &st);
     if (!di) return st;
     SB_CUDA(ctx, cudaMemsetAsync(ctx->sad_queue, 0, 4, s));
@@ -994,6 +1021,12 @@ sb_status run_graph(sb_context* ctx, const sb_pair* pairs, int n) {
   sb_status st = ensure_ws(ctx, need);
   if (st != SB_OK) return st;
   std::string key((const char*)&ctx->ws, sizeof ctx->ws);
+  {
+    std::vector<Geo> geos;
+    for (int i = 0; i < n; ++i) geos.push_back(Geo{pairs[i].w, pairs[i].h, pairs[i].p});
+    const int64_t target = sad_target(ctx, shape_key(geos.data(), n));
+    key.append((const char*)&target, sizeof target);
+  }
   for (int i = 0; i < n; ++i) {
     const sb_pair& q = pairs[i];
     key.append((const char*)&q.w, sizeof q.w);
@@ -1160,6 +1193,55 @@ sb_status run_host_io(sb_context* ctx, const sb_pair* pairs, int n, bool batched
 }
 
 }  // namespace
+
+extern "C" sb_status sb_autotune(sb_context* ctx, const sb_pair* pairs, int32_t n_pairs, uint32_t flags,
+                                 float* ms_out, int32_t* target_out) {
+  if (!ctx) return SB_ERR_INVALID_ARG;
+  if (n_pairs <= 0 || !pairs) return fail(ctx, SB_ERR_INVALID_ARG, "sb_autotune: no pairs");
+  if (ctx->capturing) return fail(ctx, SB_ERR_INVALID_ARG, "sb_autotune cannot run inside a stream capture");
+  if (flags & SB_RUN_HOST_IO)
+    return fail(ctx, SB_ERR_INVALID_ARG, "sb_autotune takes device pairs (host-buffer runs split into their own groups)");
+  cudaSetDevice(ctx->device);
+  // candidates: 1, 2, 3 and 6 waves of the persistent box-sum grid
+  const int waves[SB_AUTOTUNE_CANDIDATES] = {1, 2, 3, 6};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SB_CUDA(ctx, cudaEventCreate(&e0));
+  SB_CUDA(ctx, cudaEventCreate(&e1));
+  float best_ms = 0.f;
+  int best = 0;
+  sb_status st = SB_OK;
+  for (int c = 0; c < SB_AUTOTUNE_CANDIDATES && st == SB_OK; ++c) {
+    ctx->sad_target_override = ctx->sms * 2 * waves[c];
+    st = sb_run(ctx, pairs, n_pairs, flags);   // warm-up (and graph capture)
+    if (st != SB_OK) break;
+    cudaEventRecord(e0, ctx->stream);
+    st = sb_run(ctx, pairs, n_pairs, flags);
+    if (st != SB_OK) break;
+    cudaEventRecord(e1, ctx->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(ctx, SB_ERR_CUDA, "sb_autotune: event wait failed"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms_out) ms_out[c] = ms;
+    if (c == 0 || ms < best_ms) { best_ms = ms; best = ctx->sad_target_override; }
+  }
+  ctx->sad_target_override = 0;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != SB_OK) return st;
+  // the shape of each launch group sb_run forms with these flags
+  if (flags & SB_RUN_BATCHED) {
+    std::vector<Geo> geos;
+    for (int i = 0; i < n_pairs; ++i) geos.push_back(Geo{pairs[i].w, pairs[i].h, pairs[i].p});
+    ctx->tuned[shape_key(geos.data(), n_pairs)] = best;
+  } else {
+    for (int i = 0; i < n_pairs; ++i) {
+      Geo g{pairs[i].w, pairs[i].h, pairs[i].p};
+      ctx->tuned[shape_key(&g, 1)] = best;
+    }
+  }
+  if (target_out) *target_out = best;
+  return SB_OK;
+}
 
 extern "C" sb_status sb_run(sb_context* ctx, const sb_pair* pairs, int32_t n_pairs, uint32_t flags) {
   if (!ctx) return SB_ERR_INVALID_ARG;

@@ -12,7 +12,7 @@ if not torch.cuda.is_available():
 import oracle  # noqa: E402
 import synth  # noqa: E402
 import paper_2001_07809_b300 as sb  # noqa: E402
-from gpu_helpers import blur, dev, host, kmeans, lightness, recon, refine, run_pairs, sad  # noqa: E402
+from gpu_helpers import blur, dev, host, kmeans, lightness, params_of, recon, refine, run_pairs, sad  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 RNG = np.random.default_rng(2024)
@@ -371,6 +371,40 @@ def test_right_view_pipeline_and_lr_consistency(ctx):
         ctx.synchronize()
         o_ok, o_n = oracle.lr_consistency(disp_l, disp_r, tol)
         assert np.array_equal(host(ok), o_ok) and int(cnt.item()) == o_n
+
+
+def test_autotune_keeps_results_and_caches_the_split(ctx):
+    # the autotuner times the candidate work splits on real pairs; outputs do
+    # not depend on the split, and later runs of the shape use the chosen one
+    items = []
+    for i in range(3):
+        r = synth.Rng(800 + i)
+        sc = synth.Scene(360, 140, synth._c2_style_layers(r, 360, 140, 48, contrast=40), noise_q8=512,
+                         noise_seed=r.u64())
+        left, right, _ = sc.render(want_gt=False)
+        items.append((left, right, synth.Params(k=6, max_disp=48, block=(9, 15, 25)[i], sigma=3.0,
+                                                ranges=[(0, 16)], morph_mode=0)))
+    before = run_pairs(ctx, items, sb.SB_RUN_BATCHED)
+    pairs, outs = [], []
+    for left, right, p in items:
+        h, w = left.shape[:2]
+        o = torch.empty((h, w, 3), dtype=torch.uint8, device="cuda")
+        d = torch.empty((h, w), dtype=torch.int16, device="cuda")
+        pairs.append(sb.Pair(dev(left), dev(right), params_of(p, sb.SB_SAD_BOXSUM), o, d))
+        outs.append((o, d))
+    for flags in (sb.SB_RUN_BATCHED | sb.SB_RUN_GRAPH, sb.SB_RUN_PLAIN):
+        chosen, ms = sb.sb_autotune(ctx, pairs, flags)
+        assert chosen in [ctx_sms() * 2 * k for k in (1, 2, 3, 6)] and all(m > 0 for m in ms)
+        sb.sb_run(ctx, pairs, flags)
+        ctx.synchronize()
+        for (o, d), (b_rgb, b_disp) in zip(outs, before):
+            assert np.array_equal(host(o), b_rgb) and np.array_equal(host(d, np.uint16), b_disp)
+    with pytest.raises(sb.SbError):
+        sb.sb_autotune(ctx, pairs, sb.SB_RUN_BATCHED | sb.SB_RUN_HOST_IO)
+
+
+def ctx_sms():
+    return torch.cuda.get_device_properties(0).multi_processor_count
 
 
 def test_batched_and_graph_equal_plain_on_uneven_batch(ctx):
