@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <map>
 #include <memory>
 #include <string>
@@ -1010,6 +1011,41 @@ sb_status run_device(sb_context* ctx, const sb_pair* pairs, int n, bool batched)
   return enqueue_pipeline(ctx, runs);
 }
 
+// Record-only pass (`pass` enqueues with ctx->dry set: uploads only, into the
+// host blob), then one copy of the blob to the device on the context stream.
+// A later pass run with ctx->sink = 1 (blob cleared) makes the same uploads
+// in the same order and so gets the same device offsets.
+sb_status record_and_upload_blob(sb_context* ctx, const std::function<sb_status()>& pass) {
+  sb_status st = SB_OK;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    ctx->blob.clear();
+    ctx->sink = 1;
+    ctx->dry = true;
+    st = pass();
+    ctx->dry = false;
+    ctx->sink = 0;
+    if (st != SB_OK) return st;
+    if (ctx->blob.size() <= ctx->blob_cap) break;
+    // grow the blob (its address is baked into captured graphs: drop them)
+    SB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->graph.exec) { cudaGraphExecDestroy(ctx->graph.exec); ctx->graph.exec = nullptr; }
+    if (ctx->blob_dev) cudaFree(ctx->blob_dev);
+    if (ctx->blob_host) cudaFreeHost(ctx->blob_host);
+    ctx->blob_dev = ctx->blob_host = nullptr;
+    ctx->blob_cap = 0;
+    const size_t cap = ctx->blob.size() * 2;
+    SB_CUDA(ctx, cudaMalloc(&ctx->blob_dev, cap));
+    SB_CUDA(ctx, cudaMallocHost(&ctx->blob_host, cap));
+    ctx->blob_cap = cap;
+  }
+  if (!ctx->blob_ev) SB_CUDA(ctx, cudaEventCreateWithFlags(&ctx->blob_ev, cudaEventDisableTiming));
+  SB_CUDA(ctx, cudaEventSynchronize(ctx->blob_ev));  // the previous blob copy has been read
+  memcpy(ctx->blob_host, ctx->blob.data(), ctx->blob.size());
+  SB_CUDA(ctx, cudaMemcpyAsync(ctx->blob_dev, ctx->blob_host, ctx->blob.size(), cudaMemcpyHostToDevice, ctx->stream));
+  SB_CUDA(ctx, cudaEventRecord(ctx->blob_ev, ctx->stream));
+  return SB_OK;
+}
+
 // Graph form: the batched pipeline is captured once per batch shape (sizes,
 // parameters, workspace) and replayed.  Kernels read their job descriptors
 // from a device blob owned by the context; each call rebuilds the blob for
@@ -1034,33 +1070,9 @@ sb_status run_graph(sb_context* ctx, const sb_pair* pairs, int n) {
     key.append((const char*)&q.p, sizeof q.p);
     key.push_back(q.out_disp ? 1 : 0);
   }
-  // record-only pass: the blob for the current pointers
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    ctx->blob.clear();
-    ctx->sink = 1;
-    ctx->dry = true;
-    st = run_device(ctx, pairs, n, true);
-    ctx->dry = false;
-    ctx->sink = 0;
-    if (st != SB_OK) return st;
-    if (ctx->blob.size() <= ctx->blob_cap) break;
-    // grow the blob (its address is baked into captured graphs: drop them)
-    SB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (ctx->graph.exec) { cudaGraphExecDestroy(ctx->graph.exec); ctx->graph.exec = nullptr; }
-    if (ctx->blob_dev) cudaFree(ctx->blob_dev);
-    if (ctx->blob_host) cudaFreeHost(ctx->blob_host);
-    ctx->blob_dev = ctx->blob_host = nullptr;
-    ctx->blob_cap = 0;
-    const size_t cap = ctx->blob.size() * 2;
-    SB_CUDA(ctx, cudaMalloc(&ctx->blob_dev, cap));
-    SB_CUDA(ctx, cudaMallocHost(&ctx->blob_host, cap));
-    ctx->blob_cap = cap;
-  }
-  if (!ctx->blob_ev) SB_CUDA(ctx, cudaEventCreateWithFlags(&ctx->blob_ev, cudaEventDisableTiming));
-  SB_CUDA(ctx, cudaEventSynchronize(ctx->blob_ev));  // the previous blob copy has been read
-  memcpy(ctx->blob_host, ctx->blob.data(), ctx->blob.size());
-  SB_CUDA(ctx, cudaMemcpyAsync(ctx->blob_dev, ctx->blob_host, ctx->blob.size(), cudaMemcpyHostToDevice, ctx->stream));
-  SB_CUDA(ctx, cudaEventRecord(ctx->blob_ev, ctx->stream));
+  // record-only pass: the blob for the current pointers, uploaded ahead of the replay
+  st = record_and_upload_blob(ctx, [&]() { return run_device(ctx, pairs, n, true); });
+  if (st != SB_OK) return st;
   if (!ctx->graph.exec || ctx->graph.key != key) {
     if (ctx->graph.exec) { cudaGraphExecDestroy(ctx->graph.exec); ctx->graph.exec = nullptr; }
     cudaStream_t cap = ctx->stream;
@@ -1104,19 +1116,30 @@ sb_status run_graph(sb_context* ctx, const sb_pair* pairs, int n) {
 sb_status run_host_io(sb_context* ctx, const sb_pair* pairs, int n, bool batched) {
   if (!ctx->s_in) SB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking));
   if (!ctx->s_out) SB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking));
-  // chunking: about 1.5 GB of inputs per chunk, at least one pair
+  // chunking: up to 1.5 GB of inputs per chunk, at least one pair; the chunk
+  // size ramps up from 256 MB at the start and back down at the end, so the
+  // first upload (nothing to overlap it with yet) and the last download are short
   std::vector<std::pair<int, int>> chunks;
-  {
-    int a = 0;
-    size_t acc = 0;
-    for (int i = 0; i < n; ++i) {
-      acc += (size_t)pairs[i].w * pairs[i].h * 6;
-      if (acc >= ((size_t)1536 << 20) || i == n - 1 || !batched) {
-        chunks.push_back({a, i + 1});
-        a = i + 1;
-        acc = 0;
-      }
+  if (!batched) {
+    for (int i = 0; i < n; ++i) chunks.push_back({i, i + 1});
+  } else {
+    std::vector<std::pair<int, int>> head, tail;
+    int lo = 0, hi = n;
+    const size_t cap = (size_t)1536 << 20;
+    for (int k = 0; lo < hi; ++k) {
+      const size_t target = std::min(cap, ((size_t)256 << 20) << std::min(k, 8));
+      size_t acc = 0;
+      const int a = lo;
+      while (lo < hi && (acc < target || lo == a)) acc += (size_t)pairs[lo].w * pairs[lo].h * 6, ++lo;
+      head.push_back({a, lo});
+      if (lo >= hi) break;
+      acc = 0;
+      const int b = hi;
+      while (hi > lo && (acc < target || hi == b)) --hi, acc += (size_t)pairs[hi].w * pairs[hi].h * 6;
+      tail.push_back({hi, b});
     }
+    chunks = head;
+    chunks.insert(chunks.end(), tail.rbegin(), tail.rend());
   }
   // staging per slot: left, right, out_rgb, out_disp for the largest chunk
   size_t slot = 0;
@@ -1128,58 +1151,93 @@ sb_status run_host_io(sb_context* ctx, const sb_pair* pairs, int n, bool batched
     }
     slot = std::max(slot, b);
   }
-  if (ctx->stage_bytes < 2 * slot) {
+  // three staging slots: the upload of chunk k waits for the download of
+  // chunk k-3, so a chunk's download and the next upload (longer together than
+  // one chunk's compute when the link carries both directions) do not stall it
+  constexpr int kSlots = 3;
+  if (ctx->stage_bytes < kSlots * slot) {
     SB_CUDA(ctx, cudaDeviceSynchronize());
     if (ctx->stage) cudaFree(ctx->stage);
     ctx->stage = nullptr;
     ctx->stage_bytes = 0;
-    cudaError_t e = cudaMalloc(&ctx->stage, 2 * slot);
-    if (e != cudaSuccess) { cudaGetLastError(); return fail(ctx, SB_ERR_OOM, "staging of %zu bytes failed", 2 * slot); }
-    ctx->stage_bytes = 2 * slot;
+    cudaError_t e = cudaMalloc(&ctx->stage, kSlots * slot);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(ctx, SB_ERR_OOM, "staging of %zu bytes failed", kSlots * slot); }
+    ctx->stage_bytes = kSlots * slot;
   }
+  // device-side pairs of every chunk (slot k % kSlots of the staging)
+  std::vector<std::vector<sb_pair>> dps(chunks.size());
+  for (size_t k = 0; k < chunks.size(); ++k) {
+    uint8_t* base = ctx->stage + (k % kSlots) * slot;
+    size_t o = 0;
+    for (int i = chunks[k].first; i < chunks[k].second; ++i) {
+      const size_t N = (size_t)pairs[i].w * pairs[i].h;
+      sb_pair q = pairs[i];
+      q.left_rgb = base + o; o += al(N * 3);
+      q.right_rgb = base + o; o += al(N * 3);
+      q.out_rgb = base + o; o += al(N * 3);
+      q.out_disp = (uint16_t*)(base + o); o += al(N * 2);
+      dps[k].push_back(q);
+    }
+  }
+  // the workspace for the largest chunk first: the recorded descriptors hold
+  // workspace addresses, so it must not move between the record pass and the run
+  {
+    size_t need = 0;
+    for (auto& dp : dps) {
+      size_t b = 0;
+      for (auto& q : dp) {
+        const size_t pb = pair_ws_bytes(Geo{q.w, q.h, q.p}, q.out_disp == nullptr);
+        b = batched ? b + pb : std::max(b, pb);
+      }
+      need = std::max(need, b);
+    }
+    sb_status s0 = ensure_ws(ctx, need);
+    if (s0 != SB_OK) return s0;
+  }
+  // every chunk's job descriptors in one upload ahead of the bulk copies:
+  // small uploads on the compute stream would otherwise queue behind the next
+  // chunk's bulk copy on the same copy engine and hold up the compute
+  sb_status st = record_and_upload_blob(ctx, [&]() {
+    for (size_t k = 0; k < chunks.size(); ++k) {
+      sb_status s2 = run_device(ctx, dps[k].data(), (int)dps[k].size(), batched);
+      if (s2 != SB_OK) return s2;
+    }
+    return SB_OK;
+  });
+  if (st != SB_OK) return st;
   std::vector<cudaEvent_t> ev_in(chunks.size()), ev_comp(chunks.size()), ev_out(chunks.size());
   for (size_t k = 0; k < chunks.size(); ++k) {
     cudaEventCreateWithFlags(&ev_in[k], cudaEventDisableTiming);
     cudaEventCreateWithFlags(&ev_comp[k], cudaEventDisableTiming);
     cudaEventCreateWithFlags(&ev_out[k], cudaEventDisableTiming);
   }
-  sb_status st = SB_OK;
+  ctx->blob.clear();
+  ctx->sink = 1;   // the same uploads as the record pass: offsets into the uploaded blob
   for (size_t k = 0; k < chunks.size() && st == SB_OK; ++k) {
-    uint8_t* base = ctx->stage + (k & 1) * slot;
-    std::vector<sb_pair> dp;
-    size_t o = 0;
-    if (k >= 2) {  // the slot's previous chunk must be computed and copied out
-      cudaStreamWaitEvent(ctx->s_in, ev_comp[k - 2], 0);
-      cudaStreamWaitEvent(ctx->s_in, ev_out[k - 2], 0);
+    if (k >= (size_t)kSlots) {  // the slot's previous chunk must be computed and copied out
+      cudaStreamWaitEvent(ctx->s_in, ev_comp[k - kSlots], 0);
+      cudaStreamWaitEvent(ctx->s_in, ev_out[k - kSlots], 0);
     }
-    for (int i = chunks[k].first; i < chunks[k].second; ++i) {
-      const size_t N = (size_t)pairs[i].w * pairs[i].h;
-      sb_pair q = pairs[i];
-      uint8_t* l = base + o; o += al(N * 3);
-      uint8_t* r = base + o; o += al(N * 3);
-      uint8_t* out = base + o; o += al(N * 3);
-      uint16_t* dd = (uint16_t*)(base + o); o += al(N * 2);
-      cudaMemcpyAsync(l, pairs[i].left_rgb, N * 3, cudaMemcpyHostToDevice, ctx->s_in);
-      cudaMemcpyAsync(r, pairs[i].right_rgb, N * 3, cudaMemcpyHostToDevice, ctx->s_in);
-      q.left_rgb = l;
-      q.right_rgb = r;
-      q.out_rgb = out;
-      q.out_disp = dd;
-      dp.push_back(q);
+    for (size_t j = 0; j < dps[k].size(); ++j) {
+      const sb_pair& hp = pairs[chunks[k].first + j];
+      const size_t N = (size_t)hp.w * hp.h;
+      cudaMemcpyAsync((void*)dps[k][j].left_rgb, hp.left_rgb, N * 3, cudaMemcpyHostToDevice, ctx->s_in);
+      cudaMemcpyAsync((void*)dps[k][j].right_rgb, hp.right_rgb, N * 3, cudaMemcpyHostToDevice, ctx->s_in);
     }
     cudaEventRecord(ev_in[k], ctx->s_in);
     cudaStreamWaitEvent(ctx->stream, ev_in[k], 0);
-    st = run_device(ctx, dp.data(), (int)dp.size(), batched);
+    st = run_device(ctx, dps[k].data(), (int)dps[k].size(), batched);
     cudaEventRecord(ev_comp[k], ctx->stream);
     cudaStreamWaitEvent(ctx->s_out, ev_comp[k], 0);
-    for (size_t j = 0; j < dp.size(); ++j) {
+    for (size_t j = 0; j < dps[k].size(); ++j) {
       const sb_pair& hp = pairs[chunks[k].first + j];
       const size_t N = (size_t)hp.w * hp.h;
-      cudaMemcpyAsync(hp.out_rgb, dp[j].out_rgb, N * 3, cudaMemcpyDeviceToHost, ctx->s_out);
-      if (hp.out_disp) cudaMemcpyAsync(hp.out_disp, dp[j].out_disp, N * 2, cudaMemcpyDeviceToHost, ctx->s_out);
+      cudaMemcpyAsync(hp.out_rgb, dps[k][j].out_rgb, N * 3, cudaMemcpyDeviceToHost, ctx->s_out);
+      if (hp.out_disp) cudaMemcpyAsync(hp.out_disp, dps[k][j].out_disp, N * 2, cudaMemcpyDeviceToHost, ctx->s_out);
     }
     cudaEventRecord(ev_out[k], ctx->s_out);
   }
+  ctx->sink = 0;
   // the caller's stream sees the end of the copies
   if (!chunks.empty()) cudaStreamWaitEvent(ctx->stream, ev_out.back(), 0);
   for (size_t k = 0; k < chunks.size(); ++k) {
