@@ -520,8 +520,10 @@ def run_ours(args):
                          "ops_per_launch": ops},
             "e2e": e2e,
             "autotune": {"box_sum_work_items": {"batched": tune_batched[0], "per_pair": tune_plain[0]},
-                         "candidate_ms": {"batched": tune_batched[1], "per_pair": tune_plain[1]},
-                         "candidates": "1, 2, 3, 6 waves of the persistent box-sum grid"},
+                         "blur_tile_rows": {"batched": tune_batched[1], "per_pair": tune_plain[1]},
+                         "candidate_ms": {"batched": tune_batched[2], "per_pair": tune_plain[2]},
+                         "candidates": "box-sum split of 1, 2, 3, 6 waves of the persistent grid; "
+                                       "then blur tiles of 112 and 64 rows"},
             "uneven_batch": uneven,
             "serving": serving,
             "gpu_launches": launches,

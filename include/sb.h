@@ -227,19 +227,22 @@ sb_status sb_boundary_sad_static(const uint8_t* L_left, const uint8_t* L_right, 
                                  int32_t h, int32_t max_disp, int32_t block, int32_t variant, uint16_t* disp,
                                  uint32_t* cost, void* cuda_stream, char* errbuf, size_t errbuf_len);
 
-/* Autotuning of the box-sum SAD's work split (how many (pair, strip,
- * disparity chunk, row band) items one launch is cut into: more items balance
- * the persistent grid better, fewer repeat less warm-up work per band).  Runs
- * the pairs with sb_run(flags) once per candidate (1, 2, 3 and 6 waves of the
- * grid; a warm-up run and a timed run each, so the outputs are written), keeps
- * the fastest for the launch-group shape (each pair's w, h, max_disp and
- * block, in order) and uses it in every later sb_run of that shape on this
- * context.  Device pairs only (flags without SB_RUN_HOST_IO).  ms_out: NULL
- * or SB_AUTOTUNE_CANDIDATES timings; target_out: NULL or the chosen item
- * count.  Synchronises the context stream; not inside a stream capture. */
-#define SB_AUTOTUNE_CANDIDATES 4
+/* Autotuning of two work shapes per launch-group shape (each pair's w, h,
+ * max_disp, block and blur radius, in order): the box-sum SAD's work split
+ * (how many (pair, strip, disparity chunk, row band) items a launch is cut
+ * into: more items balance the persistent grid better, fewer repeat less
+ * warm-up work per band; candidates 1, 2, 3 and 6 waves of the grid) and the
+ * blur tile height (112 rows, two CTAs per SM, or 64 rows, three CTAs per SM
+ * with more halo work).  Runs the pairs with sb_run(flags) once per candidate
+ * (a warm-up run and a timed run each, so the outputs are written), keeps the
+ * fastest and uses it in every later sb_run of that shape on this context.
+ * Device pairs only (flags without SB_RUN_HOST_IO).  ms_out: NULL or
+ * SB_AUTOTUNE_CANDIDATES timings (4 splits, then 2 blur tiles);
+ * sad_items_out / blur_rows_out: NULL or the chosen values.  Synchronises the
+ * context stream; not inside a stream capture. */
+#define SB_AUTOTUNE_CANDIDATES 6
 sb_status sb_autotune(sb_context* ctx, const sb_pair* pairs, int32_t n_pairs, uint32_t flags, float* ms_out,
-                      int32_t* target_out);
+                      int32_t* sad_items_out, int32_t* blur_rows_out);
 
 /* Left-right consistency of a left-view disparity map dL and a right-view map
  * dR of the same pair (both uint16 h*w device arrays as sb_run writes them):

@@ -87,7 +87,7 @@ def _load():
         "sb_boundary_sad": ([V, V, V, V, I32, I32, I32, I32, I32, V, V], ctypes.c_int),
         "sb_reconstruct_disparity": ([V, V, I32, I32, I32, I32, I32, I32, V], ctypes.c_int),
         "sb_lr_consistency": ([V, V, V, I32, I32, I32, V, V], ctypes.c_int),
-        "sb_autotune": ([V, V, I32, ctypes.c_uint32, V, V], ctypes.c_int),
+        "sb_autotune": ([V, V, I32, ctypes.c_uint32, V, V, V], ctypes.c_int),
         "sb_selective_blur": ([V, V, V, I32, I32, V, I32, ctypes.c_float, V], ctypes.c_int),
         "sb_run": ([V, ctypes.POINTER(sb_pair), I32, U32], ctypes.c_int),
         "sb_profile_enable": ([V, ctypes.c_int], ctypes.c_int),
@@ -285,14 +285,14 @@ def _pairs_array(pairs: List[Pair]):
 
 
 def sb_autotune(ctx: Context, pairs: List[Pair], flags: int = SB_RUN_PLAIN):
-    """Times the candidate box-sum work splits on these pairs (running them),
-    keeps the fastest for their shape on this context; -> (items, [ms per
-    candidate])."""
+    """Times the candidate box-sum work splits and blur tile heights on these
+    pairs (running them), keeps the fastest for their shape on this context;
+    -> (work items, blur rows, [ms per candidate])."""
     arr = _pairs_array(pairs)
-    ms = (ctypes.c_float * 4)()
-    chosen = ctypes.c_int32(0)
-    _check(ctx, _lib.sb_autotune(ctx.handle, arr, len(pairs), flags, ms, ctypes.byref(chosen)))
-    return int(chosen.value), [float(v) for v in ms]
+    ms = (ctypes.c_float * 6)()
+    items, rows = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(ctx, _lib.sb_autotune(ctx.handle, arr, len(pairs), flags, ms, ctypes.byref(items), ctypes.byref(rows)))
+    return int(items.value), int(rows.value), [float(v) for v in ms]
 
 
 def sb_run(ctx: Context, pairs: List[Pair], flags: int = SB_RUN_PLAIN):

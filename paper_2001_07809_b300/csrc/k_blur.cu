@@ -11,13 +11,16 @@
 // of each input row's byte run, when the tile fits in shared memory.
 // Only pixels whose disparity lies in no range of interest take the blurred
 // value; the rest are copied, and a tile with no such pixel is copied as is.
+#include <algorithm>
 #include "sb_common.cuh"
 
 namespace sb {
 
 namespace {
 constexpr int BX = 64;    // output columns per tile
-constexpr int BY = 112;   // output rows per tile (a multiple of OB)
+// Output rows per tile (a multiple of OB), a template parameter: 112 (two
+// CTAs per SM at sigma 8) or 64 (more halo rows per output row, but three
+// CTAs per SM); the autotuner picks per batch shape.
 constexpr int OB = 16;    // outputs per thread per pass (register window)
 constexpr int kBlurThreads = 256;
 constexpr int kAll3Limit = 110 * 1024;  // stage the three channels together up to this size (2 CTAs/SM)
@@ -104,6 +107,7 @@ struct BlurGeo {
 // window refill), the blur mask [BY][BX], then the input tile: three
 // interleaved channels, rows of sr bytes that start at a per-row offset of
 // 0..15 bytes (the cp.async source alignment), or one channel [ih][iw].
+template <int BY>
 __host__ __device__ inline BlurGeo blur_geo(int R) {
   BlurGeo g;
   g.nt = 2 * R + 1;
@@ -119,8 +123,9 @@ __host__ __device__ inline BlurGeo blur_geo(int R) {
 }
 }  // namespace
 
-__host__ __device__ int blur_smem_bytes(int R) { return blur_geo(R).bytes; }
+__host__ __device__ int blur_smem_bytes(int R, int by) { return by == 64 ? blur_geo<64>(R).bytes : blur_geo<112>(R).bytes; }
 
+template <int BY>
 __global__ void __launch_bounds__(kBlurThreads) k_blur(const BlurJob* __restrict__ jobs) {
   extern __shared__ __align__(16) float fsm[];
   __shared__ int s_any;
@@ -133,7 +138,7 @@ __global__ void __launch_bounds__(kBlurThreads) k_blur(const BlurJob* __restrict
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ox = min(BX, w - tx0), oy = min(BY, h - ty0);
   const int nr = J.n_ranges;
-  const BlurGeo G = blur_geo(R);
+  const BlurGeo G = blur_geo<BY>(R);
   const int nt = G.nt, iw = G.iw, ih = G.ih, sr = G.sr;
   const int nch = G.all3 ? 3 : 1;
   float* s_tap = fsm;
@@ -261,14 +266,22 @@ __global__ void __launch_bounds__(kBlurThreads) k_blur(const BlurJob* __restrict
   }
 }
 
-void launch_blur(const BlurJob* jobs, int n_jobs, int max_w, int max_h, int max_R, cudaStream_t s) {
-  if (n_jobs <= 0) return;
+template <int BY>
+void launch_blur_by(const BlurJob* jobs, int n_jobs, int max_w, int max_h, int max_R, cudaStream_t s) {
   // every job's own layout (three channels or one) fits in the largest job's size
   int smem = 0;
-  for (int R = 0; R <= max_R; ++R) smem = smem > blur_smem_bytes(R) ? smem : blur_smem_bytes(R);
-  cudaFuncSetAttribute(k_blur, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  for (int R = 0; R <= max_R; ++R) smem = std::max(smem, blur_geo<BY>(R).bytes);
+  cudaFuncSetAttribute(k_blur<BY>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   dim3 grid((max_w + BX - 1) / BX, (max_h + BY - 1) / BY, n_jobs);
-  k_blur<<<grid, kBlurThreads, smem, s>>>(jobs);
+  k_blur<BY><<<grid, kBlurThreads, smem, s>>>(jobs);
+}
+
+void launch_blur(const BlurJob* jobs, int n_jobs, int max_w, int max_h, int max_R, int by, cudaStream_t s) {
+  if (n_jobs <= 0) return;
+  if (by == 64)
+    launch_blur_by<64>(jobs, n_jobs, max_w, max_h, max_R, s);
+  else
+    launch_blur_by<112>(jobs, n_jobs, max_w, max_h, max_R, s);
 }
 
 }  // namespace sb

@@ -201,7 +201,9 @@ struct sb_context {
   // autotune cache: launch-group shape (each pair's w, h, D, block) -> the
   // box-sum SAD's work-item target chosen by sb_autotune
   std::map<std::string, int> tuned;
+  std::map<std::string, int> tuned_blur;   // same shapes -> blur tile height (112 or 64)
   int sad_target_override = 0;   // set while sb_autotune times a candidate
+  int blur_by_override = 0;
   int sms = 148;
 };
 
@@ -439,10 +441,18 @@ struct PairRun {
 std::string shape_key(const Geo* geos, int n) {
   std::string key;
   for (int i = 0; i < n; ++i) {
-    const int32_t v[4] = {geos[i].w, geos[i].h, geos[i].p.max_disp, geos[i].p.block};
+    const int32_t v[5] = {geos[i].w, geos[i].h, geos[i].p.max_disp, geos[i].p.block,
+                          (int32_t)ceil(3.0 * (double)geos[i].p.sigma)};
     key.append((const char*)v, sizeof v);
   }
   return key;
+}
+
+// Blur tile height: the candidate being timed, else the tuned value, else 112.
+int blur_rows(const sb_context* ctx, const std::string& key) {
+  if (ctx->blur_by_override > 0) return ctx->blur_by_override;
+  auto it = ctx->tuned_blur.find(key);
+  return it != ctx->tuned_blur.end() ? it->second : 112;
 }
 
 // Box-sum work items a launch aims for: the candidate being timed, else the
@@ -642,7 +652,9 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
     const BlurJob* d = upload(ctx, J, &st);
     if (!d) return st;
     if (!ctx->dry) {
-      launch_blur(d, n, max_w, max_h, max_R, s);
+      std::vector<Geo> geos;
+      for (auto& r : runs) geos.push_back(r.g);
+      launch_blur(d, n, max_w, max_h, max_R, blur_rows(ctx, shape_key(geos.data(), n)), s);
       SB_LAUNCHED(ctx, 1);
     }
   }
@@ -972,7 +984,7 @@ sb_status sb_selective_blur(sb_context* ctx, const uint8_t* rgb, const uint16_t*
   std::vector<BlurJob> J{b};
   const BlurJob* d = upload(ctx, J, &st);
   if (!d) return st;
-  launch_blur(d, 1, w, h, R, ctx->stream);
+  launch_blur(d, 1, w, h, R, 112, ctx->stream);
   SB_LAUNCHED(ctx, 1);
   return SB_OK;
 }
@@ -1062,6 +1074,8 @@ sb_status run_graph(sb_context* ctx, const sb_pair* pairs, int n) {
     for (int i = 0; i < n; ++i) geos.push_back(Geo{pairs[i].w, pairs[i].h, pairs[i].p});
     const int64_t target = sad_target(ctx, shape_key(geos.data(), n));
     key.append((const char*)&target, sizeof target);
+    const int32_t by = blur_rows(ctx, shape_key(geos.data(), n));
+    key.append((const char*)&by, sizeof by);
   }
   for (int i = 0; i < n; ++i) {
     const sb_pair& q = pairs[i];
@@ -1253,51 +1267,71 @@ sb_status run_host_io(sb_context* ctx, const sb_pair* pairs, int n, bool batched
 }  // namespace
 
 extern "C" sb_status sb_autotune(sb_context* ctx, const sb_pair* pairs, int32_t n_pairs, uint32_t flags,
-                                 float* ms_out, int32_t* target_out) {
+                                 float* ms_out, int32_t* sad_items_out, int32_t* blur_rows_out) {
   if (!ctx) return SB_ERR_INVALID_ARG;
   if (n_pairs <= 0 || !pairs) return fail(ctx, SB_ERR_INVALID_ARG, "sb_autotune: no pairs");
   if (ctx->capturing) return fail(ctx, SB_ERR_INVALID_ARG, "sb_autotune cannot run inside a stream capture");
   if (flags & SB_RUN_HOST_IO)
     return fail(ctx, SB_ERR_INVALID_ARG, "sb_autotune takes device pairs (host-buffer runs split into their own groups)");
   cudaSetDevice(ctx->device);
-  // candidates: 1, 2, 3 and 6 waves of the persistent box-sum grid
-  const int waves[SB_AUTOTUNE_CANDIDATES] = {1, 2, 3, 6};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   SB_CUDA(ctx, cudaEventCreate(&e0));
   SB_CUDA(ctx, cudaEventCreate(&e1));
-  float best_ms = 0.f;
-  int best = 0;
-  sb_status st = SB_OK;
-  for (int c = 0; c < SB_AUTOTUNE_CANDIDATES && st == SB_OK; ++c) {
-    ctx->sad_target_override = ctx->sms * 2 * waves[c];
-    st = sb_run(ctx, pairs, n_pairs, flags);   // warm-up (and graph capture)
-    if (st != SB_OK) break;
+  // one candidate: a warm-up run (and graph capture), then a timed run
+  auto time_run = [&](float* ms) -> sb_status {
+    sb_status st = sb_run(ctx, pairs, n_pairs, flags);
+    if (st != SB_OK) return st;
     cudaEventRecord(e0, ctx->stream);
     st = sb_run(ctx, pairs, n_pairs, flags);
-    if (st != SB_OK) break;
+    if (st != SB_OK) return st;
     cudaEventRecord(e1, ctx->stream);
-    if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(ctx, SB_ERR_CUDA, "sb_autotune: event wait failed"); break; }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms_out) ms_out[c] = ms;
-    if (c == 0 || ms < best_ms) { best_ms = ms; best = ctx->sad_target_override; }
+    if (cudaEventSynchronize(e1) != cudaSuccess) return fail(ctx, SB_ERR_CUDA, "sb_autotune: event wait failed");
+    cudaEventElapsedTime(ms, e0, e1);
+    return SB_OK;
+  };
+  // candidates 0-3: the box-sum work split, 1, 2, 3 and 6 waves of the
+  // persistent grid (blur tiles of 112 rows); candidates 4-5: blur tiles of
+  // 112 and 64 rows with the chosen split
+  const int waves[4] = {1, 2, 3, 6}, rows[2] = {112, 64};
+  float ms[SB_AUTOTUNE_CANDIDATES] = {};
+  int best_items = 0, best_rows = 112;
+  float best_ms = 0.f;
+  sb_status st = SB_OK;
+  ctx->blur_by_override = 112;
+  for (int c = 0; c < 4 && st == SB_OK; ++c) {
+    ctx->sad_target_override = ctx->sms * 2 * waves[c];
+    st = time_run(&ms[c]);
+    if (st == SB_OK && (c == 0 || ms[c] < best_ms)) { best_ms = ms[c]; best_items = ctx->sad_target_override; }
+  }
+  for (int c = 0; c < 2 && st == SB_OK; ++c) {
+    ctx->sad_target_override = best_items;
+    ctx->blur_by_override = rows[c];
+    st = time_run(&ms[4 + c]);
+    if (st == SB_OK && (c == 0 || ms[4 + c] < best_ms)) { best_ms = ms[4 + c]; best_rows = rows[c]; }
   }
   ctx->sad_target_override = 0;
+  ctx->blur_by_override = 0;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != SB_OK) return st;
   // the shape of each launch group sb_run forms with these flags
+  auto keep = [&](const std::string& key) {
+    ctx->tuned[key] = best_items;
+    ctx->tuned_blur[key] = best_rows;
+  };
   if (flags & SB_RUN_BATCHED) {
     std::vector<Geo> geos;
     for (int i = 0; i < n_pairs; ++i) geos.push_back(Geo{pairs[i].w, pairs[i].h, pairs[i].p});
-    ctx->tuned[shape_key(geos.data(), n_pairs)] = best;
+    keep(shape_key(geos.data(), n_pairs));
   } else {
     for (int i = 0; i < n_pairs; ++i) {
       Geo g{pairs[i].w, pairs[i].h, pairs[i].p};
-      ctx->tuned[shape_key(&g, 1)] = best;
+      keep(shape_key(&g, 1));
     }
   }
-  if (target_out) *target_out = best;
+  if (ms_out) memcpy(ms_out, ms, sizeof ms);
+  if (sad_items_out) *sad_items_out = best_items;
+  if (blur_rows_out) *blur_rows_out = best_rows;
   return SB_OK;
 }
 

@@ -172,7 +172,8 @@ struct BlurJob {
   int32_t w, h, R, n_ranges;
   int32_t lo[8], hi[8];
 };
-void launch_blur(const BlurJob* jobs, int n_jobs, int max_w, int max_h, int max_R, cudaStream_t s);
-__host__ __device__ int blur_smem_bytes(int R);
+// by: output rows per tile, 112 or 64
+void launch_blur(const BlurJob* jobs, int n_jobs, int max_w, int max_h, int max_R, int by, cudaStream_t s);
+__host__ __device__ int blur_smem_bytes(int R, int by);
 
 }  // namespace sb

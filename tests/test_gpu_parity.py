@@ -393,8 +393,13 @@ def test_autotune_keeps_results_and_caches_the_split(ctx):
         pairs.append(sb.Pair(dev(left), dev(right), params_of(p, sb.SB_SAD_BOXSUM), o, d))
         outs.append((o, d))
     for flags in (sb.SB_RUN_BATCHED | sb.SB_RUN_GRAPH, sb.SB_RUN_PLAIN):
-        chosen, ms = sb.sb_autotune(ctx, pairs, flags)
-        assert chosen in [ctx_sms() * 2 * k for k in (1, 2, 3, 6)] and all(m > 0 for m in ms)
+        chosen, rows, ms = sb.sb_autotune(ctx, pairs, flags)
+        assert chosen in [ctx_sms() * 2 * k for k in (1, 2, 3, 6)] and rows in (64, 112)
+        assert len(ms) == 6 and all(m > 0 for m in ms)
+        ctx.synchronize()
+        # the tuner's last run used 64-row blur tiles: its outputs are checked too
+        for (o, d), (b_rgb, b_disp) in zip(outs, before):
+            assert np.array_equal(host(o), b_rgb) and np.array_equal(host(d, np.uint16), b_disp)
         sb.sb_run(ctx, pairs, flags)
         ctx.synchronize()
         for (o, d), (b_rgb, b_disp) in zip(outs, before):
