@@ -273,6 +273,147 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
   }  // next work item
 }
 
+// Tail disparities (see sad_has_tail): a persistent grid over work items
+// (pair, strip of sad_tail_strip(r) outputs, row band).  Thread t owns strip
+// column c = x0 - r + t and keeps, per tail disparity d = dt0 + k, the vertical
+// window sum V_k of |L(., c) - R(., c - d)| sliding down the band.  Rows are
+// taken in groups of kTailRows outputs, so that one round of independent loads
+// and three barriers serve a group:
+//   1. stage: the group's entering rows (y + r) and leaving rows (y - r) of
+//      both images (the right one over the strip's columns shifted by dt0,
+//      with kTailMax - 1 more columns on the left for the larger d) and its
+//      anchor flags go to shared memory;
+//   2. vertical: per output row V_k += entering cell, store V_k as that row's
+//      column sums, V_k -= leaving cell;
+//   3. horizontal: one warp per (row, disparity) line turns the line's column
+//      sums into prefix sums P in place (8 values per lane and a warp scan),
+//      and the window sum at strip output l is P[l + 2r] - P[l - 1]; anchors
+//      keep (S << 10 | d) with atomicMin into the argmin keys.
+constexpr int kTailRows = 8;                    // output rows per group
+constexpr int kTailRStride = 256 + 16;          // staged right-image bytes per row
+__host__ __device__ inline int tail_smem_bytes(int max_rem) {
+  return kTailRows * max_rem * 256 * 4 + 2 * kTailRows * 256 + 2 * kTailRows * kTailRStride + kTailRows * 256;
+}
+
+__global__ void __launch_bounds__(256) k_sad_tail(const SadJob* __restrict__ jobs, const SadItem* __restrict__ items,
+                                                  int n_items, unsigned* __restrict__ queue, int max_rem) {
+  extern __shared__ __align__(16) uint8_t t_smem[];
+  uint32_t* s_v = reinterpret_cast<uint32_t*>(t_smem);            // [kTailRows][max_rem][256] column sums
+  uint8_t* s_l = t_smem + kTailRows * max_rem * 1024;              // [2 kTailRows][256] left bytes
+  uint8_t* s_r = s_l + 2 * kTailRows * 256;                        // [2 kTailRows][kTailRStride] right bytes
+  uint8_t* s_b = s_r + 2 * kTailRows * kTailRStride;               // [kTailRows][256] anchor flags
+  __shared__ int s_item;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_item = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    if (s_item >= n_items) break;
+    const SadItem it = items[s_item];
+    const SadJob J = jobs[it.job];
+    if (sad_use_direct(J)) continue;
+    const int r = J.r, D = J.D, w = J.w;
+    const int dt0 = it.d0, rem = D + 1 - dt0;
+    const int TX = sad_tail_strip(r), NC = TX + 2 * r;
+    const int x0 = it.x0, c = x0 - r + tid;
+    const bool colv = tid < NC && c <= w - 1;       // c >= D, so c - d >= 0 for every d <= D
+    const int cr0 = x0 - r - dt0 - (kTailMax - 1);  // right-image column of staged byte 0
+    const int nr = NC + kTailMax - 1;               // staged right-image bytes per row (<= 263)
+    const int xo0 = D + r, xo1 = w - 1 - r;
+    // slot q of the staging rows <- image row `row`
+    auto stage = [&](int q, int row) {
+      const int64_t rb = (int64_t)row * w;
+      if (colv) s_l[q * 256 + tid] = J.Ll[rb + c];
+      for (int i = tid; i < nr; i += 256) {
+        const int col = cr0 + i;
+        s_r[q * kTailRStride + i] = (col >= 0 && col < w) ? J.Lr[rb + col] : (uint8_t)0;
+      }
+    };
+    // |L - R| of disparity dt0 + k at this thread's column, staging slot q
+    auto cell = [&](int q, int k) -> uint32_t {
+      const int lv = s_l[q * 256 + tid], rv = s_r[q * kTailRStride + tid + kTailMax - 1 - k];
+      return (uint32_t)(lv > rv ? lv - rv : rv - lv);
+    };
+    uint32_t V[kTailMax];
+#pragma unroll
+    for (int k = 0; k < kTailMax; ++k) V[k] = 0u;
+    // warm-up: rows y0 - r .. y0 + r - 1, 2 kTailRows at a time
+    for (int row0 = it.y0 - r; row0 < it.y0 + r; row0 += 2 * kTailRows) {
+      const int n = min(2 * kTailRows, it.y0 + r - row0);
+      for (int q = 0; q < n; ++q) stage(q, row0 + q);
+      __syncthreads();
+      if (colv)
+        for (int q = 0; q < n; ++q)
+#pragma unroll
+          for (int k = 0; k < kTailMax; ++k)
+            if (k < rem) V[k] += cell(q, k);
+      __syncthreads();
+    }
+    for (int yg = it.y0; yg <= it.y1; yg += kTailRows) {
+      const int G = min(kTailRows, it.y1 - yg + 1);
+      for (int j = 0; j < G; ++j) {
+        stage(j, yg + j + r);
+        stage(kTailRows + j, yg + j - r);
+        if (tid < TX) {
+          const int x = x0 + tid, y = yg + j;
+          s_b[j * 256 + tid] = x <= xo1 && (x == xo0 || x == xo1 || J.bmap[(int64_t)y * w + x]);
+        }
+      }
+      __syncthreads();
+      for (int j = 0; j < G; ++j) {
+#pragma unroll
+        for (int k = 0; k < kTailMax; ++k)
+          if (k < rem) {
+            if (colv) V[k] += cell(j, k);
+            s_v[(j * max_rem + k) * 256 + tid] = colv ? V[k] : 0u;
+            if (colv) V[k] -= cell(kTailRows + j, k);
+          }
+      }
+      __syncthreads();
+      for (int line = warp; line < G * rem; line += 8) {
+        const int j = line / rem, k = line - j * rem;
+        uint32_t* P = s_v + (j * max_rem + k) * 256;
+        uint4 a = reinterpret_cast<uint4*>(P)[2 * lane], b = reinterpret_cast<uint4*>(P)[2 * lane + 1];
+        a.y += a.x; a.z += a.y; a.w += a.z;
+        b.x += a.w; b.y += b.x; b.z += b.y; b.w += b.z;
+        uint32_t t = b.w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t u = __shfl_up_sync(0xffffffffu, t, o);
+          if (lane >= o) t += u;
+        }
+        const uint32_t ex = t - b.w;   // sum of the lanes before this one
+        a.x += ex; a.y += ex; a.z += ex; a.w += ex;
+        b.x += ex; b.y += ex; b.z += ex; b.w += ex;
+        reinterpret_cast<uint4*>(P)[2 * lane] = a;
+        reinterpret_cast<uint4*>(P)[2 * lane + 1] = b;
+        __syncwarp();
+        const int y = yg + j;
+        for (int xl = lane; xl < TX; xl += 32)
+          if (s_b[j * 256 + xl]) {
+            const uint32_t S = P[xl + 2 * r] - (xl > 0 ? P[xl - 1] : 0u);
+            atomicMin(&J.key[(int64_t)y * w + x0 + xl], (S << SB_KEY_DBITS) | (uint32_t)(dt0 + k));
+          }
+        __syncwarp();
+      }
+      __syncthreads();   // staging rows and column sums are rewritten by the next group
+    }
+  }
+}
+
+void launch_sad_tail(const SadJob* jobs, const SadItem* items, int n_items, int max_rem, unsigned* queue,
+                     cudaStream_t s) {
+  if (n_items <= 0) return;
+  const int smem = tail_smem_bytes(max_rem);
+  cudaFuncSetAttribute(k_sad_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int dev = 0, sms = 148, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sad_tail, 256, smem);
+  const int grid = std::min(n_items, sms * std::max(1, per_sm));
+  k_sad_tail<<<grid, 256, smem, s>>>(jobs, items, n_items, queue, max_rem);
+}
+
 int sad_boxsum_smem_bytes(int r) {
   const int ring = 2 * r + 1 + 2 * kGroup;
   return (ring + 1) * kRowBytes + 2 * kGroup * kBBytes + kGroup * kVsCols * kVsStride;

@@ -170,7 +170,7 @@ struct sb_context {
   uint64_t launches = 0;
   uint8_t* tables = nullptr;  // lin (512 B) | coarse (4096 B) | thr (257 x 4 B)
   uint32_t* dev_err = nullptr;
-  unsigned* sad_queue = nullptr;  // work-item cursor of the box-sum SAD kernel
+  unsigned* sad_queue = nullptr;  // work-item cursors of the box-sum SAD and tail kernels
   uint8_t* ws = nullptr;
   size_t ws_bytes = 0;
   Uploader up;
@@ -379,14 +379,17 @@ void sad_choice(const Geo& g, const int64_t* nb, SadJob* j, bool* direct_possibl
 
 // Box-sum work items: (pair, strip, disparity chunk, row band); bands are cut
 // so that a small batch still fills the GPU.
-void sad_items(const std::vector<std::pair<int, Geo>>& pairs, int64_t target, std::vector<SadItem>* items) {
-  int64_t base = 0;
+void sad_items(const std::vector<std::pair<int, Geo>>& pairs, int64_t target, int sms, std::vector<SadItem>* items,
+               std::vector<SadItem>* tail) {
+  int64_t base = 0, tail_strips = 0;
   for (auto& pg : pairs) {
     const Geo& g = pg.second;
     const int r = (g.p.block - 1) / 2, D = g.p.max_disp;
     const int TX = sad_boxsum_strip(r);
     const int ncols = g.w - D - 2 * r;
-    base += (int64_t)((ncols + TX - 1) / TX) * ((D + 1 + kSadChunk - 1) / kSadChunk);
+    const int chunks = sad_has_tail(D) ? sad_tail_first(D) / kSadChunk : (D + 1 + kSadChunk - 1) / kSadChunk;
+    base += (int64_t)((ncols + TX - 1) / TX) * chunks;
+    if (sad_has_tail(D)) tail_strips += (ncols + sad_tail_strip(r) - 1) / sad_tail_strip(r);
   }
   // (cost, item): cost = rows including the 2r warm-up rows x the strip's columns
   std::vector<std::pair<int64_t, SadItem>> list;
@@ -396,6 +399,7 @@ void sad_items(const std::vector<std::pair<int, Geo>>& pairs, int64_t target, st
     const int TX = sad_boxsum_strip(r);
     const int xo0 = D + r, xo1 = g.w - 1 - r, yo0 = r, yo1 = g.h - 1 - r;
     const int rows = yo1 - yo0 + 1;
+    const int dend = sad_has_tail(D) ? sad_tail_first(D) : D + 1;   // box-sum chunks cover d < dend
     int bands = (int)std::max<int64_t>(1, (target + base - 1) / std::max<int64_t>(base, 1));
     bands = std::min(bands, std::max(1, rows / std::max(8 * r, 64)));
     for (int b = 0; b < bands; ++b) {
@@ -403,7 +407,25 @@ void sad_items(const std::vector<std::pair<int, Geo>>& pairs, int64_t target, st
       if (ya > yb) continue;
       const int64_t cost = (int64_t)(yb - ya + 1 + 2 * r) * (TX + 2 * r);
       for (int x0 = xo0; x0 <= xo1; x0 += TX)
-        for (int d0 = 0; d0 <= D; d0 += kSadChunk) list.push_back({cost, SadItem{pg.first, x0, d0, ya, yb}});
+        for (int d0 = 0; d0 < dend; d0 += kSadChunk) list.push_back({cost, SadItem{pg.first, x0, d0, ya, yb}});
+    }
+    if (sad_has_tail(D)) {
+      // tail items: the band count that minimises (rounds of the persistent
+      // grid, eight 256-thread CTAs per SM) x (band rows + 2r warm-up rows)
+      const int TT = sad_tail_strip(r);
+      const int64_t slots = (int64_t)sms * 8;
+      int tb = 1;
+      int64_t best = -1;
+      for (int t = 1; t <= 16 && t <= rows; ++t) {
+        const int64_t rounds = (tail_strips * t + slots - 1) / slots;
+        const int64_t c = rounds * ((rows + t - 1) / t + 2 * r);
+        if (best < 0 || c < best) { best = c; tb = t; }
+      }
+      for (int b = 0; b < tb; ++b) {
+        const int ya = yo0 + (int)((int64_t)rows * b / tb), yb = yo0 + (int)((int64_t)rows * (b + 1) / tb) - 1;
+        if (ya > yb) continue;
+        for (int x0 = xo0; x0 <= xo1; x0 += TT) tail->push_back(SadItem{pg.first, x0, sad_tail_first(D), ya, yb});
+      }
     }
   }
   // largest first, so the persistent kernel ends on short items (ties keep generation order)
@@ -586,16 +608,27 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
     if (!box.empty()) {
       std::vector<Geo> geos;
       for (auto& r : runs) geos.push_back(r.g);
-      std::vector<SadItem> items;
-      sad_items(box, sad_target(ctx, shape_key(geos.data(), n)), &items);
+      std::vector<SadItem> items, tail;
+      sad_items(box, sad_target(ctx, shape_key(geos.data(), n)), ctx->sms, &items, &tail);
       const SadItem* di = upload(ctx, items, &st);
       if (!di) return st;
+      const SadItem* dt = tail.empty() ? nullptr : upload(ctx, tail, &st);
+      if (!tail.empty() && !dt) return st;
       int max_r = 0;
-      for (auto& b : box) max_r = std::max(max_r, (b.second.p.block - 1) / 2);
-      SB_MEMSET(ctx, (ctx->sad_queue, 0, 4, s));
+      int max_rem = 1;
+      for (auto& b : box) {
+        max_r = std::max(max_r, (b.second.p.block - 1) / 2);
+        if (sad_has_tail(b.second.p.max_disp))
+          max_rem = std::max(max_rem, b.second.p.max_disp + 1 - sad_tail_first(b.second.p.max_disp));
+      }
+      SB_MEMSET(ctx, (ctx->sad_queue, 0, 8, s));
       if (!ctx->dry) {
         launch_sad_boxsum(d, di, (int)items.size(), max_r, ctx->sad_queue, s);
         SB_LAUNCHED(ctx, 1);
+        if (!tail.empty()) {
+          launch_sad_tail(d, dt, (int)tail.size(), max_rem, ctx->sad_queue + 1, s);
+          SB_LAUNCHED(ctx, 1);
+        }
       }
     }
     for (int nw = 1; nw <= 17 && !ctx->dry; ++nw)
@@ -699,7 +732,7 @@ sb_status sb_create(int device, size_t mem_budget_bytes, void* cuda_stream, sb_c
   if (cudaSetDevice(device) != cudaSuccess) return SB_ERR_CUDA;
   if (build_tables(ctx.get()) != SB_OK) return SB_ERR_CUDA;
   if (cudaMalloc(&ctx->dev_err, 4) != cudaSuccess || cudaMemset(ctx->dev_err, 0, 4) != cudaSuccess) return SB_ERR_CUDA;
-  if (cudaMalloc(&ctx->sad_queue, 4) != cudaSuccess) return SB_ERR_CUDA;
+  if (cudaMalloc(&ctx->sad_queue, 8) != cudaSuccess) return SB_ERR_CUDA;   // box-sum and tail cursors
   if (cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) ctx->sms = 148;
   if (ctx->up.init(8 << 20) != cudaSuccess) return SB_ERR_OOM;
   *out = ctx.release();
@@ -905,13 +938,19 @@ sb_status sb_boundary_sad(sb_context* ctx, const uint8_t* L_left, const uint8_t*
   const SadJob* d = upload(ctx, std::vector<SadJob>{job}, &st);
   if (!d) return st;
   if (bp) {
-    std::vector<SadItem> items;
-    sad_items({{0, g}}, sad_target(ctx, shape_key(&g, 1)), &items);
+    std::vector<SadItem> items, tail;
+    sad_items({{0, g}}, sad_target(ctx, shape_key(&g, 1)), ctx->sms, &items, &tail);
     const SadItem* di = upload(ctx, items, &st);
     if (!di) return st;
-    SB_CUDA(ctx, cudaMemsetAsync(ctx->sad_queue, 0, 4, s));
+    const SadItem* dt = tail.empty() ? nullptr : upload(ctx, tail, &st);
+    if (!tail.empty() && !dt) return st;
+    SB_CUDA(ctx, cudaMemsetAsync(ctx->sad_queue, 0, 8, s));
     launch_sad_boxsum(d, di, (int)items.size(), (block - 1) / 2, ctx->sad_queue, s);
     SB_LAUNCHED(ctx, 1);
+    if (!tail.empty()) {
+      launch_sad_tail(d, dt, (int)tail.size(), max_disp + 1 - sad_tail_first(max_disp), ctx->sad_queue + 1, s);
+      SB_LAUNCHED(ctx, 1);
+    }
   }
   if (dp) {
     launch_sad_direct(d, 1, sad_direct_words(block), (block - 1) / 2, max_disp, s);

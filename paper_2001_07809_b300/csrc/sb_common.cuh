@@ -125,6 +125,21 @@ inline int64_t sad_direct_limit(int w, int h, int D, int B) {
 struct SadItem {
   int32_t job, x0, d0, y0, y1;  // output rows y0..y1 inclusive, inside Omega
 };
+// Tail disparities: when 1..kTailMax disparities remain past the last whole
+// chunk of 32 (D + 1 = 257, 129, 65, ...), a chunk would leave most lanes idle;
+// a separate kernel computes them (one box filter per disparity) and the
+// box-sum work list stops at the last whole chunk.
+constexpr int kTailMax = 8;
+__host__ __device__ inline int sad_tail_first(int D) { return ((D + 1) / 32) * 32; }   // 32: the box-sum chunk
+__host__ __device__ inline bool sad_has_tail(int D) {
+  const int rem = D + 1 - sad_tail_first(D);
+  return rem > 0 && rem <= kTailMax;
+}
+__host__ __device__ inline int sad_tail_strip(int r) { return (256 - 2 * r) & ~31; }   // outputs per tail item
+// items: (job, strip x0, first tail disparity, rows y0..y1); max_rem: the most
+// tail disparities among the items' jobs (sizes shared memory); queue as below
+void launch_sad_tail(const SadJob* jobs, const SadItem* items, int n_items, int max_rem, unsigned* queue,
+                     cudaStream_t s);
 // max_r: the largest block radius among the items (sizes shared memory)
 // queue: one device counter, zero before the launch (the kernel's work-item cursor)
 void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, unsigned* queue,

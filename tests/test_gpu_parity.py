@@ -134,6 +134,8 @@ SAD_CASES = [
     (40, 60, 0, 1), (40, 60, 5, 3), (61, 97, 31, 9), (61, 97, 32, 9), (61, 97, 33, 9),
     (70, 260, 64, 15), (90, 600, 40, 31), (80, 420, 100, 41), (70, 300, 64, 63), (47, 340, 255, 5),
     (65, 700, 256, 41),
+    # 1..8 disparities past the last whole chunk of 32 (the tail kernel's range)
+    (55, 330, 39, 11), (70, 360, 71, 63), (50, 300, 98, 1), (66, 520, 135, 25),
 ]
 
 
