@@ -277,31 +277,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
 // (pair, strip of sad_tail_strip(r) outputs, row band).  Thread t owns strip
 // column c = x0 - r + t and keeps, per tail disparity d = dt0 + k, the vertical
 // window sum V_k of |L(., c) - R(., c - d)| sliding down the band.  Rows are
-// taken in groups of kTailRows outputs, so that one round of independent loads
-// and three barriers serve a group:
-//   1. stage: the group's entering rows (y + r) and leaving rows (y - r) of
-//      both images (the right one over the strip's columns shifted by dt0,
-//      with kTailMax - 1 more columns on the left for the larger d) and its
-//      anchor flags go to shared memory;
-//   2. vertical: per output row V_k += entering cell, store V_k as that row's
-//      column sums, V_k -= leaving cell;
-//   3. horizontal: one warp per (row, disparity) line turns the line's column
-//      sums into prefix sums P in place (8 values per lane and a warp scan),
-//      and the window sum at strip output l is P[l + 2r] - P[l - 1]; anchors
-//      keep (S << 10 | d) with atomicMin into the argmin keys.
+// taken in groups: first the 2r warm-up rows, 16 at a time, then groups of
+// kTailRows output rows.  A group's rows (the entering rows y + r and leaving
+// rows y - r of both images, the right one over the strip's columns shifted by
+// dt0 with kTailMax - 1 more columns on the left, and the anchor-map rows) are
+// copied with cp.async into one of two shared-memory buffers while the
+// previous group is computed:
+//   vertical: per output row V_k += entering cell, store V_k as that row's
+//     column sums, V_k -= leaving cell;
+//   horizontal: one warp per (row, disparity) line turns the line's column
+//     sums into prefix sums P in place (8 values per lane and a warp scan),
+//     and the window sum at strip output l is P[l + 2r] - P[l - 1]; anchors
+//     keep (S << 10 | d) with atomicMin into the argmin keys.
 constexpr int kTailRows = 8;                    // output rows per group
-constexpr int kTailRStride = 256 + 16;          // staged right-image bytes per row
-__host__ __device__ inline int tail_smem_bytes(int max_rem) {
-  return kTailRows * max_rem * 256 * 4 + 2 * kTailRows * 256 + 2 * kTailRows * kTailRStride + kTailRows * 256;
-}
+constexpr int kTailSlots = 2 * kTailRows;       // staged image rows per group
+constexpr int kTailL = 272, kTailR = 288, kTailB = 272;   // staged bytes per row: 17, 18, 17 chunks
+constexpr int kTailBuf = kTailSlots * (kTailL + kTailR) + kTailRows * kTailB;
+__host__ __device__ inline int tail_smem_bytes(int max_rem) { return kTailRows * max_rem * 1024 + 2 * kTailBuf; }
 
-__global__ void __launch_bounds__(256) k_sad_tail(const SadJob* __restrict__ jobs, const SadItem* __restrict__ items,
+__global__ void __launch_bounds__(256, 6) k_sad_tail(const SadJob* __restrict__ jobs, const SadItem* __restrict__ items,
                                                   int n_items, unsigned* __restrict__ queue, int max_rem) {
   extern __shared__ __align__(16) uint8_t t_smem[];
   uint32_t* s_v = reinterpret_cast<uint32_t*>(t_smem);            // [kTailRows][max_rem][256] column sums
-  uint8_t* s_l = t_smem + kTailRows * max_rem * 1024;              // [2 kTailRows][256] left bytes
-  uint8_t* s_r = s_l + 2 * kTailRows * 256;                        // [2 kTailRows][kTailRStride] right bytes
-  uint8_t* s_b = s_r + 2 * kTailRows * kTailRStride;               // [kTailRows][256] anchor flags
+  uint8_t* s_stage = t_smem + kTailRows * max_rem * 1024;          // 2 x {L rows, R rows, anchor rows}
   __shared__ int s_item;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (;;) {
@@ -313,63 +311,84 @@ __global__ void __launch_bounds__(256) k_sad_tail(const SadJob* __restrict__ job
     const SadJob J = jobs[it.job];
     if (sad_use_direct(J)) continue;
     const int r = J.r, D = J.D, w = J.w;
+    const int64_t npx = (int64_t)w * J.h;
     const int dt0 = it.d0, rem = D + 1 - dt0;
     const int TX = sad_tail_strip(r), NC = TX + 2 * r;
-    const int x0 = it.x0, c = x0 - r + tid;
-    const bool colv = tid < NC && c <= w - 1;       // c >= D, so c - d >= 0 for every d <= D
-    const int cr0 = x0 - r - dt0 - (kTailMax - 1);  // right-image column of staged byte 0
-    const int nr = NC + kTailMax - 1;               // staged right-image bytes per row (<= 263)
+    const int x0 = it.x0, cstart = x0 - r;
+    const bool colv = tid < NC && cstart + tid <= w - 1;   // column >= D, so column - d >= 0 for every d <= D
+    const int cr0 = cstart - dt0 - (kTailMax - 1);         // right-image column of staged byte 0
     const int xo0 = D + r, xo1 = w - 1 - r;
-    // slot q of the staging rows <- image row `row`
-    auto stage = [&](int q, int row) {
-      const int64_t rb = (int64_t)row * w;
-      if (colv) s_l[q * 256 + tid] = J.Ll[rb + c];
-      for (int i = tid; i < nr; i += 256) {
-        const int col = cr0 + i;
-        s_r[q * kTailRStride + i] = (col >= 0 && col < w) ? J.Lr[rb + col] : (uint8_t)0;
+    const bool fast = (((uintptr_t)J.Ll | (uintptr_t)J.Lr | (uintptr_t)J.bmap) & 15) == 0;
+    const int nchL = (15 + NC + 15) / 16, nchR = (15 + NC + kTailMax - 1 + 15) / 16, nchB = (15 + TX + 15) / 16;
+    const int nwarm = (2 * r + kTailSlots - 1) / kTailSlots;
+    const int ngroups = nwarm + (it.y1 - it.y0 + kTailRows) / kTailRows;
+    // group gi: image rows per staging slot (entering / warm-up rows in slots
+    // 0.., leaving rows in slots kTailRows..) and the first output row
+    auto issue = [&](int gi, int buf) {
+      uint8_t* B = s_stage + buf * kTailBuf;
+      int nrows, row0, yg = 0, G = 0;
+      if (gi < nwarm) {
+        row0 = it.y0 - r + kTailSlots * gi;
+        nrows = min(kTailSlots, it.y0 + r - row0);
+      } else {
+        yg = it.y0 + kTailRows * (gi - nwarm);
+        G = min(kTailRows, it.y1 - yg + 1);
+        row0 = 0;
+        nrows = 2 * G;
       }
+      const int per = nchL + nchR;
+      for (int u = tid; u < nrows * per; u += 256) {
+        const int i = u / per, ch = u - i * per;
+        const int q = gi < nwarm ? i : (i < G ? i : kTailRows + i - G);
+        const int row = gi < nwarm ? row0 + i : (i < G ? yg + i + r : yg + (i - G) - r);
+        const int64_t rb = (int64_t)row * w;
+        if (ch < nchL) stage_chunk(B + q * kTailL, J.Ll, npx, (rb + cstart) & ~(int64_t)15, ch, fast);
+        else stage_chunk(B + kTailSlots * kTailL + q * kTailR, J.Lr, npx, (rb + cr0) & ~(int64_t)15, ch - nchL, fast);
+      }
+      for (int u = tid; u < G * nchB; u += 256) {
+        const int j = u / nchB, ch = u - j * nchB;
+        stage_chunk(B + kTailSlots * (kTailL + kTailR) + j * kTailB, J.bmap, npx,
+                    ((int64_t)(yg + j) * w + x0) & ~(int64_t)15, ch, fast);
+      }
+      cp_async_commit();
     };
-    // |L - R| of disparity dt0 + k at this thread's column, staging slot q
-    auto cell = [&](int q, int k) -> uint32_t {
-      const int lv = s_l[q * 256 + tid], rv = s_r[q * kTailRStride + tid + kTailMax - 1 - k];
+    // |L - R| of disparity dt0 + k at this thread's column, image row `row` staged in slot q
+    auto cell = [&](const uint8_t* B, int q, int row, int k) -> uint32_t {
+      const int64_t rb = (int64_t)row * w;
+      const int lv = B[q * kTailL + (int)((rb + cstart) & 15) + tid];
+      const int rv = B[kTailSlots * kTailL + q * kTailR + (int)((rb + cr0) & 15) + tid + kTailMax - 1 - k];
       return (uint32_t)(lv > rv ? lv - rv : rv - lv);
     };
     uint32_t V[kTailMax];
 #pragma unroll
     for (int k = 0; k < kTailMax; ++k) V[k] = 0u;
-    // warm-up: rows y0 - r .. y0 + r - 1, 2 kTailRows at a time
-    for (int row0 = it.y0 - r; row0 < it.y0 + r; row0 += 2 * kTailRows) {
-      const int n = min(2 * kTailRows, it.y0 + r - row0);
-      for (int q = 0; q < n; ++q) stage(q, row0 + q);
-      __syncthreads();
-      if (colv)
-        for (int q = 0; q < n; ++q)
+    issue(0, 0);
+    for (int gi = 0; gi < ngroups; ++gi) {
+      cp_async_wait_all();
+      __syncthreads();   // group gi has landed; every thread is done with group gi - 1
+      if (gi + 1 < ngroups) issue(gi + 1, (gi + 1) & 1);
+      const uint8_t* B = s_stage + (gi & 1) * kTailBuf;
+      if (gi < nwarm) {
+        const int row0 = it.y0 - r + kTailSlots * gi, n = min(kTailSlots, it.y0 + r - row0);
+        if (colv)
+          for (int q = 0; q < n; ++q)
 #pragma unroll
-          for (int k = 0; k < kTailMax; ++k)
-            if (k < rem) V[k] += cell(q, k);
-      __syncthreads();
-    }
-    for (int yg = it.y0; yg <= it.y1; yg += kTailRows) {
-      const int G = min(kTailRows, it.y1 - yg + 1);
-      for (int j = 0; j < G; ++j) {
-        stage(j, yg + j + r);
-        stage(kTailRows + j, yg + j - r);
-        if (tid < TX) {
-          const int x = x0 + tid, y = yg + j;
-          s_b[j * 256 + tid] = x <= xo1 && (x == xo0 || x == xo1 || J.bmap[(int64_t)y * w + x]);
-        }
+            for (int k = 0; k < kTailMax; ++k)
+              if (k < rem) V[k] += cell(B, q, row0 + q, k);
+        continue;
       }
-      __syncthreads();
+      const int yg = it.y0 + kTailRows * (gi - nwarm), G = min(kTailRows, it.y1 - yg + 1);
       for (int j = 0; j < G; ++j) {
 #pragma unroll
         for (int k = 0; k < kTailMax; ++k)
           if (k < rem) {
-            if (colv) V[k] += cell(j, k);
+            if (colv) V[k] += cell(B, j, yg + j + r, k);
             s_v[(j * max_rem + k) * 256 + tid] = colv ? V[k] : 0u;
-            if (colv) V[k] -= cell(kTailRows + j, k);
+            if (colv) V[k] -= cell(B, kTailRows + j, yg + j - r, k);
           }
       }
       __syncthreads();
+      const uint8_t* sb = B + kTailSlots * (kTailL + kTailR);
       for (int line = warp; line < G * rem; line += 8) {
         const int j = line / rem, k = line - j * rem;
         uint32_t* P = s_v + (j * max_rem + k) * 256;
@@ -389,16 +408,19 @@ __global__ void __launch_bounds__(256) k_sad_tail(const SadJob* __restrict__ job
         reinterpret_cast<uint4*>(P)[2 * lane + 1] = b;
         __syncwarp();
         const int y = yg + j;
-        for (int xl = lane; xl < TX; xl += 32)
-          if (s_b[j * 256 + xl]) {
+        const uint8_t* bm = sb + j * kTailB + (int)(((int64_t)y * w + x0) & 15);
+        for (int xl = lane; xl < TX; xl += 32) {
+          const int x = x0 + xl;
+          if (x <= xo1 && (x == xo0 || x == xo1 || bm[xl])) {
             const uint32_t S = P[xl + 2 * r] - (xl > 0 ? P[xl - 1] : 0u);
-            atomicMin(&J.key[(int64_t)y * w + x0 + xl], (S << SB_KEY_DBITS) | (uint32_t)(dt0 + k));
+            atomicMin(&J.key[(int64_t)y * w + x], (S << SB_KEY_DBITS) | (uint32_t)(dt0 + k));
           }
+        }
         __syncwarp();
       }
-      __syncthreads();   // staging rows and column sums are rewritten by the next group
     }
   }
+  cp_async_wait_all();
 }
 
 void launch_sad_tail(const SadJob* jobs, const SadItem* items, int n_items, int max_rem, unsigned* queue,

@@ -411,9 +411,9 @@ void sad_items(const std::vector<std::pair<int, Geo>>& pairs, int64_t target, in
     }
     if (sad_has_tail(D)) {
       // tail items: the band count that minimises (rounds of the persistent
-      // grid, eight 256-thread CTAs per SM) x (band rows + 2r warm-up rows)
+      // grid, six 256-thread CTAs per SM) x (band rows + 2r warm-up rows)
       const int TT = sad_tail_strip(r);
-      const int64_t slots = (int64_t)sms * 8;
+      const int64_t slots = (int64_t)sms * 6;
       int tb = 1;
       int64_t best = -1;
       for (int t = 1; t <= 16 && t <= rows; ++t) {
