@@ -262,9 +262,11 @@ uint64_t sb_launch_count(const sb_context* ctx);
  * context stream at each stage boundary (also inside captured graphs).
  * sb_profile_read waits for the last run and writes the milliseconds of up
  * to max_stages stages of it into ms (order: lightness, k-means, boundary
- * refinement, connected components, SAD, SAD finalise, reconstruction,
- * blur); returns the number written, or -1 if nothing was recorded. */
-enum { SB_STAGE_LIGHTNESS = 0, SB_STAGE_KMEANS, SB_STAGE_REFINE, SB_STAGE_CCA, SB_STAGE_SAD, SB_STAGE_SAD_FINALIZE,
+ * refinement, connected components, SAD box sums (the box-sum kernel over
+ * the disparity chunks of 32), SAD rest (the tail disparities past the last
+ * chunk and the direct-variant kernel), reconstruction, blur); returns the
+ * number written, or -1 if nothing was recorded. */
+enum { SB_STAGE_LIGHTNESS = 0, SB_STAGE_KMEANS, SB_STAGE_REFINE, SB_STAGE_CCA, SB_STAGE_SAD, SB_STAGE_SAD_REST,
        SB_STAGE_RECON, SB_STAGE_BLUR, SB_N_STAGES };
 sb_status sb_profile_enable(sb_context* ctx, int on);
 int32_t sb_profile_read(sb_context* ctx, float* ms, int32_t max_stages);

@@ -31,7 +31,7 @@ SB_VIEW_LEFT, SB_VIEW_RIGHT = 0, 1
 SB_RUN_PLAIN, SB_RUN_BATCHED, SB_RUN_GRAPH, SB_RUN_HOST_IO = 0, 1, 2, 4
 SB_MAX_RANGES = 8
 UNDETERMINED = 0xFFFF
-STAGES = ("lightness", "kmeans", "refine", "cca", "sad", "sad_finalize", "recon", "blur")
+STAGES = ("lightness", "kmeans", "refine", "cca", "sad", "sad_rest", "recon", "blur")
 _STATUS = {1: "invalid argument", 2: "CUDA error", 3: "out of memory", 4: "timeout", 5: "unsupported"}
 
 

@@ -295,11 +295,14 @@ constexpr int kTailL = 272, kTailR = 288, kTailB = 272;   // staged bytes per ro
 constexpr int kTailBuf = kTailSlots * (kTailL + kTailR) + kTailRows * kTailB;
 __host__ __device__ inline int tail_smem_bytes(int max_rem) { return kTailRows * max_rem * 1024 + 2 * kTailBuf; }
 
-__global__ void __launch_bounds__(256, 6) k_sad_tail(const SadJob* __restrict__ jobs, const SadItem* __restrict__ items,
-                                                  int n_items, unsigned* __restrict__ queue, int max_rem) {
+// REM: the most tail disparities among the launch's jobs (static loop bounds)
+template <int REM>
+__global__ void __launch_bounds__(256, 6) k_sad_tail(const SadJob* __restrict__ jobs,
+                                                     const SadItem* __restrict__ items, int n_items,
+                                                     unsigned* __restrict__ queue) {
   extern __shared__ __align__(16) uint8_t t_smem[];
-  uint32_t* s_v = reinterpret_cast<uint32_t*>(t_smem);            // [kTailRows][max_rem][256] column sums
-  uint8_t* s_stage = t_smem + kTailRows * max_rem * 1024;          // 2 x {L rows, R rows, anchor rows}
+  uint32_t* s_v = reinterpret_cast<uint32_t*>(t_smem);            // [kTailRows][REM][256] column sums
+  uint8_t* s_stage = t_smem + kTailRows * REM * 1024;              // 2 x {L rows, R rows, anchor rows}
   __shared__ int s_item;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (;;) {
@@ -310,7 +313,7 @@ __global__ void __launch_bounds__(256, 6) k_sad_tail(const SadJob* __restrict__ 
     const SadItem it = items[s_item];
     const SadJob J = jobs[it.job];
     if (sad_use_direct(J)) continue;
-    const int r = J.r, D = J.D, w = J.w;
+    const int r = J.r, D = J.D, w = J.w, w15 = w & 15;
     const int64_t npx = (int64_t)w * J.h;
     const int dt0 = it.d0, rem = D + 1 - dt0;
     const int TX = sad_tail_strip(r), NC = TX + 2 * r;
@@ -322,46 +325,51 @@ __global__ void __launch_bounds__(256, 6) k_sad_tail(const SadJob* __restrict__ 
     const int nchL = (15 + NC + 15) / 16, nchR = (15 + NC + kTailMax - 1 + 15) / 16, nchB = (15 + TX + 15) / 16;
     const int nwarm = (2 * r + kTailSlots - 1) / kTailSlots;
     const int ngroups = nwarm + (it.y1 - it.y0 + kTailRows) / kTailRows;
+    // 16-byte phase of image row `row` at column c (row * w + c mod 16, in 32-bit arithmetic)
+    auto phase = [&](int row, int c) { return (row * w15 + c) & 15; };
     // group gi: image rows per staging slot (entering / warm-up rows in slots
-    // 0.., leaving rows in slots kTailRows..) and the first output row
+    // 0.., leaving rows in slots kTailRows..); warps take rows, lanes chunks
     auto issue = [&](int gi, int buf) {
       uint8_t* B = s_stage + buf * kTailBuf;
-      int nrows, row0, yg = 0, G = 0;
+      int nrows, row0 = 0, yg = 0, G = 0;
       if (gi < nwarm) {
         row0 = it.y0 - r + kTailSlots * gi;
         nrows = min(kTailSlots, it.y0 + r - row0);
       } else {
         yg = it.y0 + kTailRows * (gi - nwarm);
         G = min(kTailRows, it.y1 - yg + 1);
-        row0 = 0;
         nrows = 2 * G;
       }
-      const int per = nchL + nchR;
-      for (int u = tid; u < nrows * per; u += 256) {
-        const int i = u / per, ch = u - i * per;
+      for (int i = warp; i < nrows; i += 8) {
         const int q = gi < nwarm ? i : (i < G ? i : kTailRows + i - G);
         const int row = gi < nwarm ? row0 + i : (i < G ? yg + i + r : yg + (i - G) - r);
         const int64_t rb = (int64_t)row * w;
-        if (ch < nchL) stage_chunk(B + q * kTailL, J.Ll, npx, (rb + cstart) & ~(int64_t)15, ch, fast);
-        else stage_chunk(B + kTailSlots * kTailL + q * kTailR, J.Lr, npx, (rb + cr0) & ~(int64_t)15, ch - nchL, fast);
+        for (int ch = lane; ch < nchL; ch += 32)
+          stage_chunk(B + q * kTailL, J.Ll, npx, (rb + cstart) & ~(int64_t)15, ch, fast);
+        for (int ch = lane; ch < nchR; ch += 32)
+          stage_chunk(B + kTailSlots * kTailL + q * kTailR, J.Lr, npx, (rb + cr0) & ~(int64_t)15, ch, fast);
       }
-      for (int u = tid; u < G * nchB; u += 256) {
-        const int j = u / nchB, ch = u - j * nchB;
-        stage_chunk(B + kTailSlots * (kTailL + kTailR) + j * kTailB, J.bmap, npx,
-                    ((int64_t)(yg + j) * w + x0) & ~(int64_t)15, ch, fast);
-      }
+      for (int j = warp; j < G; j += 8)
+        for (int ch = lane; ch < nchB; ch += 32)
+          stage_chunk(B + kTailSlots * (kTailL + kTailR) + j * kTailB, J.bmap, npx,
+                      ((int64_t)(yg + j) * w + x0) & ~(int64_t)15, ch, fast);
       cp_async_commit();
     };
-    // |L - R| of disparity dt0 + k at this thread's column, image row `row` staged in slot q
-    auto cell = [&](const uint8_t* B, int q, int row, int k) -> uint32_t {
-      const int64_t rb = (int64_t)row * w;
-      const int lv = B[q * kTailL + (int)((rb + cstart) & 15) + tid];
-      const int rv = B[kTailSlots * kTailL + q * kTailR + (int)((rb + cr0) & 15) + tid + kTailMax - 1 - k];
-      return (uint32_t)(lv > rv ? lv - rv : rv - lv);
-    };
-    uint32_t V[kTailMax];
+    uint32_t V[REM];
 #pragma unroll
-    for (int k = 0; k < kTailMax; ++k) V[k] = 0u;
+    for (int k = 0; k < REM; ++k) V[k] = 0u;
+    // V_k += sign * |L - R| of image row `row`, staged in slot q
+    auto accumulate = [&](const uint8_t* B, int q, int row, bool add) {
+      const int lv = B[q * kTailL + phase(row, cstart) + tid];
+      const uint8_t* rp = B + kTailSlots * kTailL + q * kTailR + phase(row, cr0) + tid + kTailMax - 1;
+#pragma unroll
+      for (int k = 0; k < REM; ++k)
+        if (k < rem) {
+          const int rv = rp[-k];
+          const uint32_t a = (uint32_t)(lv > rv ? lv - rv : rv - lv);
+          V[k] = add ? V[k] + a : V[k] - a;
+        }
+    };
     issue(0, 0);
     for (int gi = 0; gi < ngroups; ++gi) {
       cp_async_wait_all();
@@ -371,27 +379,22 @@ __global__ void __launch_bounds__(256, 6) k_sad_tail(const SadJob* __restrict__ 
       if (gi < nwarm) {
         const int row0 = it.y0 - r + kTailSlots * gi, n = min(kTailSlots, it.y0 + r - row0);
         if (colv)
-          for (int q = 0; q < n; ++q)
-#pragma unroll
-            for (int k = 0; k < kTailMax; ++k)
-              if (k < rem) V[k] += cell(B, q, row0 + q, k);
+          for (int q = 0; q < n; ++q) accumulate(B, q, row0 + q, true);
         continue;
       }
       const int yg = it.y0 + kTailRows * (gi - nwarm), G = min(kTailRows, it.y1 - yg + 1);
       for (int j = 0; j < G; ++j) {
+        if (colv) accumulate(B, j, yg + j + r, true);
 #pragma unroll
-        for (int k = 0; k < kTailMax; ++k)
-          if (k < rem) {
-            if (colv) V[k] += cell(B, j, yg + j + r, k);
-            s_v[(j * max_rem + k) * 256 + tid] = colv ? V[k] : 0u;
-            if (colv) V[k] -= cell(B, kTailRows + j, yg + j - r, k);
-          }
+        for (int k = 0; k < REM; ++k)
+          if (k < rem) s_v[(j * REM + k) * 256 + tid] = colv ? V[k] : 0u;
+        if (colv) accumulate(B, kTailRows + j, yg + j - r, false);
       }
       __syncthreads();
       const uint8_t* sb = B + kTailSlots * (kTailL + kTailR);
       for (int line = warp; line < G * rem; line += 8) {
-        const int j = line / rem, k = line - j * rem;
-        uint32_t* P = s_v + (j * max_rem + k) * 256;
+        const int j = REM == 1 ? line : line / rem, k = line - j * rem;
+        uint32_t* P = s_v + (j * REM + k) * 256;
         uint4 a = reinterpret_cast<uint4*>(P)[2 * lane], b = reinterpret_cast<uint4*>(P)[2 * lane + 1];
         a.y += a.x; a.z += a.y; a.w += a.z;
         b.x += a.w; b.y += b.x; b.z += b.y; b.w += b.z;
@@ -408,12 +411,14 @@ __global__ void __launch_bounds__(256, 6) k_sad_tail(const SadJob* __restrict__ 
         reinterpret_cast<uint4*>(P)[2 * lane + 1] = b;
         __syncwarp();
         const int y = yg + j;
-        const uint8_t* bm = sb + j * kTailB + (int)(((int64_t)y * w + x0) & 15);
+        const uint8_t* bm = sb + j * kTailB + phase(y, x0);
+        uint32_t* krow = J.key + (int64_t)y * w + x0;
+        const uint32_t dk = (uint32_t)(dt0 + k);
         for (int xl = lane; xl < TX; xl += 32) {
           const int x = x0 + xl;
           if (x <= xo1 && (x == xo0 || x == xo1 || bm[xl])) {
             const uint32_t S = P[xl + 2 * r] - (xl > 0 ? P[xl - 1] : 0u);
-            atomicMin(&J.key[(int64_t)y * w + x], (S << SB_KEY_DBITS) | (uint32_t)(dt0 + k));
+            atomicMin(&krow[xl], (S << SB_KEY_DBITS) | dk);
           }
         }
         __syncwarp();
@@ -423,17 +428,27 @@ __global__ void __launch_bounds__(256, 6) k_sad_tail(const SadJob* __restrict__ 
   cp_async_wait_all();
 }
 
-void launch_sad_tail(const SadJob* jobs, const SadItem* items, int n_items, int max_rem, unsigned* queue,
-                     cudaStream_t s) {
-  if (n_items <= 0) return;
-  const int smem = tail_smem_bytes(max_rem);
-  cudaFuncSetAttribute(k_sad_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+template <int REM>
+void launch_tail_rem(const SadJob* jobs, const SadItem* items, int n_items, unsigned* queue, cudaStream_t s) {
+  const int smem = tail_smem_bytes(REM);
+  cudaFuncSetAttribute(k_sad_tail<REM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   int dev = 0, sms = 148, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sad_tail, 256, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sad_tail<REM>, 256, smem);
   const int grid = std::min(n_items, sms * std::max(1, per_sm));
-  k_sad_tail<<<grid, 256, smem, s>>>(jobs, items, n_items, queue, max_rem);
+  k_sad_tail<REM><<<grid, 256, smem, s>>>(jobs, items, n_items, queue);
+}
+
+void launch_sad_tail(const SadJob* jobs, const SadItem* items, int n_items, int max_rem, unsigned* queue,
+                     cudaStream_t s) {
+  if (n_items <= 0) return;
+  switch (max_rem) {
+    case 1: launch_tail_rem<1>(jobs, items, n_items, queue, s); break;
+    case 2: launch_tail_rem<2>(jobs, items, n_items, queue, s); break;
+    case 3: case 4: launch_tail_rem<4>(jobs, items, n_items, queue, s); break;
+    default: launch_tail_rem<kTailMax>(jobs, items, n_items, queue, s); break;
+  }
 }
 
 int sad_boxsum_smem_bytes(int r) {

@@ -625,11 +625,14 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
       if (!ctx->dry) {
         launch_sad_boxsum(d, di, (int)items.size(), max_r, ctx->sad_queue, s);
         SB_LAUNCHED(ctx, 1);
-        if (!tail.empty()) {
-          launch_sad_tail(d, dt, (int)tail.size(), max_rem, ctx->sad_queue + 1, s);
-          SB_LAUNCHED(ctx, 1);
-        }
       }
+      SB_MARK(ctx, SB_STAGE_SAD_REST);
+      if (!tail.empty() && !ctx->dry) {
+        launch_sad_tail(d, dt, (int)tail.size(), max_rem, ctx->sad_queue + 1, s);
+        SB_LAUNCHED(ctx, 1);
+      }
+    } else {
+      SB_MARK(ctx, SB_STAGE_SAD_REST);
     }
     for (int nw = 1; nw <= 17 && !ctx->dry; ++nw)
       if (direct_nw & (1u << nw)) {
@@ -638,7 +641,6 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
       }
     // the argmin keys go straight to Algorithm 1 (its kernel decodes them), so
     // the pipeline needs no key-to-disparity pass
-    SB_MARK(ctx, SB_STAGE_SAD_FINALIZE);
   }
   SB_MARK(ctx, SB_STAGE_RECON);
   // 6. reconstruction (Algorithms 1 and 2)
