@@ -530,7 +530,7 @@ def run_ours(args):
                          "blur_tile_rows": {"batched": tune_batched[1], "per_pair": tune_plain[1]},
                          "candidate_ms": {"batched": tune_batched[2], "per_pair": tune_plain[2]},
                          "candidates": "box-sum split of 1, 2, 3, 6 waves of the persistent grid; "
-                                       "then blur tiles of 112 and 64 rows"},
+                                       "then the blur forms: tiles of 112 and 64 rows, strips (32)"},
             "uneven_batch": uneven,
             "serving": serving,
             "gpu_launches": launches,

@@ -185,6 +185,18 @@ sb_status sb_reconstruct_disparity(sb_context* ctx, uint16_t* disp, int32_t w, i
 sb_status sb_selective_blur(sb_context* ctx, const uint8_t* rgb, const uint16_t* disp, int32_t w, int32_t h,
                             const sb_range* ranges, int32_t n_ranges, float sigma, uint8_t* out_rgb);
 
+/* Blur kernel form for later sb_selective_blur and sb_run calls on this
+ * context: SB_BLUR_TILES_112 / SB_BLUR_TILES_64 (2-D tiles of 64 columns by
+ * 112 or 64 rows, each filtering its own halo rows), SB_BLUR_STRIP (a CTA
+ * walks 64-column strips down bands of 512 rows, 32 rows per step, keeping
+ * the horizontally filtered rows in a ring so no row is filtered twice; taken
+ * where its shared memory fits the largest radius of the launch, else tiles
+ * of 112 rows), or SB_BLUR_AUTO (the form sb_autotune chose for the launch
+ * shape, else tiles of 112 rows).  Every form gives the same bytes.  Returns
+ * SB_ERR_INVALID_ARG for any other value. */
+enum { SB_BLUR_AUTO = 0, SB_BLUR_STRIP = 32, SB_BLUR_TILES_64 = 64, SB_BLUR_TILES_112 = 112 };
+sb_status sb_set_blur_form(sb_context* ctx, int32_t form);
+
 /* One stereo pair for sb_run. */
 typedef struct {
   const uint8_t* left_rgb;   /* h*w*3 */
@@ -232,15 +244,18 @@ sb_status sb_boundary_sad_static(const uint8_t* L_left, const uint8_t* L_right, 
  * (how many (pair, strip, disparity chunk, row band) items a launch is cut
  * into: more items balance the persistent grid better, fewer repeat less
  * warm-up work per band; candidates 1, 2, 3 and 6 waves of the grid) and the
- * blur tile height (112 rows, two CTAs per SM, or 64 rows, three CTAs per SM
- * with more halo work).  Runs the pairs with sb_run(flags) once per candidate
+ * blur form (tiles of 112 rows, two CTAs per SM; tiles of 64 rows, three CTAs
+ * per SM with more halo work; or strips, see sb_set_blur_form).  Runs the
+ * pairs with sb_run(flags) once per candidate
  * (a warm-up run and a timed run each, so the outputs are written), keeps the
  * fastest and uses it in every later sb_run of that shape on this context.
  * Device pairs only (flags without SB_RUN_HOST_IO).  ms_out: NULL or
- * SB_AUTOTUNE_CANDIDATES timings (4 splits, then 2 blur tiles);
- * sad_items_out / blur_rows_out: NULL or the chosen values.  Synchronises the
- * context stream; not inside a stream capture. */
-#define SB_AUTOTUNE_CANDIDATES 6
+ * SB_AUTOTUNE_CANDIDATES timings (4 splits, then the blur forms 112, 64 and
+ * strip); sad_items_out / blur_rows_out: NULL or the chosen values (the blur
+ * form as in sb_set_blur_form).  A form set with sb_set_blur_form stays in
+ * force over the tuned one.  Synchronises the context stream; not inside a
+ * stream capture. */
+#define SB_AUTOTUNE_CANDIDATES 7
 sb_status sb_autotune(sb_context* ctx, const sb_pair* pairs, int32_t n_pairs, uint32_t flags, float* ms_out,
                       int32_t* sad_items_out, int32_t* blur_rows_out);
 

@@ -18,7 +18,8 @@ __all__ = [
     "SbError", "Context", "Pair", "sb_default_params", "make_params", "sb_create", "sb_destroy",
     "sb_rgb_to_lightness", "sb_kmeans_segment", "sb_refine_boundaries", "sb_boundary_sad",
     "sb_reconstruct_disparity", "sb_selective_blur", "sb_run", "sb_synchronize", "sb_launch_count",
-    "sb_lr_consistency", "sb_autotune", "SB_PEEK_SNAPSHOT", "SB_PEEK_INPLACE", "SB_VIEW_LEFT", "SB_VIEW_RIGHT",
+    "sb_lr_consistency", "sb_autotune", "sb_set_blur_form", "SB_BLUR_AUTO", "SB_BLUR_STRIP", "SB_BLUR_TILES_64",
+    "SB_BLUR_TILES_112", "SB_PEEK_SNAPSHOT", "SB_PEEK_INPLACE", "SB_VIEW_LEFT", "SB_VIEW_RIGHT",
     "SB_RUN_PLAIN", "SB_RUN_BATCHED", "SB_RUN_GRAPH", "SB_RUN_HOST_IO", "SB_SAD_AUTO", "SB_SAD_DIRECT",
     "SB_SAD_BOXSUM", "SB_MORPH_FILL_REMOVE", "SB_MORPH_OPEN_CLOSE", "UNDETERMINED", "library_path",
 ]
@@ -29,6 +30,8 @@ SB_SAD_AUTO, SB_SAD_DIRECT, SB_SAD_BOXSUM = 0, 1, 2
 SB_PEEK_SNAPSHOT, SB_PEEK_INPLACE = 0, 1
 SB_VIEW_LEFT, SB_VIEW_RIGHT = 0, 1
 SB_RUN_PLAIN, SB_RUN_BATCHED, SB_RUN_GRAPH, SB_RUN_HOST_IO = 0, 1, 2, 4
+SB_BLUR_AUTO, SB_BLUR_STRIP, SB_BLUR_TILES_64, SB_BLUR_TILES_112 = 0, 32, 64, 112
+SB_AUTOTUNE_CANDIDATES = 7
 SB_MAX_RANGES = 8
 UNDETERMINED = 0xFFFF
 STAGES = ("lightness", "kmeans", "refine", "cca", "sad", "sad_rest", "recon", "blur")
@@ -88,6 +91,7 @@ def _load():
         "sb_reconstruct_disparity": ([V, V, I32, I32, I32, I32, I32, I32, V], ctypes.c_int),
         "sb_lr_consistency": ([V, V, V, I32, I32, I32, V, V], ctypes.c_int),
         "sb_autotune": ([V, V, I32, ctypes.c_uint32, V, V, V], ctypes.c_int),
+        "sb_set_blur_form": ([V, I32], ctypes.c_int),
         "sb_selective_blur": ([V, V, V, I32, I32, V, I32, ctypes.c_float, V], ctypes.c_int),
         "sb_run": ([V, ctypes.POINTER(sb_pair), I32, U32], ctypes.c_int),
         "sb_profile_enable": ([V, ctypes.c_int], ctypes.c_int),
@@ -285,14 +289,20 @@ def _pairs_array(pairs: List[Pair]):
 
 
 def sb_autotune(ctx: Context, pairs: List[Pair], flags: int = SB_RUN_PLAIN):
-    """Times the candidate box-sum work splits and blur tile heights on these
-    pairs (running them), keeps the fastest for their shape on this context;
-    -> (work items, blur rows, [ms per candidate])."""
+    """Times the candidate box-sum work splits and blur forms on these pairs
+    (running them), keeps the fastest for their shape on this context;
+    -> (work items, blur form, [ms per candidate])."""
     arr = _pairs_array(pairs)
-    ms = (ctypes.c_float * 6)()
+    ms = (ctypes.c_float * SB_AUTOTUNE_CANDIDATES)()
     items, rows = ctypes.c_int32(0), ctypes.c_int32(0)
     _check(ctx, _lib.sb_autotune(ctx.handle, arr, len(pairs), flags, ms, ctypes.byref(items), ctypes.byref(rows)))
     return int(items.value), int(rows.value), [float(v) for v in ms]
+
+
+def sb_set_blur_form(ctx: Context, form: int):
+    """Blur kernel form for later calls on this context (SB_BLUR_*; 0 = the
+    tuned form, else tiles of 112 rows)."""
+    _check(ctx, _lib.sb_set_blur_form(ctx.handle, int(form)))
 
 
 def sb_run(ctx: Context, pairs: List[Pair], flags: int = SB_RUN_PLAIN):

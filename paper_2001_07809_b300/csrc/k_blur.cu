@@ -266,6 +266,210 @@ __global__ void __launch_bounds__(kBlurThreads) k_blur(const BlurJob* __restrict
   }
 }
 
+// ----------------------------------------------------------------- strip form
+// A CTA walks down a strip of BX output columns over a band of kBandRows output
+// rows, kSB output rows per step.  The horizontal results live in a ring of
+// M = 2R + kSB + 1 rows per channel (the rows the vertical pass of one step
+// reads), so no input row is filtered twice; the ring advances kSB rows per
+// step.  Input rows for the next batch of horizontal rows are copied with
+// cp.async while the current batch or the vertical pass runs.  The blur mask
+// of the whole band is taken once, as bits, at the start; a step with no
+// blurred pixel is copied, and a batch of horizontal rows that no remaining
+// blurred step reads is skipped.
+namespace {
+constexpr int kSB = 32;              // output rows per step
+constexpr int kStripThreads = 384;   // = kSB x 3 channels x BX/OB (horizontal) = BX x 3 x kSB/OB (vertical)
+constexpr int kBandRows = 512;       // output rows per CTA
+constexpr int kMaxSteps = kBandRows / kSB;
+
+struct StripGeo {
+  int nt, M, iw, sr, h_off, in_off, bytes;
+};
+__host__ __device__ inline StripGeo strip_geo(int R) {
+  StripGeo g;
+  g.nt = 2 * R + 1;
+  g.M = 2 * R + kSB + 1;
+  g.iw = BX + 2 * R + 1;
+  g.sr = ((g.iw * 3 + 15 + 15) / 16) * 16;
+  g.h_off = ((g.nt + 3) & ~3) * 4;                                   // taps first
+  g.in_off = (g.h_off + 3 * g.M * HS * 4 + 15) & ~15;                // then the ring, 3 channels (cp.async
+                                                                     // destinations need 16-byte alignment)
+  g.bytes = g.in_off + 2 * kSB * g.sr;                               // then two input buffers
+  return g;
+}
+}  // namespace
+
+__host__ __device__ bool blur_strip_fits(int R) { return strip_geo(R).bytes <= 200 * 1024; }
+
+__global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* __restrict__ jobs) {
+  extern __shared__ __align__(16) float fsm[];
+  __shared__ uint32_t s_mbits[kBandRows * BX / 32];   // 1 = blurred
+  __shared__ int s_flag[kMaxSteps];
+  __shared__ int s_lo[8], s_hi[8];
+  __shared__ uint8_t s_off[2][kSB];
+  const BlurJob J = jobs[blockIdx.z];
+  const int w = J.w, h = J.h, R = J.R;
+  const int tx0 = blockIdx.x * BX, yb0 = blockIdx.y * kBandRows;
+  if (tx0 >= w || yb0 >= h) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kWarps = kStripThreads / 32;
+  const int ox = min(BX, w - tx0), rows = min(kBandRows, h - yb0);
+  const int nsteps = (rows + kSB - 1) / kSB;
+  const StripGeo G = strip_geo(R);
+  const int nt = G.nt, M = G.M, iw = G.iw, sr = G.sr;
+  float* s_tap = fsm;
+  float* s_h = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(fsm) + G.h_off);
+  uint8_t* s_in = reinterpret_cast<uint8_t*>(fsm) + G.in_off;
+  const int xs = tx0 - R;
+  const bool interior = xs >= 0 && xs + iw <= w;
+  const int64_t nbytes = (int64_t)w * h * 3;
+  const bool fast = interior && ((reinterpret_cast<uintptr_t>(J.rgb) & 15) == 0);
+  if (tid < 8) { s_lo[tid] = jobs[blockIdx.z].lo[tid]; s_hi[tid] = jobs[blockIdx.z].hi[tid]; }
+  for (int t = tid; t < nt; t += kStripThreads) s_tap[t] = J.taps[t];
+  __syncthreads();
+  // mask bits of the band (warp-wide ballots of 32 columns) and per-step flags
+  const int nr = J.n_ranges;
+  for (int p = warp * 32 + lane; p < kSB * nsteps * BX; p += kStripThreads) {
+    const int i = p / BX, c = p % BX;
+    bool m = false;
+    if (i < rows && c < ox) m = !in_focus(J.disp[(int64_t)(yb0 + i) * w + tx0 + c], s_lo, s_hi, nr);
+    const unsigned word = __ballot_sync(0xffffffffu, m);
+    if (lane == 0) s_mbits[p >> 5] = word;
+  }
+  __syncthreads();
+  for (int st = tid; st < nsteps; st += kStripThreads) {
+    int any = 0;
+    for (int q = st * kSB * (BX / 32); q < (st + 1) * kSB * (BX / 32); ++q) any |= s_mbits[q] != 0u;
+    s_flag[st] = any;
+  }
+  __syncthreads();
+  int any_step = 0;
+  for (int st = 0; st < nsteps; ++st) any_step |= s_flag[st];
+  if (!any_step) {   // nothing to blur in the band: copy it
+    for (int i = warp; i < rows; i += kWarps) {
+      const int64_t row = ((int64_t)(yb0 + i) * w + tx0) * 3;
+      for (int b = lane; b < ox * 3; b += 32) J.out[row + b] = J.rgb[row + b];
+    }
+    return;
+  }
+  // horizontal batches: first the ring fill (rows yb0 - R .. yb0 + kSB + R,
+  // kSB at a time), then one batch per step s >= 1 (rows y_s + R + 1 ..
+  // y_s + kSB + R, read first by step s)
+  const int nfill = (M + kSB - 1) / kSB;
+  const int nbatch = nfill + nsteps - 1;
+  auto batch_row0 = [&](int k) { return k < nfill ? yb0 - R + kSB * k : yb0 + kSB * (k - nfill + 1) + R + 1; };
+  auto batch_rows = [&](int k) { return k < nfill ? min(kSB, M - kSB * k) : kSB; };
+  // does any blurred step read rows a .. a + n - 1?  step t reads y_t - R .. y_t + kSB + R
+  auto batch_needed = [&](int k) {
+    if (k < nfill) return true;
+    const int a = batch_row0(k), b = a + batch_rows(k) - 1;
+    for (int t = 0; t < nsteps; ++t) {
+      const int yt = yb0 + kSB * t;
+      if (s_flag[t] && yt - R <= b && yt + kSB + R >= a) return true;
+    }
+    return false;
+  };
+  auto stage = [&](int k, int buf) {
+    const int a = batch_row0(k), n = batch_rows(k);
+    uint8_t* base = s_in + buf * kSB * sr;
+    for (int i = warp; i < n; i += kWarps) {
+      const int y = min(max(a + i, 0), h - 1);
+      uint8_t* dst = base + i * sr;
+      if (fast) {
+        const int64_t s0 = ((int64_t)y * w + xs) * 3, a16 = s0 & ~(int64_t)15;
+        if (lane == 0) s_off[buf][i] = (uint8_t)(s0 - a16);
+        const int nchunk = (iw * 3 + 15 + 15) / 16;
+        for (int c = lane; c < nchunk; c += 32) {
+          const int64_t src = a16 + 16 * c;
+          if (src + 16 <= nbytes) {
+            cp_async16(dst + 16 * c, J.rgb + src);
+          } else {
+            for (int q = 0; q < 16; ++q) dst[16 * c + q] = J.rgb[min(src + q, nbytes - 1)];
+          }
+        }
+      } else {
+        if (lane == 0) s_off[buf][i] = 0;
+        const uint8_t* src_row = J.rgb + (int64_t)y * w * 3;
+        for (int b = lane; b < iw * 3; b += 32) {
+          const int j = b / 3, c = b - 3 * j;
+          dst[b] = src_row[min(max(xs + j, 0), w - 1) * 3 + c];
+        }
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  };
+  auto slot = [&](int y) { return (y - (yb0 - R)) % M; };   // ring row of image row y >= yb0 - R
+  auto hpass = [&](int k, int buf) {
+    const int a = batch_row0(k), n = batch_rows(k);
+    const uint8_t* base = s_in + buf * kSB * sr;
+    for (int task = tid; task < n * 3 * (BX / OB); task += kStripThreads) {
+      const int i = task / (3 * (BX / OB)), rest = task - i * (3 * (BX / OB));
+      const int ch = rest / (BX / OB), j0 = (rest - ch * (BX / OB)) * OB;
+      const uint8_t* in = base + i * sr + s_off[buf][i] + j0 * 3 + ch;   // output j0+o uses in[3(o .. o+2R)]
+      float acc[OB];
+      conv16(acc, s_tap, nt, [in](int j) { return u8f(in[j * 3]); });
+      float* dst = s_h + (ch * M + slot(a + i)) * HS + j0;
+#pragma unroll
+      for (int o = 0; o < OB; ++o) dst[o] = acc[o];
+    }
+  };
+  stage(0, 0);
+  for (int k = 0; k < nfill; ++k) {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    if (k + 1 < nbatch) stage(k + 1, (k + 1) & 1);
+    hpass(k, k & 1);
+  }
+  for (int st = 0; st < nsteps; ++st) {
+    __syncthreads();   // the ring holds every row step st reads
+    const int ys = yb0 + kSB * st, nrow = min(kSB, rows - kSB * st);
+    if (s_flag[st]) {
+      // vertical pass: task = (column, channel, block of OB output rows)
+      const int col = tid % BX, rest = tid / BX, ch = rest % 3, blk = rest / 3;
+      const int i0 = blk * OB;
+      const int b0 = slot(ys + i0 - R);
+      const float* hc = s_h + ch * M * HS + col;
+      float acc[OB];
+      conv16(acc, s_tap, nt, [hc, b0, M](int j) {
+        int q = b0 + j;
+        if (q >= M) q -= M;
+        return hc[q * HS];
+      });
+      if (col < ox) {
+#pragma unroll
+        for (int o = 0; o < OB; ++o) {
+          const int i = i0 + o;
+          if (i < nrow) {
+            const int bi = kSB * st + i;   // band row
+            const int64_t at = ((int64_t)(ys + i) * w + tx0 + col) * 3 + ch;
+            uint8_t v;
+            if ((s_mbits[(bi * BX + col) >> 5] >> (col & 31)) & 1u) {
+              const int q = __float2int_rd(acc[o] + 0.5f);
+              v = (uint8_t)min(max(q, 0), 255);
+            } else {
+              v = J.rgb[at];
+            }
+            J.out[at] = v;
+          }
+        }
+      }
+    } else {
+      for (int i = warp; i < nrow; i += kWarps) {
+        const int64_t row = ((int64_t)(ys + i) * w + tx0) * 3;
+        for (int b = lane; b < ox * 3; b += 32) J.out[row + b] = J.rgb[row + b];
+      }
+    }
+    const int k = nfill + st;   // the batch step st + 1 reads first
+    if (k < nbatch) {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      __syncthreads();   // batch k staged; every vertical read of the ring slots it replaces is done
+      if (k + 1 < nbatch) stage(k + 1, (k + 1) & 1);
+      if (batch_needed(k)) hpass(k, k & 1);
+    }
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <int BY>
 void launch_blur_by(const BlurJob* jobs, int n_jobs, int max_w, int max_h, int max_R, cudaStream_t s) {
   // every job's own layout (three channels or one) fits in the largest job's size
@@ -278,6 +482,13 @@ void launch_blur_by(const BlurJob* jobs, int n_jobs, int max_w, int max_h, int m
 
 void launch_blur(const BlurJob* jobs, int n_jobs, int max_w, int max_h, int max_R, int by, cudaStream_t s) {
   if (n_jobs <= 0) return;
+  if (by == kBlurStrip && blur_strip_fits(max_R)) {
+    const int smem = strip_geo(max_R).bytes;
+    cudaFuncSetAttribute(k_blur_strip, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    dim3 grid((max_w + BX - 1) / BX, (max_h + kBandRows - 1) / kBandRows, n_jobs);
+    k_blur_strip<<<grid, kStripThreads, smem, s>>>(jobs);
+    return;
+  }
   if (by == 64)
     launch_blur_by<64>(jobs, n_jobs, max_w, max_h, max_R, s);
   else

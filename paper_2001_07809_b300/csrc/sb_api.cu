@@ -1025,8 +1025,16 @@ sb_status sb_selective_blur(sb_context* ctx, const uint8_t* rgb, const uint16_t*
   std::vector<BlurJob> J{b};
   const BlurJob* d = upload(ctx, J, &st);
   if (!d) return st;
-  launch_blur(d, 1, w, h, R, 112, ctx->stream);
+  launch_blur(d, 1, w, h, R, ctx->blur_by_override > 0 ? ctx->blur_by_override : 112, ctx->stream);
   SB_LAUNCHED(ctx, 1);
+  return SB_OK;
+}
+
+sb_status sb_set_blur_form(sb_context* ctx, int32_t form) {
+  if (!ctx) return SB_ERR_INVALID_ARG;
+  if (form != SB_BLUR_AUTO && form != SB_BLUR_STRIP && form != SB_BLUR_TILES_64 && form != SB_BLUR_TILES_112)
+    return fail(ctx, SB_ERR_INVALID_ARG, "blur form must be 0, 32, 64 or 112, got %d", form);
+  ctx->blur_by_override = form;
   return SB_OK;
 }
 
@@ -1333,25 +1341,26 @@ extern "C" sb_status sb_autotune(sb_context* ctx, const sb_pair* pairs, int32_t 
   // candidates 0-3: the box-sum work split, 1, 2, 3 and 6 waves of the
   // persistent grid (blur tiles of 112 rows); candidates 4-5: blur tiles of
   // 112 and 64 rows with the chosen split
-  const int waves[4] = {1, 2, 3, 6}, rows[2] = {112, 64};
+  const int waves[4] = {1, 2, 3, 6}, rows[3] = {SB_BLUR_TILES_112, SB_BLUR_TILES_64, SB_BLUR_STRIP};
   float ms[SB_AUTOTUNE_CANDIDATES] = {};
   int best_items = 0, best_rows = 112;
   float best_ms = 0.f;
   sb_status st = SB_OK;
+  const int forced = ctx->blur_by_override;
   ctx->blur_by_override = 112;
   for (int c = 0; c < 4 && st == SB_OK; ++c) {
     ctx->sad_target_override = ctx->sms * 2 * waves[c];
     st = time_run(&ms[c]);
     if (st == SB_OK && (c == 0 || ms[c] < best_ms)) { best_ms = ms[c]; best_items = ctx->sad_target_override; }
   }
-  for (int c = 0; c < 2 && st == SB_OK; ++c) {
+  for (int c = 0; c < 3 && st == SB_OK; ++c) {
     ctx->sad_target_override = best_items;
     ctx->blur_by_override = rows[c];
     st = time_run(&ms[4 + c]);
     if (st == SB_OK && (c == 0 || ms[4 + c] < best_ms)) { best_ms = ms[4 + c]; best_rows = rows[c]; }
   }
   ctx->sad_target_override = 0;
-  ctx->blur_by_override = 0;
+  ctx->blur_by_override = forced;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != SB_OK) return st;

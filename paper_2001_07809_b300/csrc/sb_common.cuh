@@ -187,8 +187,12 @@ struct BlurJob {
   int32_t w, h, R, n_ranges;
   int32_t lo[8], hi[8];
 };
-// by: output rows per tile, 112 or 64
+// by: output rows per tile, 112 or 64, or kBlurStrip for the strip form
+// (bands walked kSB = 32 rows at a time; used where its shared memory fits
+// the largest radius, else tiles of 112 rows)
+constexpr int kBlurStrip = 32;
 void launch_blur(const BlurJob* jobs, int n_jobs, int max_w, int max_h, int max_R, int by, cudaStream_t s);
+__host__ __device__ bool blur_strip_fits(int R);
 __host__ __device__ int blur_smem_bytes(int R, int by);
 
 }  // namespace sb

@@ -296,6 +296,39 @@ def test_blur_interior_tiles(ctx, sigma, offset):
     assert np.abs(host(out).astype(int) - want.astype(int)).max() <= 1
 
 
+@pytest.mark.parametrize("sigma", [3.0, 8.0])
+def test_blur_forms_agree_with_oracle(ctx, sigma):
+    # tiles of 112 and 64 rows and the strip form give the same bytes; 1100
+    # rows span three 512-row strip bands (the last one ragged), 300 columns
+    # end in a ragged 44-column strip; rows 0..399 are all in focus (steps with
+    # no blurred pixel are copied and the filtered rows only they read are
+    # skipped) and so is the band of rows 512..1023 except one row
+    h, w = 1100, 300
+    rgb = RNG.integers(0, 256, (h, w, 3)).astype(np.uint8)
+    disp = RNG.integers(0, 40, (h, w)).astype(np.uint16)
+    disp[:400] = 15
+    disp[512:1024] = 12
+    disp[700, 17:60] = 3
+    ranges = [(10, 20)]
+    want = oracle.selective_blur(rgb, disp, ranges, sigma)
+    outs = []
+    try:
+        for form in (sb.SB_BLUR_TILES_112, sb.SB_BLUR_TILES_64, sb.SB_BLUR_STRIP):
+            sb.sb_set_blur_form(ctx, form)
+            outs.append(blur(ctx, rgb, disp, ranges, sigma))
+    finally:
+        sb.sb_set_blur_form(ctx, sb.SB_BLUR_AUTO)
+    assert np.abs(outs[0].astype(int) - want.astype(int)).max() <= 1
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    keep = (disp >= 10) & (disp <= 20)
+    assert np.array_equal(outs[2][keep], rgb[keep])
+
+
+def test_blur_form_rejects_unknown_values(ctx):
+    with pytest.raises(sb.SbError):
+        sb.sb_set_blur_form(ctx, 48)
+
+
 def test_blur_constant_image_unchanged(ctx):
     rgb = np.full((140, 260, 3), 93, np.uint8)
     rgb[..., 2] = 250
@@ -396,10 +429,10 @@ def test_autotune_keeps_results_and_caches_the_split(ctx):
         outs.append((o, d))
     for flags in (sb.SB_RUN_BATCHED | sb.SB_RUN_GRAPH, sb.SB_RUN_PLAIN):
         chosen, rows, ms = sb.sb_autotune(ctx, pairs, flags)
-        assert chosen in [ctx_sms() * 2 * k for k in (1, 2, 3, 6)] and rows in (64, 112)
-        assert len(ms) == 6 and all(m > 0 for m in ms)
+        assert chosen in [ctx_sms() * 2 * k for k in (1, 2, 3, 6)] and rows in (32, 64, 112)
+        assert len(ms) == sb.SB_AUTOTUNE_CANDIDATES == 7 and all(m > 0 for m in ms)
         ctx.synchronize()
-        # the tuner's last run used 64-row blur tiles: its outputs are checked too
+        # the tuner's last run used the strip-form blur: its outputs are checked too
         for (o, d), (b_rgb, b_disp) in zip(outs, before):
             assert np.array_equal(host(o), b_rgb) and np.array_equal(host(d, np.uint16), b_disp)
         sb.sb_run(ctx, pairs, flags)
