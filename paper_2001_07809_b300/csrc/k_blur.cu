@@ -283,12 +283,16 @@ constexpr int kBandRows = 512;       // output rows per CTA
 constexpr int kMaxSteps = kBandRows / kSB;
 
 struct StripGeo {
-  int nt, M, iw, sr, h_off, in_off, bytes;
+  int nt, F, M, iw, sr, h_off, in_off, bytes;
 };
+// F: filtered rows one step reads (2R + kSB + 1); M: ring rows, F rounded up
+// to a multiple of OB so that a block of OB consecutive ring rows starting at
+// a multiple of OB never wraps
 __host__ __device__ inline StripGeo strip_geo(int R) {
   StripGeo g;
   g.nt = 2 * R + 1;
-  g.M = 2 * R + kSB + 1;
+  g.F = 2 * R + kSB + 1;
+  g.M = (g.F + OB - 1) / OB * OB;
   g.iw = BX + 2 * R + 1;
   g.sr = ((g.iw * 3 + 15 + 15) / 16) * 16;
   g.h_off = ((g.nt + 3) & ~3) * 4;                                   // taps first
@@ -298,6 +302,48 @@ __host__ __device__ inline StripGeo strip_geo(int R) {
   return g;
 }
 }  // namespace
+
+// conv16 over ring rows b0 + j (mod M) of one column (hc: the column's row-0
+// entry, row stride HS); b0 and M are multiples of OB, so the wrap is taken
+// once per block of OB rows
+__device__ __forceinline__ void conv16_ring(float (&acc)[OB], const float* tap, int nt, const float* hc, int b0,
+                                            int M) {
+  auto block = [&](int j) {   // j: a multiple of OB
+    int q = b0 + j;
+    if (q >= M) q -= M;
+    return hc + q * HS;
+  };
+  float win[OB];
+  const float* p = block(0);
+#pragma unroll
+  for (int o = 0; o < OB; ++o) { acc[o] = 0.f; win[o] = p[o * HS]; }
+  int t = 0;
+  for (; t + OB <= nt; t += OB) {
+    const float* pn = block(t + OB);
+#pragma unroll
+    for (int u = 0; u < OB; ++u) {
+      const float tp = tap[t + u];
+#pragma unroll
+      for (int o = 0; o < OB; ++o) acc[o] = fmaf(tp, win[(u + o) % OB], acc[o]);
+      win[u] = pn[u * HS];
+    }
+  }
+  const int rem = nt - t;
+  const float* pn = block(t + OB);   // the refills of the remaining taps: rows t + OB .. t + OB + rem - 1
+  auto x = [pn, t](int j) { return pn[(j - t - OB) * HS]; };
+  if (rem >= 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float tp = tap[t + u];
+#pragma unroll
+      for (int o = 0; o < OB; ++o) acc[o] = fmaf(tp, win[(u + o) % OB], acc[o]);
+      win[u] = pn[u * HS];
+    }
+    conv_tail<8>(acc, win, tap, t + 8, rem - 8, x);
+  } else {
+    conv_tail<0>(acc, win, tap, t, rem, x);
+  }
+}
 
 __host__ __device__ bool blur_strip_fits(int R) { return strip_geo(R).bytes <= 200 * 1024; }
 
@@ -329,12 +375,23 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
   __syncthreads();
   // mask bits of the band (warp-wide ballots of 32 columns) and per-step flags
   const int nr = J.n_ranges;
-  for (int p = warp * 32 + lane; p < kSB * nsteps * BX; p += kStripThreads) {
-    const int i = p / BX, c = p % BX;
-    bool m = false;
-    if (i < rows && c < ox) m = !in_focus(J.disp[(int64_t)(yb0 + i) * w + tx0 + c], s_lo, s_hi, nr);
-    const unsigned word = __ballot_sync(0xffffffffu, m);
-    if (lane == 0) s_mbits[p >> 5] = word;
+  const int npix = kSB * nsteps * BX;   // a multiple of 64: the loop bounds are warp-uniform
+  for (int p0 = warp * 32 + lane; p0 < npix; p0 += 8 * kStripThreads) {
+    uint32_t dv[8];   // eight independent loads in flight, then the ballots
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int p = p0 + k * kStripThreads, i = p / BX, c = p % BX;
+      dv[k] = (p < npix && i < rows && c < ox) ? (uint32_t)J.disp[(int64_t)(yb0 + i) * w + tx0 + c] : 0x10000u;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int p = p0 + k * kStripThreads;
+      if (p < npix) {
+        const bool m = dv[k] <= 0xFFFFu && !in_focus((uint16_t)dv[k], s_lo, s_hi, nr);
+        const unsigned word = __ballot_sync(0xffffffffu, m);
+        if (lane == 0) s_mbits[p >> 5] = word;
+      }
+    }
   }
   __syncthreads();
   for (int st = tid; st < nsteps; st += kStripThreads) {
@@ -355,10 +412,11 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
   // horizontal batches: first the ring fill (rows yb0 - R .. yb0 + kSB + R,
   // kSB at a time), then one batch per step s >= 1 (rows y_s + R + 1 ..
   // y_s + kSB + R, read first by step s)
-  const int nfill = (M + kSB - 1) / kSB;
+  const int F = G.F;
+  const int nfill = (F + kSB - 1) / kSB;
   const int nbatch = nfill + nsteps - 1;
   auto batch_row0 = [&](int k) { return k < nfill ? yb0 - R + kSB * k : yb0 + kSB * (k - nfill + 1) + R + 1; };
-  auto batch_rows = [&](int k) { return k < nfill ? min(kSB, M - kSB * k) : kSB; };
+  auto batch_rows = [&](int k) { return k < nfill ? min(kSB, F - kSB * k) : kSB; };
   // does any blurred step read rows a .. a + n - 1?  step t reads y_t - R .. y_t + kSB + R
   auto batch_needed = [&](int k) {
     if (k < nfill) return true;
@@ -428,13 +486,8 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
       const int col = tid % BX, rest = tid / BX, ch = rest % 3, blk = rest / 3;
       const int i0 = blk * OB;
       const int b0 = slot(ys + i0 - R);
-      const float* hc = s_h + ch * M * HS + col;
       float acc[OB];
-      conv16(acc, s_tap, nt, [hc, b0, M](int j) {
-        int q = b0 + j;
-        if (q >= M) q -= M;
-        return hc[q * HS];
-      });
+      conv16_ring(acc, s_tap, nt, s_h + ch * M * HS + col, b0, M);
       if (col < ox) {
 #pragma unroll
         for (int o = 0; o < OB; ++o) {
