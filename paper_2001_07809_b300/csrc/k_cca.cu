@@ -53,43 +53,84 @@ __device__ __forceinline__ bool unite(int* P, int a, int b) {
 }
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_cca_local(const CcaJob* __restrict__ jobs, uint32_t* dev_err) {
-  __shared__ int s_p[CT * CT];
+// Tile-local labelling, one warp per 32x32 tile, rows in order (the classic
+// raster two-pass scheme with a warp holding one row): lane x of the warp is
+// tile column x.  The 32 row masks are ballots of the map (all rows loaded up
+// front); each horizontal run of a row is one union-find node, named by its
+// first pixel (tile-local index y * 32 + start), which is the smallest index
+// of the run.  Row y's runs are united with the runs of row y - 1 they touch
+// (8-connectivity: columns x - 1 .. x + 1), one union per (run above, run
+// below) pair: lane q takes the pairs that first touch at column q of the row
+// above.  Unions hang the larger root under the smaller, so a component's
+// root is its smallest index, the label the raster flood fill gives.  A last
+// pass finds every pixel's root from the row masks and writes the labels.
+constexpr int kCcaWarps = 8;   // tiles per CTA (along x)
+
+__device__ __forceinline__ int run_start(unsigned mask, int c) {
+  const unsigned z = ~mask & ((1u << c) - 1u);   // clear columns left of c (c = 0: none)
+  return z ? 32 - __clz(z) : 0;
+}
+
+__global__ void __launch_bounds__(kCcaWarps * 32) k_cca_local(const CcaJob* __restrict__ jobs, uint32_t* dev_err) {
+  __shared__ int s_par[kCcaWarps][CT * CT];
   const CcaJob J = jobs[blockIdx.z];
-  const int tx0 = blockIdx.x * CT, ty0 = blockIdx.y * CT;
-  if (tx0 >= J.w || ty0 >= J.h) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tx0 = (blockIdx.x * kCcaWarps + warp) * CT, ty0 = blockIdx.y * CT;
+  if (tx0 >= J.w || ty0 >= J.h) return;   // whole warps leave together
   const int w = J.w, h = J.h;
-  for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) {
-    const int x = tx0 + (i & (CT - 1)), y = ty0 + (i >> 5);
-    s_p[i] = (x < w && y < h && J.b[(int64_t)y * w + x]) ? i : -1;
+  int* P = s_par[warp];
+  const int x = tx0 + lane;
+  // the tile's 32 bytes of column `lane`, then lane y keeps the mask of row y
+  unsigned colbits = 0;
+  {
+    uint8_t v[CT];
+#pragma unroll
+    for (int y = 0; y < CT; ++y) v[y] = (x < w && ty0 + y < h) ? J.b[(int64_t)(ty0 + y) * w + x] : (uint8_t)0;
+#pragma unroll
+    for (int y = 0; y < CT; ++y) colbits |= (v[y] ? 1u : 0u) << y;
   }
-  __syncthreads();
+  unsigned rowmask = 0;
+#pragma unroll
+  for (int y = 0; y < CT; ++y) {
+    const unsigned m = __ballot_sync(0xffffffffu, (colbits >> y) & 1u);
+    if (lane == y) rowmask = m;
+  }
   bool ok = true;
-  for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) {
-    if (s_p[i] < 0) continue;
-    const int lx = i & (CT - 1), ly = i >> 5;
-    // previous neighbours inside the tile (W, NW, N, NE), by the usual
-    // 8-connectivity decision tree: N alone when it is set (W, NW and NE all
-    // touch N, and their links to N are made when those pixels are visited);
-    // otherwise W or else NW (they touch each other), plus NE
-    if (ly > 0 && s_p[i - CT] >= 0) {
-      ok &= unite(s_p, i, i - CT);
-    } else {
-      if (lx > 0 && s_p[i - 1] >= 0) ok &= unite(s_p, i, i - 1);
-      else if (ly > 0 && lx > 0 && s_p[i - CT - 1] >= 0) ok &= unite(s_p, i, i - CT - 1);
-      if (ly > 0 && lx < CT - 1 && s_p[i - CT + 1] >= 0) ok &= unite(s_p, i, i - CT + 1);
+  unsigned prev = 0;
+  for (int y = 0; y < CT; ++y) {
+    const unsigned cur = __shfl_sync(0xffffffffu, rowmask, y);
+    if (cur) {
+      const bool set = (cur >> lane) & 1u;
+      if (set && run_start(cur, lane) == lane) P[y * CT + lane] = y * CT + lane;   // a new node per run
+      __syncwarp();
+      if (prev && ((prev >> lane) & 1u)) {
+        const int q = lane;
+        const int A = (y - 1) * CT + run_start(prev, q);                 // the run above through column q
+        const bool left_above = q > 0 && ((prev >> (q - 1)) & 1u);       // column q - 1 above: same run, its lane
+        auto cb = [&](int c) { return c >= 0 && c < CT && ((cur >> c) & 1u); };
+        if (left_above) {
+          // lane q - 1 took the runs through columns q - 2 .. q; a run starting at q + 1 is new
+          if (cb(q + 1) && !cb(q)) ok &= unite(P, A, y * CT + q + 1);
+        } else {
+          if (cb(q - 1)) ok &= unite(P, A, y * CT + run_start(cur, q - 1));
+          if (cb(q) && !cb(q - 1)) ok &= unite(P, A, y * CT + q);
+          if (cb(q + 1) && !cb(q)) ok &= unite(P, A, y * CT + q + 1);
+        }
+      }
+      __syncwarp();
     }
+    prev = cur;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) {
-    const int x = tx0 + (i & (CT - 1)), y = ty0 + (i >> 5);
-    if (x >= w || y >= h) continue;
+  // labels: every pixel's root, as a linear index of the image
+  for (int y = 0; y < CT && ty0 + y < h; ++y) {
+    const unsigned cur = __shfl_sync(0xffffffffu, rowmask, y);
+    if (x >= w) continue;
     int v = -1;
-    if (s_p[i] >= 0) {
-      const int root = find_root(s_p, i);
+    if ((cur >> lane) & 1u) {
+      const int root = find_root(P, y * CT + run_start(cur, lane));
       v = (ty0 + (root >> 5)) * w + tx0 + (root & (CT - 1));
     }
-    J.lab[(int64_t)y * w + x] = v;
+    J.lab[(int64_t)(ty0 + y) * w + x] = v;
   }
   if (!ok) atomicOr(dev_err, DEV_ERR_CCA_ITER);
 }
@@ -327,7 +368,8 @@ __global__ void __launch_bounds__(256) k_cc_filter(const CcaJob* __restrict__ jo
 void launch_cca(const CcaJob* jobs, int n_jobs, int max_w, int max_h, uint32_t* dev_err, cudaStream_t s) {
   if (n_jobs <= 0) return;
   dim3 tiles((max_w + CT - 1) / CT, (max_h + CT - 1) / CT, n_jobs);
-  k_cca_local<<<tiles, 256, 0, s>>>(jobs, dev_err);
+  const int tiles_x = (max_w + CT - 1) / CT;
+  k_cca_local<<<dim3((tiles_x + kCcaWarps - 1) / kCcaWarps, tiles.y, n_jobs), kCcaWarps * 32, 0, s>>>(jobs, dev_err);
   k_cca_merge<<<tiles, 128, 0, s>>>(jobs, dev_err);
 }
 

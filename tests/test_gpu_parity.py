@@ -104,6 +104,23 @@ def test_cc_cut_inside_a_size_class(ctx, frac):
     assert np.array_equal(bnd, o_bnd)
 
 
+@pytest.mark.parametrize("noise", [0.3, 0.7])
+def test_cca_dense_noisy_maps(ctx, noise):
+    # dense, irregular boundary maps: many runs per tile row, diagonal links,
+    # runs touching several runs of the row above, components merging late
+    h, w = 211, 389
+    labels = RNG.integers(0, 2, (h // 3 + 1, w // 3 + 1))
+    labels = np.kron(labels, np.ones((3, 3), np.int64))[:h, :w]
+    flip = RNG.random((h, w)) < noise
+    labels = np.where(flip, RNG.integers(0, 3, (h, w)), labels).astype(np.uint8)
+    ref, lab, bnd = refine(ctx, labels, 1, 0.04)
+    o_ref = oracle.refine(oracle.boundary(labels), 1)
+    o_lab, _ = oracle.cca(o_ref)
+    assert np.array_equal(ref, o_ref)
+    assert np.array_equal(lab, o_lab)
+    assert np.array_equal(bnd, oracle.cc_filter(o_ref, o_lab, 0.04))
+
+
 def test_refine_degenerate(ctx):
     # K = 1: no boundary at all; one label row; a single pixel image
     for labels in (np.zeros((40, 50), np.uint8), np.array([[0, 1, 1, 0, 2]], np.uint8), np.zeros((1, 1), np.uint8)):
