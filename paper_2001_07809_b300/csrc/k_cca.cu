@@ -58,12 +58,13 @@ __device__ __forceinline__ bool unite(int* P, int a, int b) {
 // tile column x.  The 32 row masks are ballots of the map (all rows loaded up
 // front); each horizontal run of a row is one union-find node, named by its
 // first pixel (tile-local index y * 32 + start), which is the smallest index
-// of the run.  Row y's runs are united with the runs of row y - 1 they touch
-// (8-connectivity: columns x - 1 .. x + 1), one union per (run above, run
-// below) pair: lane q takes the pairs that first touch at column q of the row
-// above.  Unions hang the larger root under the smaller, so a component's
-// root is its smallest index, the label the raster flood fill gives.  A last
-// pass finds every pixel's root from the row masks and writes the labels.
+// of the run.  A run of row y touches the runs of row y - 1 that cross its
+// columns widened by one on each side (8-connectivity); the lane at its start
+// hangs the new node under the root of the first of them and unites that
+// tree with the trees of the others (rare: where two branches meet).  Every
+// link goes from a larger index to a smaller one, so a component's root is
+// its smallest index, the label the raster flood fill gives.  A last pass
+// finds every pixel's root from the row masks and writes the labels.
 constexpr int kCcaWarps = 8;   // tiles per CTA (along x)
 
 __device__ __forceinline__ int run_start(unsigned mask, int c) {
@@ -100,21 +101,28 @@ __global__ void __launch_bounds__(kCcaWarps * 32) k_cca_local(const CcaJob* __re
   for (int y = 0; y < CT; ++y) {
     const unsigned cur = __shfl_sync(0xffffffffu, rowmask, y);
     if (cur) {
-      const bool set = (cur >> lane) & 1u;
-      if (set && run_start(cur, lane) == lane) P[y * CT + lane] = y * CT + lane;   // a new node per run
-      __syncwarp();
-      if (prev && ((prev >> lane) & 1u)) {
-        const int q = lane;
-        const int A = (y - 1) * CT + run_start(prev, q);                 // the run above through column q
-        const bool left_above = q > 0 && ((prev >> (q - 1)) & 1u);       // column q - 1 above: same run, its lane
-        auto cb = [&](int c) { return c >= 0 && c < CT && ((cur >> c) & 1u); };
-        if (left_above) {
-          // lane q - 1 took the runs through columns q - 2 .. q; a run starting at q + 1 is new
-          if (cb(q + 1) && !cb(q)) ok &= unite(P, A, y * CT + q + 1);
+      // the lane at the start of each run links the run (a fresh node) to the
+      // root of the first run above it touches, and unites that tree with the
+      // tree of every further run above it touches
+      const unsigned starts = cur & ~(cur << 1);
+      if ((starts >> lane) & 1u) {
+        const int C = y * CT + lane;
+        const unsigned inv = ~(cur >> lane);
+        const int len = inv ? __ffs(inv) - 1 : CT - lane;
+        const unsigned run = (len == 32 ? 0xffffffffu : ((1u << len) - 1u)) << lane;
+        const unsigned T = prev & (run | (run << 1) | (run >> 1));   // columns above it touches
+        if (!T) {
+          P[C] = C;
         } else {
-          if (cb(q - 1)) ok &= unite(P, A, y * CT + run_start(cur, q - 1));
-          if (cb(q) && !cb(q - 1)) ok &= unite(P, A, y * CT + q);
-          if (cb(q + 1) && !cb(q)) ok &= unite(P, A, y * CT + q + 1);
+          const int s1 = run_start(prev, __ffs(T) - 1);
+          const int r1 = find_root(P, (y - 1) * CT + s1);
+          P[C] = r1;   // r1 < C: the smaller index stays the root
+          unsigned others = T & (prev & ~(prev << 1)) & ~(1u << s1);   // starts of the other runs above
+          while (others) {
+            const int b = __ffs(others) - 1;
+            others &= others - 1u;
+            ok &= unite(P, r1, (y - 1) * CT + b);
+          }
         }
       }
       __syncwarp();
@@ -165,55 +173,85 @@ __global__ void __launch_bounds__(256) k_cca_merge(const CcaJob* __restrict__ jo
   if (!ok) atomicOr(dev_err, DEV_ERR_CCA_ITER);
 }
 
-// Final labels and component sizes: every pixel of a 32x32 tile follows its
-// parent chain to the root (and stores it: the label is then the root), the
-// tile counts its pixels per root in a small shared-memory hash table and
-// adds one total per (tile, root) to the global size array, so a large
-// component costs one atomic per tile it touches instead of one per pixel.
-// Roots append themselves to the job's root list, and the tile's boundary
-// pixels are added to N_b.
+// Final labels and component sizes.  After the tile labelling every pixel's
+// label is its tile-local root; the border merge then re-points some of those
+// roots (to a root in this tile or another).  So a pixel p's local root u is
+// its label when that lies in the tile, else p itself (a local root whose
+// label the merge changed to another tile).  A 32x32 tile counts its pixels
+// per local root in shared memory, then only the referenced local roots
+// follow their parent chains in global memory (one to a few hops) to the
+// component root R, add their counts to size[R] and, when a local root is R
+// itself, append it to the job's root list; a last pass writes R as every
+// pixel's label.  The tile's boundary pixels are added to N_b.
+__device__ __forceinline__ int tile_local(int v, int base, int w, float inv_w) {
+  const int d = v - base;   // v = base + dy * w + dx for a pixel of the tile
+  if (d < 0) return -1;
+  int dy = (int)((float)d * inv_w);
+  if (dy * w > d) --dy;
+  else if ((dy + 1) * w <= d) ++dy;   // exact for dy < 32, where it matters
+  if (dy >= CT) return -1;
+  const int dx = d - dy * w;
+  return dx < CT && dx < w ? dy * CT + dx : -1;
+}
+
 __global__ void __launch_bounds__(256) k_cc_count(const CcaJob* __restrict__ jobs) {
-  constexpr int HS = 256;  // hash slots (a tile rarely holds more than a few dozen roots)
-  __shared__ int s_key[HS];
-  __shared__ unsigned s_cnt[HS];
+  constexpr int kPer = CT * CT / 256;   // pixels per thread
+  __shared__ unsigned s_cnt[CT * CT];   // pixels per local root
+  __shared__ int s_root[CT * CT];       // component root of each referenced local root
   __shared__ unsigned s_total;
   const CcaJob J = jobs[blockIdx.z];
+  const int w = J.w, h = J.h;
   const int tx0 = blockIdx.x * CT, ty0 = blockIdx.y * CT;
-  if (tx0 >= J.w || ty0 >= J.h) return;
-  for (int i = threadIdx.x; i < HS; i += blockDim.x) { s_key[i] = -1; s_cnt[i] = 0; }
+  if (tx0 >= w || ty0 >= h) return;
+  const int base = ty0 * w + tx0;
+  const float inv_w = 1.0f / (float)w;
+  for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) s_cnt[i] = 0u;
   if (threadIdx.x == 0) s_total = 0;
   __syncthreads();
+  int u[kPer], v[kPer];
   unsigned mine = 0;
-  for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) {
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int i = threadIdx.x + 256 * k;
     const int x = tx0 + (i & (CT - 1)), y = ty0 + (i >> 5);
-    if (x >= J.w || y >= J.h) continue;
-    const int64_t p = (int64_t)y * J.w + x;
-    int v = J.lab[p];
-    if (v < 0) continue;
-    ++mine;
-    const int f = find_root(J.lab, v);
-    if (f != v) J.lab[p] = f;   // only shortens paths other tiles may be following
-    if (f == (int)p) J.roots[atomicAdd(reinterpret_cast<unsigned long long*>(&J.cut[5]), 1ull)] = f;
-    v = f;
-    unsigned hsh = ((unsigned)v * 2654435761u) >> 24;  // 8 bits
-    bool placed = false;
-    volatile int* vkey = s_key;
-    for (int probe = 0; probe < HS; ++probe) {
-      const int slot = (hsh + probe) & (HS - 1);
-      const int k = vkey[slot];
-      if (k == v || (k == -1 && (atomicCAS(&s_key[slot], -1, v) == -1 || vkey[slot] == v))) {
-        atomicAdd(&s_cnt[slot], 1u);
-        placed = true;
-        break;
-      }
+    v[k] = (x < w && y < h) ? J.lab[(int64_t)y * w + x] : -1;
+  }
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    u[k] = -1;
+    if (v[k] >= 0) {
+      const int i = threadIdx.x + 256 * k;
+      const int t = tile_local(v[k], base, w, inv_w);
+      u[k] = t >= 0 ? t : i;
+      atomicAdd(&s_cnt[u[k]], 1u);
+      ++mine;
     }
-    if (!placed) atomicAdd(&J.size[v], 1u);  // table full: count directly
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int i = threadIdx.x + 256 * k;
+    const unsigned c = s_cnt[i];
+    if (c) {   // pixel i is a local root some pixel of the tile refers to
+      const int g = (ty0 + (i >> 5)) * w + tx0 + (i & (CT - 1));
+      const int R = find_root(J.lab, g);
+      s_root[i] = R;
+      atomicAdd(&J.size[R], c);
+      if (R == g) J.roots[atomicAdd(reinterpret_cast<unsigned long long*>(&J.cut[5]), 1ull)] = R;
+    }
   }
   for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
   if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&s_total, mine);
   __syncthreads();
-  for (int i = threadIdx.x; i < HS; i += blockDim.x)
-    if (s_key[i] >= 0 && s_cnt[i]) atomicAdd(&J.size[s_key[i]], s_cnt[i]);
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    if (u[k] < 0) continue;
+    const int R = s_root[u[k]];
+    if (R != v[k]) {
+      const int i = threadIdx.x + 256 * k;
+      J.lab[(int64_t)(ty0 + (i >> 5)) * w + tx0 + (i & (CT - 1))] = R;   // other tiles may follow it: R is an ancestor
+    }
+  }
   if (threadIdx.x == 0 && s_total) atomicAdd(reinterpret_cast<unsigned long long*>(&J.cut[0]), (unsigned long long)s_total);
 }
 
@@ -352,17 +390,28 @@ __global__ void __launch_bounds__(256) k_cc_filter(const CcaJob* __restrict__ jo
   const int64_t n = (int64_t)J.w * J.h;
   const uint32_t sstar = (uint32_t)J.cut[2];
   const long long T = J.cut[4];
+  auto keep = [&](int v) -> uint32_t {
+    if (v < 0) return 0u;
+    const uint32_t sz = J.size[v];
+    return sz < sstar || (sz == sstar && (long long)v < T) ? 0u : 1u;
+  };
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-    const int v = J.lab[p];
-    uint8_t keep = 0;
-    if (v >= 0) {
-      const uint32_t sz = J.size[v];
-      const bool gone = sz < sstar || (sz == sstar && (long long)v < T);
-      keep = gone ? 0 : 1;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // four pixels per step (16-byte label loads, one size lookup per distinct
+  // label: neighbours mostly share their root), then the last n % 4 pixels
+  const int64_t n4 = n / 4;
+  const bool vec = ((reinterpret_cast<uintptr_t>(J.lab) | reinterpret_cast<uintptr_t>(J.out)) & 15) == 0;
+  if (vec) {
+    for (int64_t q = t0; q < n4; q += stride) {
+      const int4 v = reinterpret_cast<const int4*>(J.lab)[q];
+      const uint32_t k0 = keep(v.x);
+      const uint32_t k1 = v.y == v.x ? k0 : keep(v.y);
+      const uint32_t k2 = v.z == v.y ? k1 : keep(v.z);
+      const uint32_t k3 = v.w == v.z ? k2 : keep(v.w);
+      reinterpret_cast<uint32_t*>(J.out)[q] = k0 | (k1 << 8) | (k2 << 16) | (k3 << 24);
     }
-    J.out[p] = keep;
   }
+  for (int64_t p = (vec ? 4 * n4 : 0) + t0; p < n; p += stride) J.out[p] = (uint8_t)keep(J.lab[p]);
 }
 
 void launch_cca(const CcaJob* jobs, int n_jobs, int max_w, int max_h, uint32_t* dev_err, cudaStream_t s) {
