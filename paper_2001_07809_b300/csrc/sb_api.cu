@@ -173,6 +173,8 @@ struct sb_context {
   unsigned* sad_queue = nullptr;  // work-item cursors of the box-sum SAD and tail kernels
   uint8_t* ws = nullptr;
   size_t ws_bytes = 0;
+  cudaMemPool_t ws_pool = nullptr;   // the workspace's own stream-ordered pool (keeps freed memory)
+  bool ws_pooled = false;            // ws came from ws_pool
   Uploader up;
   cudaStream_t s_in = nullptr, s_out = nullptr;  // host-buffer streaming
   // graph cache (batched form)
@@ -293,13 +295,65 @@ sb_status ensure_ws(sb_context* ctx, size_t bytes) {
   if (ctx->budget && bytes > ctx->budget)
     return fail(ctx, SB_ERR_OOM, "workspace of %zu bytes exceeds the budget of %zu bytes", bytes, ctx->budget);
   // grow by at least half again, so that a context fed batches of varying
-  // size (a serving loop) re-allocates, and synchronises, a few times only
+  // size (a serving loop) re-allocates a few times only
   size_t grow = ctx->ws_bytes + ctx->ws_bytes / 2;
   if (ctx->budget && grow > ctx->budget) grow = ctx->budget;
+  if (!ctx->capturing) {
+    // stream-ordered: the old workspace is released after the work queued on
+    // this stream, the new one taken from the context's pool, and nothing
+    // waits (cudaFree and cudaMalloc would synchronise the whole device,
+    // stalling the other streams of a serving process)
+    if (!ctx->ws_pool) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = ctx->device;
+      if (cudaMemPoolCreate(&ctx->ws_pool, &props) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;   // freed blocks stay in the pool for the next, larger request
+        cudaMemPoolSetAttribute(ctx->ws_pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      } else {
+        cudaGetLastError();
+        ctx->ws_pool = nullptr;
+      }
+    }
+    if (ctx->ws_pool) {
+      if (ctx->ws) {
+        if (ctx->ws_pooled) cudaFreeAsync(ctx->ws, ctx->stream);
+        else {
+          SB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+          cudaFree(ctx->ws);
+        }
+      }
+      ctx->ws = nullptr;
+      ctx->ws_bytes = 0;
+      cudaError_t e = cudaErrorMemoryAllocation;
+      if (grow > bytes) {
+        e = cudaMallocFromPoolAsync((void**)&ctx->ws, grow, ctx->ws_pool, ctx->stream);
+        if (e == cudaSuccess) bytes = grow;
+        else cudaGetLastError();
+      }
+      if (e != cudaSuccess) e = cudaMallocFromPoolAsync((void**)&ctx->ws, bytes, ctx->ws_pool, ctx->stream);
+      if (e == cudaSuccess) {
+        ctx->ws_bytes = bytes;
+        ctx->ws_pooled = true;
+        return SB_OK;
+      }
+      cudaGetLastError();
+      ctx->ws = nullptr;
+      // the pool could not serve it: return its cached blocks and take the plain path
+      SB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      cudaMemPoolTrimTo(ctx->ws_pool, 0);
+    }
+  }
   SB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->ws) {
+    if (ctx->ws_pooled) cudaFreeAsync(ctx->ws, ctx->stream);
+    else cudaFree(ctx->ws);
+    SB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   ctx->ws = nullptr;
   ctx->ws_bytes = 0;
+  ctx->ws_pooled = false;
   cudaError_t e = cudaErrorMemoryAllocation;
   if (grow > bytes) {
     e = cudaMalloc(&ctx->ws, grow);
@@ -756,7 +810,15 @@ void sb_destroy(sb_context* ctx) {
   if (ctx->tables) cudaFree(ctx->tables);
   if (ctx->dev_err) cudaFree(ctx->dev_err);
   if (ctx->sad_queue) cudaFree(ctx->sad_queue);
-  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->ws) {
+    if (ctx->ws_pooled) {
+      cudaFreeAsync(ctx->ws, ctx->stream);
+      cudaStreamSynchronize(ctx->stream);
+    } else {
+      cudaFree(ctx->ws);
+    }
+  }
+  if (ctx->ws_pool) cudaMemPoolDestroy(ctx->ws_pool);
   if (ctx->stage) cudaFree(ctx->stage);
   if (ctx->s_in) cudaStreamDestroy(ctx->s_in);
   if (ctx->s_out) cudaStreamDestroy(ctx->s_out);
