@@ -484,7 +484,27 @@ void sad_items(const std::vector<std::pair<int, Geo>>& pairs, int64_t target, in
   }
   // largest first, so the persistent kernel ends on short items (ties keep generation order)
   std::stable_sort(list.begin(), list.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-  for (auto& c : list) items->push_back(c.second);
+  // the last grid's worth of items (two resident CTAs per SM) is cut into four
+  // row bands each, so that the grid drains on quarter items instead of
+  // waiting on whole ones; only where the list holds several rounds and every
+  // band keeps at least max(8r, 64) rows
+  const size_t slots = (size_t)sms * 2;
+  size_t keep = list.size();
+  std::vector<SadItem> tail_parts;
+  if (list.size() >= 4 * slots) {
+    std::map<int, int> radius;
+    for (auto& pg : pairs) radius[pg.first] = (pg.second.p.block - 1) / 2;
+    for (size_t k = list.size() - slots; k < list.size(); ++k) {
+      const SadItem& it = list[k].second;
+      const int rows = it.y1 - it.y0 + 1;
+      if (rows < 4 * std::max(8 * radius[it.job], 64)) { tail_parts.clear(); break; }
+      for (int b = 0; b < 4; ++b)
+        tail_parts.push_back(SadItem{it.job, it.x0, it.d0, it.y0 + rows * b / 4, it.y0 + rows * (b + 1) / 4 - 1});
+    }
+    if (!tail_parts.empty()) keep = list.size() - slots;
+  }
+  for (size_t k = 0; k < keep; ++k) items->push_back(list[k].second);
+  for (auto& it : tail_parts) items->push_back(it);
 }
 
 // Stage boundary marks for sb_profile_read (external records inside captures).
@@ -1241,7 +1261,7 @@ sb_status run_graph(sb_context* ctx, const sb_pair* pairs, int n) {
 sb_status run_host_io(sb_context* ctx, const sb_pair* pairs, int n, bool batched) {
   if (!ctx->s_in) SB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking));
   if (!ctx->s_out) SB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking));
-  // chunking: up to 1.5 GB of inputs per chunk, at least one pair; the chunk
+  // chunking: up to 3 GB of inputs per chunk, at least one pair; the chunk
   // size ramps up from 256 MB at the start and back down at the end, so the
   // first upload (nothing to overlap it with yet) and the last download are short
   std::vector<std::pair<int, int>> chunks;
@@ -1250,7 +1270,7 @@ sb_status run_host_io(sb_context* ctx, const sb_pair* pairs, int n, bool batched
   } else {
     std::vector<std::pair<int, int>> head, tail;
     int lo = 0, hi = n;
-    const size_t cap = (size_t)1536 << 20;
+    const size_t cap = (size_t)3072 << 20;
     for (int k = 0; lo < hi; ++k) {
       const size_t target = std::min(cap, ((size_t)256 << 20) << std::min(k, 8));
       size_t acc = 0;
