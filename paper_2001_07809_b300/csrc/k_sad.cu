@@ -318,7 +318,9 @@ __global__ void __launch_bounds__(256, 6) k_sad_tail(const SadJob* __restrict__ 
     const int dt0 = it.d0, rem = D + 1 - dt0;
     const int TX = sad_tail_strip(r), NC = TX + 2 * r;
     const int x0 = it.x0, cstart = x0 - r;
-    const bool colv = tid < NC && cstart + tid <= w - 1;   // column >= D, so column - d >= 0 for every d <= D
+    // every thread keeps column sums, also past the strip (tid >= NC) or the
+    // image (column > w - 1): no window of an output reads those, and their
+    // staged bytes lie inside the staging rows
     const int cr0 = cstart - dt0 - (kTailMax - 1);         // right-image column of staged byte 0
     const int xo0 = D + r, xo1 = w - 1 - r;
     const bool fast = (((uintptr_t)J.Ll | (uintptr_t)J.Lr | (uintptr_t)J.bmap) & 15) == 0;
@@ -378,17 +380,19 @@ __global__ void __launch_bounds__(256, 6) k_sad_tail(const SadJob* __restrict__ 
       const uint8_t* B = s_stage + (gi & 1) * kTailBuf;
       if (gi < nwarm) {
         const int row0 = it.y0 - r + kTailSlots * gi, n = min(kTailSlots, it.y0 + r - row0);
-        if (colv)
-          for (int q = 0; q < n; ++q) accumulate(B, q, row0 + q, true);
+        for (int q = 0; q < n; ++q) accumulate(B, q, row0 + q, true);
         continue;
       }
       const int yg = it.y0 + kTailRows * (gi - nwarm), G = min(kTailRows, it.y1 - yg + 1);
-      for (int j = 0; j < G; ++j) {
-        if (colv) accumulate(B, j, yg + j + r, true);
 #pragma unroll
-        for (int k = 0; k < REM; ++k)
-          if (k < rem) s_v[(j * REM + k) * 256 + tid] = colv ? V[k] : 0u;
-        if (colv) accumulate(B, kTailRows + j, yg + j - r, false);
+      for (int j = 0; j < kTailRows; ++j) {
+        if (j < G) {
+          accumulate(B, j, yg + j + r, true);
+#pragma unroll
+          for (int k = 0; k < REM; ++k)
+            if (k < rem) s_v[(j * REM + k) * 256 + tid] = V[k];
+          accumulate(B, kTailRows + j, yg + j - r, false);
+        }
       }
       __syncthreads();
       const uint8_t* sb = B + kTailSlots * (kTailL + kTailR);
@@ -416,10 +420,9 @@ __global__ void __launch_bounds__(256, 6) k_sad_tail(const SadJob* __restrict__ 
         const uint32_t dk = (uint32_t)(dt0 + k);
         for (int xl = lane; xl < TX; xl += 32) {
           const int x = x0 + xl;
-          if (x <= xo1 && (x == xo0 || x == xo1 || bm[xl])) {
-            const uint32_t S = P[xl + 2 * r] - (xl > 0 ? P[xl - 1] : 0u);
-            atomicMin(&krow[xl], (S << SB_KEY_DBITS) | dk);
-          }
+          const bool anc = (x <= xo1) & ((x == xo0) | (x == xo1) | (bm[xl] != 0));
+          const uint32_t S = P[xl + 2 * r] - (xl > 0 ? P[xl - 1] : 0u);
+          if (anc) atomicMin(&krow[xl], (S << SB_KEY_DBITS) | dk);
         }
         __syncwarp();
       }
