@@ -143,14 +143,17 @@ __global__ void __launch_bounds__(kCcaWarps * 32) k_cca_local(const CcaJob* __re
   if (!ok) atomicOr(dev_err, DEV_ERR_CCA_ITER);
 }
 
-__global__ void __launch_bounds__(256) k_cca_merge(const CcaJob* __restrict__ jobs, uint32_t* dev_err) {
+constexpr int kMergeTiles = 4;   // tiles per CTA of k_cca_merge (along x)
+__global__ void __launch_bounds__(128) k_cca_merge(const CcaJob* __restrict__ jobs, uint32_t* dev_err) {
   const CcaJob J = jobs[blockIdx.z];
-  const int tx0 = blockIdx.x * CT, ty0 = blockIdx.y * CT;
-  if (tx0 >= J.w || ty0 >= J.h) return;
+  const int ty0 = blockIdx.y * CT;
+  if (blockIdx.x * kMergeTiles * CT >= J.w || ty0 >= J.h) return;
   const int w = J.w, h = J.h;
   bool ok = true;
   // tile border pixels: top row (32), left column (31 more), right column (31 more)
-  for (int t = threadIdx.x; t < 3 * CT; t += blockDim.x) {
+  for (int tt = threadIdx.x; tt < kMergeTiles * 3 * CT; tt += blockDim.x) {
+    const int tx0 = (blockIdx.x * kMergeTiles + tt / (3 * CT)) * CT, t = tt % (3 * CT);
+    if (tx0 >= w) continue;
     int lx, ly;
     if (t < CT) { lx = t; ly = 0; }
     else if (t < 2 * CT - 1) { lx = 0; ly = t - CT + 1; }
@@ -194,62 +197,77 @@ __device__ __forceinline__ int tile_local(int v, int base, int w, float inv_w) {
   return dx < CT && dx < w ? dy * CT + dx : -1;
 }
 
+constexpr int kCountTiles = 2;   // tiles per CTA of k_cc_count (along x)
 __global__ void __launch_bounds__(256) k_cc_count(const CcaJob* __restrict__ jobs) {
-  constexpr int kPer = CT * CT / 256;   // pixels per thread
-  __shared__ unsigned s_cnt[CT * CT];   // pixels per local root
-  __shared__ int s_root[CT * CT];       // component root of each referenced local root
+  constexpr int kPer = CT * CT / 256;   // pixels per thread and tile
+  __shared__ unsigned s_cnt[kCountTiles][CT * CT];   // pixels per local root
+  __shared__ int s_root[kCountTiles][CT * CT];       // component root of each referenced local root
   __shared__ unsigned s_total;
   const CcaJob J = jobs[blockIdx.z];
   const int w = J.w, h = J.h;
-  const int tx0 = blockIdx.x * CT, ty0 = blockIdx.y * CT;
-  if (tx0 >= w || ty0 >= h) return;
-  const int base = ty0 * w + tx0;
+  const int ty0 = blockIdx.y * CT;
+  if (blockIdx.x * kCountTiles * CT >= w || ty0 >= h) return;
   const float inv_w = 1.0f / (float)w;
-  for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) s_cnt[i] = 0u;
+  for (int i = threadIdx.x; i < kCountTiles * CT * CT; i += blockDim.x) (&s_cnt[0][0])[i] = 0u;
   if (threadIdx.x == 0) s_total = 0;
   __syncthreads();
-  int u[kPer], v[kPer];
+  int u[kCountTiles][kPer], v[kCountTiles][kPer];
   unsigned mine = 0;
 #pragma unroll
-  for (int k = 0; k < kPer; ++k) {
-    const int i = threadIdx.x + 256 * k;
-    const int x = tx0 + (i & (CT - 1)), y = ty0 + (i >> 5);
-    v[k] = (x < w && y < h) ? J.lab[(int64_t)y * w + x] : -1;
-  }
+  for (int tt = 0; tt < kCountTiles; ++tt)
 #pragma unroll
-  for (int k = 0; k < kPer; ++k) {
-    u[k] = -1;
-    if (v[k] >= 0) {
+    for (int k = 0; k < kPer; ++k) {
       const int i = threadIdx.x + 256 * k;
-      const int t = tile_local(v[k], base, w, inv_w);
-      u[k] = t >= 0 ? t : i;
-      atomicAdd(&s_cnt[u[k]], 1u);
-      ++mine;
+      const int x = (blockIdx.x * kCountTiles + tt) * CT + (i & (CT - 1)), y = ty0 + (i >> 5);
+      v[tt][k] = (x < w && y < h) ? J.lab[(int64_t)y * w + x] : -1;
+    }
+#pragma unroll
+  for (int tt = 0; tt < kCountTiles; ++tt) {
+    const int tx0 = (blockIdx.x * kCountTiles + tt) * CT;
+    const int base = ty0 * w + tx0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      u[tt][k] = -1;
+      if (v[tt][k] >= 0) {
+        const int i = threadIdx.x + 256 * k;
+        const int t = tile_local(v[tt][k], base, w, inv_w);
+        u[tt][k] = t >= 0 ? t : i;
+        atomicAdd(&s_cnt[tt][u[tt][k]], 1u);
+        ++mine;
+      }
     }
   }
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < kPer; ++k) {
-    const int i = threadIdx.x + 256 * k;
-    const unsigned c = s_cnt[i];
-    if (c) {   // pixel i is a local root some pixel of the tile refers to
-      const int g = (ty0 + (i >> 5)) * w + tx0 + (i & (CT - 1));
-      const int R = find_root(J.lab, g);
-      s_root[i] = R;
-      atomicAdd(&J.size[R], c);
-      if (R == g) J.roots[atomicAdd(reinterpret_cast<unsigned long long*>(&J.cut[5]), 1ull)] = R;
+  for (int tt = 0; tt < kCountTiles; ++tt) {
+    const int tx0 = (blockIdx.x * kCountTiles + tt) * CT;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int i = threadIdx.x + 256 * k;
+      const unsigned c = s_cnt[tt][i];
+      if (c) {   // pixel i is a local root some pixel of the tile refers to
+        const int g = (ty0 + (i >> 5)) * w + tx0 + (i & (CT - 1));
+        const int R = find_root(J.lab, g);
+        s_root[tt][i] = R;
+        atomicAdd(&J.size[R], c);
+        if (R == g) J.roots[atomicAdd(reinterpret_cast<unsigned long long*>(&J.cut[5]), 1ull)] = R;
+      }
     }
   }
   for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
   if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&s_total, mine);
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < kPer; ++k) {
-    if (u[k] < 0) continue;
-    const int R = s_root[u[k]];
-    if (R != v[k]) {
-      const int i = threadIdx.x + 256 * k;
-      J.lab[(int64_t)(ty0 + (i >> 5)) * w + tx0 + (i & (CT - 1))] = R;   // other tiles may follow it: R is an ancestor
+  for (int tt = 0; tt < kCountTiles; ++tt) {
+    const int tx0 = (blockIdx.x * kCountTiles + tt) * CT;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      if (u[tt][k] < 0) continue;
+      const int R = s_root[tt][u[tt][k]];
+      if (R != v[tt][k]) {
+        const int i = threadIdx.x + 256 * k;
+        J.lab[(int64_t)(ty0 + (i >> 5)) * w + tx0 + (i & (CT - 1))] = R;   // other tiles may follow it: R is an ancestor
+      }
     }
   }
   if (threadIdx.x == 0 && s_total) atomicAdd(reinterpret_cast<unsigned long long*>(&J.cut[0]), (unsigned long long)s_total);
@@ -419,7 +437,7 @@ void launch_cca(const CcaJob* jobs, int n_jobs, int max_w, int max_h, uint32_t* 
   dim3 tiles((max_w + CT - 1) / CT, (max_h + CT - 1) / CT, n_jobs);
   const int tiles_x = (max_w + CT - 1) / CT;
   k_cca_local<<<dim3((tiles_x + kCcaWarps - 1) / kCcaWarps, tiles.y, n_jobs), kCcaWarps * 32, 0, s>>>(jobs, dev_err);
-  k_cca_merge<<<tiles, 128, 0, s>>>(jobs, dev_err);
+  k_cca_merge<<<dim3((tiles_x + kMergeTiles - 1) / kMergeTiles, tiles.y, n_jobs), 128, 0, s>>>(jobs, dev_err);
 }
 
 void launch_cc_filter(const CcaJob* jobs, int n_jobs, int max_w, int max_h, cudaStream_t s) {
@@ -428,7 +446,8 @@ void launch_cc_filter(const CcaJob* jobs, int n_jobs, int max_w, int max_h, cuda
   int bpj = (int)((n + 256 * 8 - 1) / (256 * 8));
   if (bpj > 1184) bpj = 1184;
   if (bpj < 1) bpj = 1;
-  k_cc_count<<<dim3((max_w + CT - 1) / CT, (max_h + CT - 1) / CT, n_jobs), 256, 0, s>>>(jobs);
+  const int tiles_x = (max_w + CT - 1) / CT;
+  k_cc_count<<<dim3((tiles_x + kCountTiles - 1) / kCountTiles, (max_h + CT - 1) / CT, n_jobs), 256, 0, s>>>(jobs);
   const int rpj = std::max(1, std::min(bpj, 148));   // root-list passes: roots are few
   k_cc_hist<<<dim3(rpj, n_jobs), 256, 0, s>>>(jobs);
   k_cc_cut<<<n_jobs, 1024, 0, s>>>(jobs);
