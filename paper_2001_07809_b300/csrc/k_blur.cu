@@ -373,24 +373,42 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
   if (tid < 8) { s_lo[tid] = jobs[blockIdx.z].lo[tid]; s_hi[tid] = jobs[blockIdx.z].hi[tid]; }
   for (int t = tid; t < nt; t += kStripThreads) s_tap[t] = J.taps[t];
   __syncthreads();
-  // mask bits of the band (warp-wide ballots of 32 columns) and per-step flags
+  // mask bits of the band (little-endian: bit j of word q is pixel 32q + j) and per-step flags
   const int nr = J.n_ranges;
-  const int npix = kSB * nsteps * BX;   // a multiple of 64: the loop bounds are warp-uniform
-  for (int p0 = warp * 32 + lane; p0 < npix; p0 += 8 * kStripThreads) {
-    uint32_t dv[8];   // eight independent loads in flight, then the ballots
+  const int npix = kSB * nsteps * BX;
+  uint8_t* mbytes = reinterpret_cast<uint8_t*>(s_mbits);   // byte g: pixels 8g .. 8g+7 of the band, bit j = pixel 8g+j
+  const bool vec8 = ox == BX && ((reinterpret_cast<uintptr_t>(J.disp) | ((int64_t)w * 2) | (tx0 * 2)) & 15) == 0;
+  if (vec8) {
+    // eight disparities per 16-byte load, all of a thread's loads in flight
+    constexpr int kG = (kBandRows * BX / 8 + kStripThreads - 1) / kStripThreads;   // groups per thread
+    uint4 dv[kG];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int p = p0 + k * kStripThreads, i = p / BX, c = p % BX;
-      dv[k] = (p < npix && i < rows && c < ox) ? (uint32_t)J.disp[(int64_t)(yb0 + i) * w + tx0 + c] : 0x10000u;
+    for (int k = 0; k < kG; ++k) {
+      const int g = tid + k * kStripThreads, i = g / (BX / 8), c = (g % (BX / 8)) * 8;
+      dv[k] = g * 8 < npix && i < rows
+                  ? *reinterpret_cast<const uint4*>(J.disp + (int64_t)(yb0 + i) * w + tx0 + c)
+                  : make_uint4(0u, 0u, 0u, 0u);
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int p = p0 + k * kStripThreads;
-      if (p < npix) {
-        const bool m = dv[k] <= 0xFFFFu && !in_focus((uint16_t)dv[k], s_lo, s_hi, nr);
-        const unsigned word = __ballot_sync(0xffffffffu, m);
-        if (lane == 0) s_mbits[p >> 5] = word;
-      }
+    for (int k = 0; k < kG; ++k) {
+      const int g = tid + k * kStripThreads, i = g / (BX / 8);
+      if (g * 8 >= npix) continue;
+      const uint32_t wv[4] = {dv[k].x, dv[k].y, dv[k].z, dv[k].w};
+      uint32_t m = 0;
+      if (i < rows)
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          m |= (uint32_t)!in_focus((uint16_t)(wv[j >> 1] >> (16 * (j & 1))), s_lo, s_hi, nr) << j;
+      mbytes[g] = (uint8_t)m;
+    }
+  } else {
+    for (int g = tid; g * 8 < npix; g += kStripThreads) {
+      const int i = g / (BX / 8), c0 = (g % (BX / 8)) * 8;
+      uint32_t m = 0;
+      if (i < rows)
+        for (int j = 0; j < 8; ++j)
+          if (c0 + j < ox) m |= (uint32_t)!in_focus(J.disp[(int64_t)(yb0 + i) * w + tx0 + c0 + j], s_lo, s_hi, nr) << j;
+      mbytes[g] = (uint8_t)m;
     }
   }
   __syncthreads();
