@@ -175,13 +175,42 @@ __global__ void __launch_bounds__(kBlurThreads) k_blur(const BlurJob* __restrict
   __syncthreads();
   // blur mask of the tile (1 = blurred: the disparity is in no range of interest)
   int any = 0;
+  if (ox == BX && ((reinterpret_cast<uintptr_t>(J.disp) | ((int64_t)w * 2) | (tx0 * 2)) & 15) == 0) {
+    // eight disparities per 16-byte load, all of a thread's loads issued first
+    constexpr int kG = (BY * BX / 8 + kBlurThreads - 1) / kBlurThreads;
+    uint4 dv[kG];
+#pragma unroll
+    for (int k = 0; k < kG; ++k) {
+      const int g = tid + k * kBlurThreads, i = g / (BX / 8), c = (g % (BX / 8)) * 8;
+      dv[k] = g < BY * BX / 8 && i < oy ? *reinterpret_cast<const uint4*>(J.disp + (int64_t)(ty0 + i) * w + tx0 + c)
+                                        : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int k = 0; k < kG; ++k) {
+      const int g = tid + k * kBlurThreads, i = g / (BX / 8);
+      if (g >= BY * BX / 8) continue;
+      const uint32_t wv[4] = {dv[k].x, dv[k].y, dv[k].z, dv[k].w};
+      uint32_t lo = 0, hi = 0;   // mask bytes of pixels 0..3 and 4..7
+      if (i < oy)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const uint32_t m = !in_focus((uint16_t)(wv[j >> 1] >> (16 * (j & 1))), s_lo, s_hi, nr);
+          if (j < 4) lo |= m << (8 * j);
+          else hi |= m << (8 * (j - 4));
+        }
+      reinterpret_cast<uint32_t*>(s_mask)[2 * g] = lo;       // s_mask is 4-byte aligned (not 8)
+      reinterpret_cast<uint32_t*>(s_mask)[2 * g + 1] = hi;
+      any |= (lo | hi) != 0;
+    }
+  } else {
 #pragma unroll 7
-  for (int t = tid; t < BY * BX; t += kBlurThreads) {
-    const int i = t / BX, j = t % BX;  // BX is a power of two
-    uint8_t m = 0;
-    if (i < oy && j < ox) m = !in_focus(J.disp[(int64_t)(ty0 + i) * w + tx0 + j], s_lo, s_hi, nr);
-    s_mask[t] = m;
-    any |= m;
+    for (int t = tid; t < BY * BX; t += kBlurThreads) {
+      const int i = t / BX, j = t % BX;  // BX is a power of two
+      uint8_t m = 0;
+      if (i < oy && j < ox) m = !in_focus(J.disp[(int64_t)(ty0 + i) * w + tx0 + j], s_lo, s_hi, nr);
+      s_mask[t] = m;
+      any |= m;
+    }
   }
   if (any) s_any = 1;
   if (fast) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
