@@ -11,6 +11,9 @@
 // of each input row's byte run, when the tile fits in shared memory.
 // Only pixels whose disparity lies in no range of interest take the blurred
 // value; the rest are copied, and a tile with no such pixel is copied as is.
+// A second form (k_blur_strip, below) walks 64-column strips down the image
+// and keeps the horizontally filtered rows in a ring, so no halo row is
+// filtered twice; both forms apply the same taps in the same order.
 #include <algorithm>
 #include "sb_common.cuh"
 

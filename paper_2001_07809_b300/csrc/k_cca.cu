@@ -1,12 +1,12 @@
 // Connected components analysis and small-component removal (Section III).
 //
-// Labelling (8-connectivity) is union-find: each 32x32 tile first unites its
-// pixels in shared memory (at most two unions per pixel, by the decision tree
-// of two-pass labelling), then pixels on tile borders unite across tiles in
-// global memory, then every pixel jumps to its root while the sizes are
-// counted.  Unions always hang the larger root under the smaller (atomicMin),
-// so a component's final root is its smallest linear index: the same label a
-// raster-order flood fill gives.
+// Labelling (8-connectivity) is union-find: a warp labels each 32x32 tile by
+// sweeping its rows in order with one node per horizontal run (in shared
+// memory), then pixels on tile borders unite across tiles in global memory,
+// then every tile-local root is chased to its component root while the sizes
+// are counted.  Unions always hang the larger root under the smaller
+// (atomicMin), so a component's final root is its smallest linear index: the
+// same label a raster-order flood fill gives.
 //
 // Removal: the components are ordered by (size, label) and the longest
 // prefix holding at most floor(frac * N_b) pixels is removed.  On the device

@@ -21,6 +21,10 @@
 //     the same add-entering / drop-leaving update) and, at anchor pixels
 //     (warp-uniform test), reduces (S << 10 | d) over the 32 lanes with
 //     redux.sync and atomically keeps the minimum in the per-pixel key.
+// Tail kernel: the 1..8 disparities past the last whole chunk of 32 (one
+// disparity at D = 2^n), a thread per column with the vertical sums and a
+// warp prefix sum per row for the horizontal ones, so the box-sum work list
+// need not spend a mostly idle chunk on them.
 // Direct variant (for low boundary density and small blocks): a warp per
 // anchor, lanes = disparities, vabsdiff4.add over the re-aligned 4-byte
 // words of each window row.
