@@ -153,6 +153,9 @@ SAD_CASES = [
     (65, 700, 256, 41),
     # 1..8 disparities past the last whole chunk of 32 (the tail kernel's range)
     (55, 330, 39, 11), (70, 360, 71, 63), (50, 300, 98, 1), (66, 520, 135, 25),
+    # the largest disparity range the 10-bit key holds (32 whole chunks), a tail
+    # of 8 at a large range, and a 9-disparity partial chunk with the largest block
+    (40, 1100, 1023, 5), (45, 1100, 999, 9), (70, 1200, 1000, 63),
 ]
 
 
@@ -341,6 +344,26 @@ def test_blur_forms_agree_with_oracle(ctx, sigma):
     assert np.array_equal(outs[2][keep], rgb[keep])
 
 
+@pytest.mark.parametrize("sigma", [0.5, 20.0])
+def test_blur_strip_small_and_large_radius(ctx, sigma):
+    # R = 2 and R = 60 (a ring of 160 filtered rows): two bands, the second
+    # ragged, and a ragged last strip; every form gives the oracle's bytes within one level
+    h, w = 600, 300
+    rgb = RNG.integers(0, 256, (h, w, 3)).astype(np.uint8)
+    disp = RNG.integers(0, 40, (h, w)).astype(np.uint16)
+    ranges = [(10, 20)]
+    want = oracle.selective_blur(rgb, disp, ranges, sigma)
+    outs = []
+    try:
+        for form in (sb.SB_BLUR_TILES_112, sb.SB_BLUR_STRIP):
+            sb.sb_set_blur_form(ctx, form)
+            outs.append(blur(ctx, rgb, disp, ranges, sigma))
+    finally:
+        sb.sb_set_blur_form(ctx, sb.SB_BLUR_AUTO)
+    assert np.abs(outs[1].astype(int) - want.astype(int)).max() <= 1
+    assert np.array_equal(outs[0], outs[1])
+
+
 def test_blur_form_rejects_unknown_values(ctx):
     with pytest.raises(sb.SbError):
         sb.sb_set_blur_form(ctx, 48)
@@ -512,6 +535,19 @@ def test_invalid_arguments_raise(ctx):
     ok = sb.make_params(max_disp=4, block=5, k=2)
     sb.sb_run(ctx, [sb.Pair(left, left, ok, out)])    # the context is still usable
     ctx.synchronize()
+
+
+def test_pipeline_large_disparity_range(ctx):
+    # D = 600 on a 700-pixel-wide pair: the domain is 92 columns wide, the SAD
+    # runs 18 whole chunks of 32 and a partial one (601 = 18 * 32 + 25)
+    w, h, D, B, K = 700, 90, 600, 9, 4
+    r = synth.Rng(900)
+    layers = synth._c2_style_layers(r, w, h, 120, contrast=60)
+    sc = synth.Scene(w, h, layers, noise_q8=256, noise_seed=r.u64())
+    left, right, _ = sc.render()
+    p = synth.Params(k=K, max_disp=D, block=B, sigma=2.0, ranges=[(40, D)])
+    (o_rgb, o_disp), = run_pairs(ctx, [(left, right, p)], sb.SB_RUN_BATCHED)
+    _compare_full(o_rgb, o_disp, left, right, p)
 
 
 def test_minimum_sizes(ctx):
