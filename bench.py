@@ -48,6 +48,10 @@ BOX_DISPARITIES_C3 = 256
 # its own
 SAD_DRAM_BYTES_PER_PAIR = (456.510208e6 + 168.654592e6) / 8
 METRIC = "stereo pairs/s at 4096x2304 (batched vs per-pair), SAD Gcell/s, p99 latency"
+# --sad-variant: the library's per-pair choice (box sums at this workload's density), or either
+# SAD kernel forced (the roofline then describes that kernel)
+SAD_VARIANTS = {"auto": lambda sb: sb.SB_SAD_AUTO, "boxsum": lambda sb: sb.SB_SAD_BOXSUM,
+                "direct": lambda sb: sb.SB_SAD_DIRECT}
 WORKLOAD = ("batched video: %d pairs of 4096x2304 RGB per GPU, 12 drifting layers (seed 2), D=256, block 41, K=8, "
             "sigma 8, interest [120,256]")
 
@@ -384,7 +388,7 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     params = sb.make_params(k=K_C3, max_disp=D_C3, block=B_C3, disp_threshold=1, sigma=SIGMA_C3,
-                            ranges=INTEREST_C3, sad_variant=sb.SB_SAD_AUTO)
+                            ranges=INTEREST_C3, sad_variant=SAD_VARIANTS[args.sad_variant](sb))
     ctx = sb.Context(local)
     pairs = [sb.Pair(lefts[i], rights[i], params, outs[i], disps[i]) for i in range(P)]
     flags = sb.SB_RUN_BATCHED | sb.SB_RUN_GRAPH
@@ -437,10 +441,11 @@ def run_ours(args):
     plain_ms = e0.elapsed_time(e1) / plain_steps
     plain_value = aggregate_rate(P, world, max_ranks(plain_ms))
     # identical outputs batched vs plain (spot check of one pair)
-    ref_out, ref_disp = outs[7].clone(), disps[7].clone()
+    spot = min(7, P - 1)
+    ref_out, ref_disp = outs[spot].clone(), disps[spot].clone()
     sb.sb_run(ctx, pairs, flags)
     ctx.synchronize()
-    same = bool(torch.equal(ref_out, outs[7]) and torch.equal(ref_disp, disps[7]))
+    same = bool(torch.equal(ref_out, outs[spot]) and torch.equal(ref_disp, disps[spot]))
 
     # anchors -> SAD cell rate and roofline of the box-sum kernel
     nb = anchor_counts(ctx, sb, torch, lefts, rights, params)
@@ -483,7 +488,7 @@ def run_ours(args):
         t1 = time.perf_counter()
         barrier()
         e2e_s = max_ranks((t1 - t0) / e2e_steps)
-        same = same and bool(torch.equal(ho[7].cuda(), outs[7]))
+        same = same and bool(torch.equal(ho[spot].cuda(), outs[spot]))
         e2e = {"value": P * world / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": P * H * W * 6,
                "d2h_bytes_per_step": P * H * W * 5, "ms_per_step": e2e_s * 1000.0}
         del hl, hr, ho, hd
@@ -502,6 +507,31 @@ def run_ours(args):
         cpu = {"value": 1.0 / c["seconds_per_pair"], "unit": "pairs/s", "cores": 1, "kind": "oracle",
                "sample": c["sample"], "stages_s": c["stages_s"]}
 
+    if args.sad_variant == "direct":
+        # the direct kernel runs in the "sad_rest" stage (after the box-sum launch, which skips
+        # every pair here); its work is the paper's: N_b (D+1) B^2 absolute differences, four per
+        # vabsdiff4.add, against the vabsdiff4 cell rate (64 lanes per SM per clock x 4 cells)
+        direct_ms = stage_avg[sb.STAGES.index("sad_rest")]
+        cell_peak = 148 * 64 * 4 * sm_max * 1e6 / 1e12    # Tcell/s
+        got = cells / (direct_ms / 1000.0) / 1e12
+        roofline = {"bound": "alu", "kernel": "k_sad_direct", "achieved": got, "peak": cell_peak,
+                    "unit": "Tcell/s", "frac": got / cell_peak, "traffic": None,
+                    "traffic_note": "not captured for this form",
+                    "peak_note": "derived: 148 SMs x 64 vabsdiff4 lanes x 4 cells x %.0f MHz" % sm_max,
+                    "measured_rates": rates,
+                    "frac_of_measured_vabsdiff4": (got / rates["vabsdiff4_tcell_s"]) if "vabsdiff4_tcell_s" in rates else None,
+                    "cells_per_launch": cells, "launch_ms": direct_ms}
+    else:
+        roofline = {"bound": "alu", "kernel": "k_sad_boxsum", "achieved": achieved, "peak": alu_peak,
+                    "unit": "Tops/s", "frac": achieved / alu_peak,
+                    "traffic": SAD_DRAM_BYTES_PER_PAIR * P,
+                    "traffic_note": "bytes per launch: ncu dram read+write of an 8-pair launch, x P/8",
+                    "peak_note": "derived: 148 SMs x 128 INT32 lanes x %.0f MHz (max SM clock)" % sm_max,
+                    "measured_rates": rates,
+                    "frac_of_measured_iadd": (achieved / rates["iadd_tops"]) if "iadd_tops" in rates else None,
+                    "ops_per_launch": ops,
+                    "ops_note": "6 ops x |Omega| x 256 disparities (the box-sum chunks, d = 0..255) x pairs",
+                    "launch_ms": box_ms}
     if rank == 0:
         line = {
             "metric": METRIC,
@@ -509,22 +539,14 @@ def run_ours(args):
             "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u8/int32 (SAD), fp32 (blur)", "data": "synthetic",
             "config": {"workload": WORKLOAD % P,
-                       "form": "batched, CUDA graph replay", "l2": "inputs 56.6 MB per pair x %d, larger than L2" % P},
+                       "form": "batched, CUDA graph replay", "l2": "inputs 56.6 MB per pair x %d, larger than L2" % P,
+                       "sad_variant": args.sad_variant},
             "per_pair_plain": {"value": plain_value, "unit": "pairs/s", "ms_per_step": plain_ms},
             "batched_equals_plain": same,
             "sad_gcell_s": cells / (sad_ms / 1000.0) / 1e9,
             "stage_ms": dict(zip(sb.STAGES, stage_avg)),
             "anchors_per_pair": sum(nb) / len(nb),
-            "roofline": {"bound": "alu", "kernel": "k_sad_boxsum", "achieved": achieved, "peak": alu_peak,
-                         "unit": "Tops/s", "frac": achieved / alu_peak,
-                         "traffic": SAD_DRAM_BYTES_PER_PAIR * P,
-                         "traffic_note": "bytes per launch: ncu dram read+write of an 8-pair launch, x P/8",
-                         "peak_note": "derived: 148 SMs x 128 INT32 lanes x %.0f MHz (max SM clock)" % sm_max,
-                         "measured_rates": rates,
-                         "frac_of_measured_iadd": (achieved / rates["iadd_tops"]) if "iadd_tops" in rates else None,
-                         "ops_per_launch": ops,
-                         "ops_note": "6 ops x |Omega| x 256 disparities (the box-sum chunks, d = 0..255) x pairs",
-                         "launch_ms": box_ms},
+            "roofline": roofline,
             "e2e": e2e,
             "autotune": {"box_sum_work_items": {"batched": tune_batched[0], "per_pair": tune_plain[0]},
                          "blur_tile_rows": {"batched": tune_batched[1], "per_pair": tune_plain[1]},
@@ -633,6 +655,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--accuracy", action="store_true", help="Eq. 3 study of the open readings, then exit")
+    ap.add_argument("--sad-variant", choices=sorted(SAD_VARIANTS), default="auto",
+                    help="SAD kernel: the per-pair automatic choice (default) or one forced")
     args = ap.parse_args()
     if args.accuracy:
         return run_accuracy(args)
