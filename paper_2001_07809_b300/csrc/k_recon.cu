@@ -27,6 +27,7 @@ namespace sb {
 
 namespace {
 constexpr uint16_t NONE = SB_UNDET16;
+constexpr uint16_t kAnchorBit = 0x8000;   // Algorithm 1, between its passes: the pixel is an anchor
 // the final map's entry for (y, x) of the working orientation
 __device__ __forceinline__ uint16_t& out_at(const ReconJob& J, int y, int x) {
   return J.out[(int64_t)y * J.w + (J.mirror ? J.w - 1 - x : x)];
@@ -59,7 +60,9 @@ __global__ void __launch_bounds__(256) k_recon_fill(const ReconJob* __restrict__
     const int src_lane = below ? 31 - __clz(below) : 0;
     const uint16_t left = __shfl_sync(0xffffffffu, v, src_lane);
     const uint16_t pd = below ? left : carry;
-    if (x < w) dst[x] = anc ? v : pd;
+    // anchors are marked with bit 15 (values stay <= 1023, and NONE = 0xffff
+    // has bits 10..14 set), so the second pass needs only this row
+    if (x < w) dst[x] = anc ? (uint16_t)(v | kAnchorBit) : pd;
     if (mask) carry = __shfl_sync(0xffffffffu, v, 31 - __clz(mask));
   }
   __syncwarp();
@@ -68,17 +71,15 @@ __global__ void __launch_bounds__(256) k_recon_fill(const ReconJob* __restrict__
   const int nchunks = (w + 31) / 32;
   for (int ci = nchunks - 1; ci >= 0; --ci) {
     const int x = ci * 32 + lane;
-    const uint16_t v = x < w ? src(x) : NONE;
-    const bool anc = v != NONE;
+    const uint16_t t = x < w ? dst[x] : NONE;
+    const bool anc = t != NONE && (t & kAnchorBit);
+    const uint16_t v = anc ? (uint16_t)(t & ~kAnchorBit) : t;   // the anchor's value, or the left carry
     const unsigned mask = __ballot_sync(0xffffffffu, anc);
     const unsigned above = lane == 31 ? 0u : (mask & ~((2u << lane) - 1u));
     const int src_lane = above ? __ffs(above) - 1 : 0;
     const uint16_t right = __shfl_sync(0xffffffffu, v, src_lane);
     const uint16_t nd = above ? right : carry;
-    if (x < w && !anc) {
-      const uint16_t pd = dst[x];
-      dst[x] = (pd != NONE && pd == nd) ? pd : NONE;
-    }
+    if (x < w) dst[x] = anc ? v : ((v != NONE && v == nd) ? v : NONE);
     if (mask) carry = __shfl_sync(0xffffffffu, v, __ffs(mask) - 1);
   }
 }
