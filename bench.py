@@ -9,15 +9,21 @@ disparities outside [120, 256].  A step is one pass of the whole pipeline
 reconstruction, selective blur) over the 250 pairs.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--pairs P] [--sad-variant auto|boxsum|direct] [--no-e2e] [--no-cpu]
+                  [--no-serve] [--accuracy]
 
 Prints one JSON line (rank 0).  ``value`` is pairs/s with inputs resident in
 HBM (batched form replayed from a CUDA graph); ``e2e`` is the same metric
 through sb_run with pinned HOST buffers (copies inside the timed region);
 ``per_pair_plain`` is the per-pair launch form on the same GPU;
-``sad_gcell_s`` counts N_b (D+1) B^2 cells over the SAD kernel time;
-``roofline`` is for the box-sum SAD kernel (integer ALU bound);
-``cpu_baseline`` is the CPU oracle timed on a bounded sample of one pair.
-Under torchrun each rank processes its own 250 frames (weak scaling).
+``stage_ms`` splits the step by stage (CUDA events inside the graph);
+``sad_gcell_s`` counts N_b (D+1) B^2 cells over the SAD kernels' time;
+``roofline`` is for the SAD kernel the run uses (the box sums by default:
+integer ALU bound; ``--sad-variant direct`` reports the direct kernel
+against the vabsdiff4 cell rate); ``uneven_batch`` and ``serving`` are the
+mixed-size batch and the served request stream; ``cpu_baseline`` is the CPU
+oracle timed on a bounded sample of one pair (``all_cores``: one process per
+host core).  Under torchrun each rank processes its own frames (weak scaling).
 """
 from __future__ import annotations
 
