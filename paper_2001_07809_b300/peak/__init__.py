@@ -1,7 +1,8 @@
 """Measured instruction rates of the current GPU (see int_peak.cu).
 
 ``measure()`` returns thread-instructions per second for add.u32,
-vabsdiff4 (four byte cells each), fma.f32 and prmt, measured with CUDA
+vabsdiff4 (four byte cells each), fma.f32, prmt and fma.f32x2 (two FMAs
+each), measured with CUDA
 events over a full grid.  Used by bench.py beside the derived peaks."""
 from __future__ import annotations
 
@@ -18,9 +19,10 @@ def measure() -> dict:
     lib = ctypes.CDLL(LIB)
     lib.sb_peak_measure.argtypes = [ctypes.POINTER(ctypes.c_double)]
     lib.sb_peak_measure.restype = ctypes.c_int
-    rates = (ctypes.c_double * 4)()
+    rates = (ctypes.c_double * 5)()
     if lib.sb_peak_measure(rates) != 0:
         raise RuntimeError("sb_peak_measure failed")
     return {"iadd_tops": rates[0] / 1e12, "vabsdiff4_tinstr_s": rates[1] / 1e12,
             "vabsdiff4_tcell_s": 4 * rates[1] / 1e12, "ffma_tflops": 2 * rates[2] / 1e12,
-            "prmt_tinstr_s": rates[3] / 1e12}
+            "prmt_tinstr_s": rates[3] / 1e12, "ffma2_tinstr_s": rates[4] / 1e12,
+            "ffma2_tflops": 4 * rates[4] / 1e12}

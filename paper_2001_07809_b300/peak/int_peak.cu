@@ -17,14 +17,18 @@ template <int OP>
 __global__ void __launch_bounds__(256) k_peak(uint32_t* out, uint32_t seed) {
   uint32_t a[kChains], b[kChains];
   float f[kChains];
+  uint64_t f2[kChains];   // packed float pairs (fma.rn.f32x2)
 #pragma unroll
   for (int i = 0; i < kChains; ++i) {
     a[i] = seed * (threadIdx.x + 1 + i);
     b[i] = seed ^ (i * 0x9e3779b9u + threadIdx.x);
     f[i] = (float)(a[i] & 255);
+    asm("mov.b64 %0, {%1, %2};" : "=l"(f2[i]) : "f"(f[i]), "f"(f[i] + 1.f));
   }
   const uint32_t c = seed + 7;
   const float fb = 1.0001f;
+  uint64_t fb2;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(fb2) : "f"(fb));
   for (int it = 0; it < kIters; ++it) {
 #pragma unroll
     for (int i = 0; i < kChains; ++i) {
@@ -32,11 +36,12 @@ __global__ void __launch_bounds__(256) k_peak(uint32_t* out, uint32_t seed) {
       if (OP == 1) asm volatile("vabsdiff4.u32.u32.u32.add %0, %1, %2, %0;" : "+r"(a[i]) : "r"(b[i]), "r"(c));
       if (OP == 2) asm volatile("fma.rn.f32 %0, %0, %1, %1;" : "+f"(f[i]) : "f"(fb));
       if (OP == 3) asm volatile("prmt.b32 %0, %0, %1, 0x5140;" : "+r"(a[i]) : "r"(b[i]));
+      if (OP == 4) asm volatile("fma.rn.f32x2 %0, %0, %1, %1;" : "+l"(f2[i]) : "l"(fb2));
     }
   }
   uint32_t s = 0;
 #pragma unroll
-  for (int i = 0; i < kChains; ++i) s += a[i] + (uint32_t)f[i];
+  for (int i = 0; i < kChains; ++i) s += a[i] + (uint32_t)f[i] + (uint32_t)f2[i];
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
@@ -59,8 +64,9 @@ int time_op(int blocks, uint32_t* out, double* per_s) {
 }
 }  // namespace
 
-// rates[0..3]: thread-instructions per second of add.u32, vabsdiff4 (4 byte
-// cells each), fma.f32 and prmt on the current device.  Returns 0 on success.
+// rates[0..4]: thread-instructions per second of add.u32, vabsdiff4 (4 byte
+// cells each), fma.f32, prmt and fma.f32x2 (two FMAs each) on the current
+// device.  Returns 0 on success.
 extern "C" int sb_peak_measure(double* rates) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
@@ -72,6 +78,7 @@ extern "C" int sb_peak_measure(double* rates) {
   rc |= time_op<1>(blocks, out, &rates[1]);
   rc |= time_op<2>(blocks, out, &rates[2]);
   rc |= time_op<3>(blocks, out, &rates[3]);
+  rc |= time_op<4>(blocks, out, &rates[4]);
   cudaFree(out);
   return rc;
 }
