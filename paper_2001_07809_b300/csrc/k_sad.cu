@@ -19,8 +19,9 @@
 //     S = sum_{|j|<=r} V(c+j) along its row segment in blocks of 8 outputs
 //     (a zero column before each row of column sums lets every output use
 //     the same add-entering / drop-leaving update) and, at anchor pixels
-//     (warp-uniform test), reduces (S << 10 | d) over the 32 lanes with
-//     redux.sync and atomically keeps the minimum in the per-pixel key.
+//     (warp-uniform bits, one uniform jump per four outputs), reduces
+//     (S << 10 | d) over the 32 lanes with redux.sync and atomically keeps
+//     the minimum in the per-pixel key.
 // Tail kernel: the 1..8 disparities past the last whole chunk of 32 (one
 // disparity at D = 2^n), a thread per column with the vertical sums and a
 // warp prefix sum per row for the horizontal ones, so the box-sum work list
@@ -73,6 +74,52 @@ __device__ __forceinline__ void stage_chunk(uint8_t* dst, const uint8_t* img, in
 }  // namespace
 
 __host__ __device__ int sad_boxsum_strip(int r) { return (kVsCols - 1 - 2 * r) & ~15; }
+
+namespace {
+// Anchor emission for four consecutive outputs K0 .. K0+3 of a block whose
+// anchor bits are the compile-time nibble NIB: the warp minimum of
+// (S << 10 | d) over the 32 disparities of each anchor first, then lane 0's
+// atomic minima into the argmin keys, so that the latencies of the
+// reductions overlap instead of each atomic waiting for its own.  Lanes past
+// D carry dbits = all ones, which makes their key all ones (never the minimum).
+template <unsigned NIB, int K0>
+__device__ __forceinline__ void emit_nibble(const uint32_t (&Sv)[8], uint32_t dbits, uint32_t* kp, int lane) {
+  uint32_t m[4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+    if (NIB & (1u << b)) m[b] = __reduce_min_sync(0xffffffffu, (Sv[K0 + b] << SB_KEY_DBITS) | dbits);
+  if (lane == 0) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      if (NIB & (1u << b)) atomicMin(kp + K0 + b, m[b]);
+  }
+}
+
+// one case per non-empty nibble value: the bits are warp-uniform, so the
+// switch is a uniform jump and every case's code is straight-line
+template <int K0>
+__device__ __forceinline__ void emit_block_half(unsigned nib, const uint32_t (&Sv)[8], uint32_t dbits, uint32_t* kp,
+                                                int lane) {
+  switch (nib) {
+    case 1: emit_nibble<1, K0>(Sv, dbits, kp, lane); break;
+    case 2: emit_nibble<2, K0>(Sv, dbits, kp, lane); break;
+    case 3: emit_nibble<3, K0>(Sv, dbits, kp, lane); break;
+    case 4: emit_nibble<4, K0>(Sv, dbits, kp, lane); break;
+    case 5: emit_nibble<5, K0>(Sv, dbits, kp, lane); break;
+    case 6: emit_nibble<6, K0>(Sv, dbits, kp, lane); break;
+    case 7: emit_nibble<7, K0>(Sv, dbits, kp, lane); break;
+    case 8: emit_nibble<8, K0>(Sv, dbits, kp, lane); break;
+    case 9: emit_nibble<9, K0>(Sv, dbits, kp, lane); break;
+    case 10: emit_nibble<10, K0>(Sv, dbits, kp, lane); break;
+    case 11: emit_nibble<11, K0>(Sv, dbits, kp, lane); break;
+    case 12: emit_nibble<12, K0>(Sv, dbits, kp, lane); break;
+    case 13: emit_nibble<13, K0>(Sv, dbits, kp, lane); break;
+    case 14: emit_nibble<14, K0>(Sv, dbits, kp, lane); break;
+    case 15: emit_nibble<15, K0>(Sv, dbits, kp, lane); break;
+    default: break;
+  }
+}
+}  // namespace
 
 // Persistent: each CTA takes the next work item from the queue counter (zero
 // before the launch) until the list is exhausted; items come in the order of
@@ -235,11 +282,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
             const int xl = x0 + xi;
             return xi < xb && xl >= xo0 && xl <= xo1 && (xl == xo0 || xl == xo1 || bm[xi]);
           };
-          auto emit = [&](uint32_t S, int xi) {
-            const uint32_t key = dbits == 0xFFFFFFFFu ? 0xFFFFFFFFu : ((S << SB_KEY_DBITS) | dbits);
-            const uint32_t kmin = __reduce_min_sync(0xffffffffu, key);
-            if (lane == 0) atomicMin(&krow[xi], kmin);
-          };
           // S starts as the window of output xa - 1 (column xa - 1 + j, shifted by
           // the zero column: slot column xa + j), then every output adds its
           // entering column and drops its leaving one; HW is a multiple of 8.
@@ -259,16 +301,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
                 Sv[k] = S;
               }
               const unsigned bits = (mask >> i) & 0xFFu;
-              if (bits & 0x0Fu) {
-  #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                  if (bits & (1u << k)) emit(Sv[k], xbase + i + k);
-              }
-              if (bits & 0xF0u) {
-  #pragma unroll
-                for (int k = 4; k < 8; ++k)
-                  if (bits & (1u << k)) emit(Sv[k], xbase + i + k);
-              }
+              emit_block_half<0>(bits & 15u, Sv, dbits, krow + xbase + i, lane);
+              emit_block_half<4>(bits >> 4, Sv, dbits, krow + xbase + i, lane);
             }
           }
         }
