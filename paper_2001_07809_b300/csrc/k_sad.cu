@@ -278,17 +278,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
           constexpr int CS = kVsStride / 2;                              // u16 per column
           const uint8_t* bm = s_bm + (buf * kGroup + g) * kBBytes + (int)(((int64_t)y * w + x0) & 15);
           uint32_t* krow = J.key + (int64_t)y * w + x0;
-          auto anchor = [&](int xi) -> bool {  // strip-relative output column
+          // anchor test of strip-relative output column xi, given its map byte
+          auto anchor = [&](int xi, uint8_t b) -> bool {
             const int xl = x0 + xi;
-            return xi < xb && xl >= xo0 && xl <= xo1 && (xl == xo0 || xl == xo1 || bm[xi]);
+            return xi < xb && xl >= xo0 && xl <= xo1 && (xl == xo0 || xl == xo1 || b);
           };
           // S starts as the window of output xa - 1 (column xa - 1 + j, shifted by
           // the zero column: slot column xa + j), then every output adds its
           // entering column and drops its leaving one; HW is a multiple of 8.
           uint32_t S = 0;
           for (int j = 0; j <= 2 * r; ++j) S += vcol[(xa + j) * CS];
+          // the map bytes of the next 32 outputs are read one chunk ahead
+          uint8_t bcur = xa + lane < xb ? bm[xa + lane] : (uint8_t)0;
           for (int xbase = xa; xbase < xb; xbase += 32) {
-            const unsigned mask = __ballot_sync(0xffffffffu, anchor(xbase + lane));
+            const uint8_t bnext = xbase + 32 + lane < xb ? bm[xbase + 32 + lane] : (uint8_t)0;
+            const unsigned mask = __ballot_sync(0xffffffffu, anchor(xbase + lane, bcur));
             const int n = min(32, xb - xbase);
             const uint16_t* pin = vcol + (xbase + 2 * r + 1) * CS;  // slot column of strip column x + 2r
             const uint16_t* pout = vcol + xbase * CS;             // slot column of x - 1
@@ -304,6 +308,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
               emit_block_half<0>(bits & 15u, Sv, dbits, krow + xbase + i, lane);
               emit_block_half<4>(bits >> 4, Sv, dbits, krow + xbase + i, lane);
             }
+            bcur = bnext;
           }
         }
       }
