@@ -173,7 +173,8 @@ sb_status sb_boundary_sad(sb_context* ctx, const uint8_t* L_left, const uint8_t*
  * peek_mode SB_PEEK_SNAPSHOT or SB_PEEK_INPLACE selects the reading of
  * "nearest determined pixel above" (see the enum).
  * Out: every pixel set; pixels outside Omega are 0.
- * filled: NULL or uint16 h*w out, the map after Algorithm 1 only. */
+ * filled: NULL or uint16 h*w out, the map after Algorithm 1 only; a buffer
+ * of its own (SB_ERR_INVALID_ARG when it overlaps disp). */
 sb_status sb_reconstruct_disparity(sb_context* ctx, uint16_t* disp, int32_t w, int32_t h, int32_t max_disp,
                                    int32_t block, int32_t disp_threshold, int32_t peek_mode, uint16_t* filled);
 

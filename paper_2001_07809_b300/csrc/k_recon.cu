@@ -3,9 +3,10 @@
 // Algorithm 1 ("Fill"): in each row, every pixel between two consecutive
 // anchors of equal disparity takes that disparity.  Equivalently, a
 // non-anchor pixel is filled exactly when the nearest anchor on its left and
-// the nearest on its right agree.  One warp per row: a left-to-right pass
-// carries the last anchor's disparity through 32-pixel chunks (ballot +
-// shuffle), a right-to-left pass does the same for the next anchor.
+// the nearest on its right agree.  One warp per row, four pixels per lane: a
+// left-to-right pass carries the last anchor's disparity through 128-pixel
+// chunks (ballot + shuffle between lanes, a scan inside each lane), a
+// right-to-left pass does the same for the next anchor.
 //
 // Algorithm 2 ("Peek"): each pixel still undetermined after Algorithm 1
 // takes, from the nearest determined pixels above and below in its column
@@ -41,46 +42,96 @@ __global__ void __launch_bounds__(256) k_recon_fill(const ReconJob* __restrict__
   const int lane = threadIdx.x & 31, w = J.w;
   const uint16_t* srow = J.sparse + (int64_t)y * w;
   const uint32_t* krow = J.keys ? J.keys + (int64_t)y * w : nullptr;
+  uint16_t* dst = J.filled + (int64_t)y * w;
+  // a lane owns four consecutive pixels of each 128-pixel chunk; whole rows
+  // are read and written four elements at a time when they are aligned
+  const bool vec = (w & 3) == 0 && ((reinterpret_cast<uintptr_t>(J.filled) & 7) == 0) &&
+                   (krow ? (reinterpret_cast<uintptr_t>(J.keys) & 15) == 0 : (reinterpret_cast<uintptr_t>(J.sparse) & 7) == 0);
   // the anchor's disparity at x, or NONE: from the SAD output, or decoded from
   // the argmin keys (no real key is all ones: costs stay below 2^22)
-  auto src = [&](int x) -> uint16_t {
-    if (!krow) return srow[x];
-    const uint32_t k = krow[x];
+  auto decode = [](uint32_t k) -> uint16_t {
     return k == 0xFFFFFFFFu ? NONE : (uint16_t)(k & ((1u << SB_KEY_DBITS) - 1u));
   };
-  uint16_t* dst = J.filled + (int64_t)y * w;
-  // pass 1: disparity of the nearest anchor strictly to the left (NONE if none)
+  auto load4 = [&](int x, uint16_t (&v)[4]) {
+    if (vec && x + 3 < w) {
+      if (krow) {
+        const uint4 k = *reinterpret_cast<const uint4*>(krow + x);
+        v[0] = decode(k.x); v[1] = decode(k.y); v[2] = decode(k.z); v[3] = decode(k.w);
+      } else {
+        const uint2 q = *reinterpret_cast<const uint2*>(srow + x);
+        v[0] = (uint16_t)q.x; v[1] = (uint16_t)(q.x >> 16); v[2] = (uint16_t)q.y; v[3] = (uint16_t)(q.y >> 16);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = x + j < w ? (krow ? decode(krow[x + j]) : srow[x + j]) : NONE;
+    }
+  };
+  auto store4 = [&](int x, const uint16_t (&o)[4]) {
+    if (vec && x + 3 < w) {
+      *reinterpret_cast<uint2*>(dst + x) = make_uint2((uint32_t)o[0] | ((uint32_t)o[1] << 16),
+                                                      (uint32_t)o[2] | ((uint32_t)o[3] << 16));
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (x + j < w) dst[x + j] = o[j];
+    }
+  };
+  const int nchunks = (w + 127) / 128;
+  // pass 1: disparity of the nearest anchor strictly to the left (NONE if
+  // none); anchors are marked with bit 15 (values stay <= 1023, and NONE =
+  // 0xffff has bits 10..14 set), so the second pass needs only this row
   uint16_t carry = NONE;
-  for (int x0 = 0; x0 < w; x0 += 32) {
-    const int x = x0 + lane;
-    const uint16_t v = x < w ? src(x) : NONE;
-    const bool anc = v != NONE;
-    const unsigned mask = __ballot_sync(0xffffffffu, anc);
+  for (int ci = 0; ci < nchunks; ++ci) {
+    const int x = ci * 128 + 4 * lane;
+    uint16_t v[4], o[4];
+    load4(x, v);
+    uint16_t last = NONE;   // the lane's rightmost anchor
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (v[j] != NONE) last = v[j];
+    const unsigned mask = __ballot_sync(0xffffffffu, last != NONE);
     const unsigned below = mask & ((1u << lane) - 1u);
-    const int src_lane = below ? 31 - __clz(below) : 0;
-    const uint16_t left = __shfl_sync(0xffffffffu, v, src_lane);
-    const uint16_t pd = below ? left : carry;
-    // anchors are marked with bit 15 (values stay <= 1023, and NONE = 0xffff
-    // has bits 10..14 set), so the second pass needs only this row
-    if (x < w) dst[x] = anc ? (uint16_t)(v | kAnchorBit) : pd;
-    if (mask) carry = __shfl_sync(0xffffffffu, v, 31 - __clz(mask));
+    const uint16_t from = __shfl_sync(0xffffffffu, last, below ? 31 - __clz(below) : 0);
+    uint16_t cur = below ? from : carry;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool anc = v[j] != NONE;
+      o[j] = anc ? (uint16_t)(v[j] | kAnchorBit) : cur;
+      if (anc) cur = v[j];
+    }
+    store4(x, o);
+    if (mask) carry = __shfl_sync(0xffffffffu, last, 31 - __clz(mask));
   }
   __syncwarp();
   // pass 2: nearest anchor strictly to the right; fill when both sides agree
   carry = NONE;
-  const int nchunks = (w + 31) / 32;
   for (int ci = nchunks - 1; ci >= 0; --ci) {
-    const int x = ci * 32 + lane;
-    const uint16_t t = x < w ? dst[x] : NONE;
-    const bool anc = t != NONE && (t & kAnchorBit);
-    const uint16_t v = anc ? (uint16_t)(t & ~kAnchorBit) : t;   // the anchor's value, or the left carry
-    const unsigned mask = __ballot_sync(0xffffffffu, anc);
+    const int x = ci * 128 + 4 * lane;
+    uint16_t t[4], o[4];
+    if (vec && x + 3 < w) {
+      const uint2 q = *reinterpret_cast<const uint2*>(dst + x);
+      t[0] = (uint16_t)q.x; t[1] = (uint16_t)(q.x >> 16); t[2] = (uint16_t)q.y; t[3] = (uint16_t)(q.y >> 16);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) t[j] = x + j < w ? dst[x + j] : NONE;
+    }
+    uint16_t first = NONE;   // the lane's leftmost anchor value
+#pragma unroll
+    for (int j = 3; j >= 0; --j)
+      if (t[j] != NONE && (t[j] & kAnchorBit)) first = (uint16_t)(t[j] & ~kAnchorBit);
+    const unsigned mask = __ballot_sync(0xffffffffu, first != NONE);
     const unsigned above = lane == 31 ? 0u : (mask & ~((2u << lane) - 1u));
-    const int src_lane = above ? __ffs(above) - 1 : 0;
-    const uint16_t right = __shfl_sync(0xffffffffu, v, src_lane);
-    const uint16_t nd = above ? right : carry;
-    if (x < w) dst[x] = anc ? v : ((v != NONE && v == nd) ? v : NONE);
-    if (mask) carry = __shfl_sync(0xffffffffu, v, __ffs(mask) - 1);
+    const uint16_t from = __shfl_sync(0xffffffffu, first, above ? __ffs(above) - 1 : 0);
+    uint16_t cur = above ? from : carry;
+#pragma unroll
+    for (int j = 3; j >= 0; --j) {
+      const bool anc = t[j] != NONE && (t[j] & kAnchorBit);
+      const uint16_t v = anc ? (uint16_t)(t[j] & ~kAnchorBit) : t[j];   // the anchor's value, or the left carry
+      o[j] = anc ? v : ((v != NONE && v == cur) ? v : NONE);
+      if (anc) cur = v;
+    }
+    store4(x, o);
+    if (mask) carry = __shfl_sync(0xffffffffu, first, __ffs(mask) - 1);
   }
 }
 
@@ -132,31 +183,52 @@ __global__ void __launch_bounds__(128) k_recon_peek_apply(const ReconJob* __rest
     if (v != NONE) { below = v; break; }
   }
   // upward sweep: remember the nearest determined value below each pixel
+  // (rows in blocks of 8 whose loads are issued together)
+  const uint16_t* __restrict__ fl = J.filled + x;
+  uint16_t* __restrict__ oc = J.out + (J.mirror ? w - 1 - x : x);
   uint16_t nb = below;
-  for (int y = yb; y >= ya; --y) {
-    const int64_t p = (int64_t)y * w + x;
-    const uint16_t v = J.filled[p];
+  int y = yb;
+  for (; y - 7 >= ya; y -= 8) {
+    uint16_t v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = fl[(int64_t)(y - k) * w];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (v[k] != NONE) nb = v[k];
+      oc[(int64_t)(y - k) * w] = v[k] != NONE ? v[k] : nb;
+    }
+  }
+  for (; y >= ya; --y) {
+    const uint16_t v = fl[(int64_t)y * w];
     if (v != NONE) nb = v;
-    out_at(J, y, x) = v != NONE ? v : nb;
+    oc[(int64_t)y * w] = v != NONE ? v : nb;
   }
   // downward sweep: combine with the nearest determined value above
   uint16_t na = above;
   const int T = J.threshold;
-  for (int y = ya; y <= yb; ++y) {
-    const int64_t p = (int64_t)y * w + x;
-    const uint16_t v = J.filled[p];
-    if (v != NONE) { na = v; continue; }
-    const uint16_t b = out_at(J, y, x);
-    uint16_t o;
-    if (na == NONE && b == NONE) o = 0;
-    else if (na == NONE) o = b;
-    else if (b == NONE) o = na;
-    else {
-      const int a = na, c = b;
-      const int range = a > c ? a - c : c - a;
-      o = (uint16_t)(range > T ? min(a, c) : (a + c) / 2);
+  auto combine = [T](uint16_t na_, uint16_t b) -> uint16_t {
+    if (na_ == NONE && b == NONE) return 0;
+    if (na_ == NONE) return b;
+    if (b == NONE) return na_;
+    const int a = na_, c = b;
+    const int range = a > c ? a - c : c - a;
+    return (uint16_t)(range > T ? min(a, c) : (a + c) / 2);
+  };
+  y = ya;
+  for (; y + 7 <= yb; y += 8) {
+    uint16_t v[8], b[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { v[k] = fl[(int64_t)(y + k) * w]; b[k] = oc[(int64_t)(y + k) * w]; }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (v[k] != NONE) { na = v[k]; continue; }
+      oc[(int64_t)(y + k) * w] = combine(na, b[k]);
     }
-    out_at(J, y, x) = o;
+  }
+  for (; y <= yb; ++y) {
+    const uint16_t v = fl[(int64_t)y * w];
+    if (v != NONE) { na = v; continue; }
+    oc[(int64_t)y * w] = combine(na, oc[(int64_t)y * w]);
   }
 }
 

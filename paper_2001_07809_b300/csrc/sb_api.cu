@@ -1054,6 +1054,8 @@ sb_status sb_reconstruct_disparity(sb_context* ctx, uint16_t* disp, int32_t w, i
   sb_status st = SB_OK;
   if (!geometry_ok(ctx, w, h, max_disp, block, &st)) return st;
   const size_t N = (size_t)w * h;
+  if (filled && (uintptr_t)filled < (uintptr_t)(disp + N) && (uintptr_t)disp < (uintptr_t)(filled + N))
+    return fail(ctx, SB_ERR_INVALID_ARG, "reconstruct_disparity: filled overlaps disp");
   const int nseg = (h + kSegRows - 1) / kSegRows;
   st = ensure_ws(ctx, al(N * 2) + al((size_t)nseg * w * 2) * 2);
   if (st != SB_OK) return st;

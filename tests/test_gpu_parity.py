@@ -535,6 +535,10 @@ def test_invalid_arguments_raise(ctx):
     ok = sb.make_params(max_disp=4, block=5, k=2)
     sb.sb_run(ctx, [sb.Pair(left, left, ok, out)])    # the context is still usable
     ctx.synchronize()
+    disp = torch.zeros((20, 30), dtype=torch.int16, device="cuda")
+    with pytest.raises(sb.SbError) as ei:            # Algorithm 1's map must not overlap the in-place one
+        sb.sb_reconstruct_disparity(ctx, disp, 4, 5, 1, disp[1:])
+    assert ei.value.status == 1
 
 
 def test_pipeline_large_disparity_range(ctx):
