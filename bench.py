@@ -49,10 +49,10 @@ BOX_OPS_PER_PXD = 6
 # tail disparity d=256 runs in its own kernel (timed in the "sad_rest" stage)
 BOX_DISPARITIES_C3 = 256
 # DRAM bytes of k_sad_boxsum per 4096x2304 pair (D=256, block 41, d = 0..255): the ncu
-# capture of one 8-pair launch read 456.51 MB and wrote 168.65 MB (L maps and boundary map
+# capture of one 8-pair launch read 457.10 MB and wrote 169.55 MB (L maps and boundary map
 # in, argmin keys out); a launch over P pairs moves P times that, since each pair's data is
 # its own
-SAD_DRAM_BYTES_PER_PAIR = (456.510208e6 + 168.654592e6) / 8
+SAD_DRAM_BYTES_PER_PAIR = (457.103360e6 + 169.545984e6) / 8
 METRIC = "stereo pairs/s at 4096x2304 (batched vs per-pair), SAD Gcell/s, p99 latency"
 # --sad-variant: the library's per-pair choice (box sums at this workload's density), or either
 # SAD kernel forced (the roofline then describes that kernel)
