@@ -347,6 +347,7 @@ __global__ void __launch_bounds__(256, 6) k_sad_tail(const SadJob* __restrict__ 
   uint32_t* s_v = reinterpret_cast<uint32_t*>(t_smem);            // [kTailRows][REM][256] column sums
   uint8_t* s_stage = t_smem + kTailRows * REM * 1024;              // 2 x {L rows, R rows, anchor rows}
   __shared__ int s_item;
+  __shared__ uint16_t s_ph[2][kTailSlots];   // per staged row: 16-byte phase of its L run | R run << 8
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (;;) {
     __syncthreads();
@@ -389,6 +390,7 @@ __global__ void __launch_bounds__(256, 6) k_sad_tail(const SadJob* __restrict__ 
         const int q = gi < nwarm ? i : (i < G ? i : kTailRows + i - G);
         const int row = gi < nwarm ? row0 + i : (i < G ? yg + i + r : yg + (i - G) - r);
         const int64_t rb = (int64_t)row * w;
+        if (lane == 0) s_ph[buf][q] = (uint16_t)(phase(row, cstart) | (phase(row, cr0) << 8));
         for (int ch = lane; ch < nchL; ch += 32)
           stage_chunk(B + q * kTailL, J.Ll, npx, (rb + cstart) & ~(int64_t)15, ch, fast);
         for (int ch = lane; ch < nchR; ch += 32)
@@ -403,16 +405,16 @@ __global__ void __launch_bounds__(256, 6) k_sad_tail(const SadJob* __restrict__ 
     uint32_t V[REM];
 #pragma unroll
     for (int k = 0; k < REM; ++k) V[k] = 0u;
-    // V_k += sign * |L - R| of image row `row`, staged in slot q
-    auto accumulate = [&](const uint8_t* B, int q, int row, bool add) {
-      const int lv = B[q * kTailL + phase(row, cstart) + tid];
-      const uint8_t* rp = B + kTailSlots * kTailL + q * kTailR + phase(row, cr0) + tid + kTailMax - 1;
+    // V_k += sign * |L - R| of the image row staged in slot q of buffer b
+    auto accumulate = [&](const uint8_t* B, int b, int q, bool add) {
+      const unsigned ph = s_ph[b][q];
+      const unsigned lv = B[q * kTailL + (ph & 15u) + tid];
+      const uint8_t* rp = B + kTailSlots * kTailL + q * kTailR + (ph >> 8) + tid + kTailMax - 1;
 #pragma unroll
       for (int k = 0; k < REM; ++k)
         if (k < rem) {
-          const int rv = rp[-k];
-          const uint32_t a = (uint32_t)(lv > rv ? lv - rv : rv - lv);
-          V[k] = add ? V[k] + a : V[k] - a;
+          const unsigned rv = rp[-k];
+          V[k] = add ? __usad(lv, rv, V[k]) : V[k] - __usad(lv, rv, 0u);
         }
     };
     issue(0, 0);
@@ -423,18 +425,18 @@ __global__ void __launch_bounds__(256, 6) k_sad_tail(const SadJob* __restrict__ 
       const uint8_t* B = s_stage + (gi & 1) * kTailBuf;
       if (gi < nwarm) {
         const int row0 = it.y0 - r + kTailSlots * gi, n = min(kTailSlots, it.y0 + r - row0);
-        for (int q = 0; q < n; ++q) accumulate(B, q, row0 + q, true);
+        for (int q = 0; q < n; ++q) accumulate(B, gi & 1, q, true);
         continue;
       }
       const int yg = it.y0 + kTailRows * (gi - nwarm), G = min(kTailRows, it.y1 - yg + 1);
 #pragma unroll
       for (int j = 0; j < kTailRows; ++j) {
         if (j < G) {
-          accumulate(B, j, yg + j + r, true);
+          accumulate(B, gi & 1, j, true);
 #pragma unroll
           for (int k = 0; k < REM; ++k)
             if (k < rem) s_v[(j * REM + k) * 256 + tid] = V[k];
-          accumulate(B, kTailRows + j, yg + j - r, false);
+          accumulate(B, gi & 1, kTailRows + j, false);
         }
       }
       __syncthreads();
