@@ -86,40 +86,44 @@ __global__ void __launch_bounds__(kBitThreads) k_boundary_bits(const MorphJob* _
     s_lab[i] = v;
   }
   __syncthreads();
-  // boundary bits on staged rows 1 .. R-2: an in-image 8-neighbour with another label
-  for (int t = tid; t < (R - 2) * NWD; t += kBitThreads) {
-    const int row = 1 + t / NWD, k = t - (row - 1) * NWD, y = ry0 + row;
-    uint32_t word = 0;
-    if (y >= 0 && y < h) {
+  // boundary bits on staged rows 1 .. R-2: an in-image 8-neighbour with another
+  // label.  A thread takes one 4-pixel group (consecutive threads read
+  // consecutive label words: no bank conflicts); the eight groups of a
+  // 32-column bit word sit in eight consecutive lanes and are OR-ed together
+  // with shuffles.  Every thread runs every round (the shuffles need all lanes).
+  for (int t0 = 0; t0 < (R - 2) * LW; t0 += kBitThreads) {
+    const int t = t0 + tid;
+    const bool live = t < (R - 2) * LW;
+    const int row = 1 + t / LW, idx = t - (row - 1) * LW, k = idx >> 3, q = idx & 7, y = ry0 + row;
+    uint32_t nib = 0;
+    if (live && y >= 0 && y < h) {
       const bool up = y - 1 >= 0, dn = y + 1 < h;
       const uint32_t* L0 = s_lab + row * LW;
-      auto lw = [&](const uint32_t* Lr, int idx) { return idx >= 0 && idx < LW ? Lr[idx] : 0u; };
+      auto lw = [&](const uint32_t* Lr, int i) { return i >= 0 && i < LW ? Lr[i] : 0u; };
       const int c0 = cx0 + 32 * k;
       const bool interior = c0 >= 1 && c0 + 32 < w;   // every pixel and both column neighbours inside
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int idx = 8 * k + q;
-        const uint32_t cur = L0[idx];
-        uint32_t acc = 0;
-        auto row_diff = [&](const uint32_t* Lr, bool centre) {
-          const uint32_t m = lw(Lr, idx), pv = lw(Lr, idx - 1), nx = lw(Lr, idx + 1);
-          const uint32_t lft = (m << 8) | (pv >> 24), rgt = (m >> 8) | (nx << 24);
-          uint32_t dl = __vcmpne4(cur, lft), dr = __vcmpne4(cur, rgt);
-          if (!interior) {
-            const int x4 = c0 + 4 * q;
-            dl &= col_mask(x4, 1, w + 1);    // x - 1 inside
-            dr &= col_mask(x4, -1, w - 1);   // x + 1 inside
-          }
-          return dl | dr | (centre ? 0u : __vcmpne4(cur, m));
-        };
-        acc |= row_diff(L0, true);
-        if (up) acc |= row_diff(L0 - LW, false);
-        if (dn) acc |= row_diff(L0 + LW, false);
-        if (!interior) acc &= col_mask(c0 + 4 * q, 0, w);
-        word |= byte_bits(acc) << (4 * q);
-      }
+      const uint32_t cur = L0[idx];
+      auto row_diff = [&](const uint32_t* Lr, bool centre) {
+        const uint32_t m = lw(Lr, idx), pv = lw(Lr, idx - 1), nx = lw(Lr, idx + 1);
+        const uint32_t lft = (m << 8) | (pv >> 24), rgt = (m >> 8) | (nx << 24);
+        uint32_t dl = __vcmpne4(cur, lft), dr = __vcmpne4(cur, rgt);
+        if (!interior) {
+          const int x4 = c0 + 4 * q;
+          dl &= col_mask(x4, 1, w + 1);    // x - 1 inside
+          dr &= col_mask(x4, -1, w - 1);   // x + 1 inside
+        }
+        return dl | dr | (centre ? 0u : __vcmpne4(cur, m));
+      };
+      uint32_t acc = row_diff(L0, true);
+      if (up) acc |= row_diff(L0 - LW, false);
+      if (dn) acc |= row_diff(L0 + LW, false);
+      if (!interior) acc &= col_mask(c0 + 4 * q, 0, w);
+      nib = byte_bits(acc) << (4 * q);
     }
-    s_p[row * NWD + k] = word;
+    nib |= __shfl_xor_sync(0xffffffffu, nib, 1);
+    nib |= __shfl_xor_sync(0xffffffffu, nib, 2);
+    nib |= __shfl_xor_sync(0xffffffffu, nib, 4);
+    if (live && q == 0) s_p[row * NWD + k] = nib;
   }
   __syncthreads();
   // word neighbours of bit rows: x - 1 and x + 1 (bits shifted in from the next words; 0 past the tile)
