@@ -313,6 +313,10 @@ constexpr int kSB = 32;              // output rows per step
 constexpr int kStripThreads = 384;   // = kSB x 3 channels x BX/OB (horizontal) = BX x 3 x kSB/OB (vertical)
 constexpr int kBandRows = 512;       // output rows per CTA
 constexpr int kMaxSteps = kBandRows / kSB;
+// channel c's ring starts at c * (M * HS + kChPad) floats: with the 4-float
+// pad, the horizontal pass's stores of the three channels and four column
+// segments a warp holds fall in different banks (2-way at most, 6-way without)
+constexpr int kChPad = 4;
 
 struct StripGeo {
   int nt, F, M, iw, sr, h_off, in_off, bytes;
@@ -328,7 +332,7 @@ __host__ __device__ inline StripGeo strip_geo(int R) {
   g.iw = BX + 2 * R + 1;
   g.sr = ((g.iw * 3 + 15 + 15) / 16) * 16;
   g.h_off = ((g.nt + 3) & ~3) * 4;                                   // taps first
-  g.in_off = (g.h_off + 3 * g.M * HS * 4 + 15) & ~15;                // then the ring, 3 channels (cp.async
+  g.in_off = (g.h_off + (3 * g.M * HS + 2 * kChPad) * 4 + 15) & ~15;  // then the ring, 3 channels (cp.async
                                                                      // destinations need 16-byte alignment)
   g.bytes = g.in_off + 2 * kSB * g.sr;                               // then two input buffers
   return g;
@@ -516,7 +520,7 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
       const uint8_t* in = base + i * sr + s_off[buf][i] + j0 * 3 + ch;   // output j0+o uses in[3(o .. o+2R)]
       float acc[OB];
       conv16(acc, s_tap, nt, [in](int j) { return u8f(in[j * 3]); });
-      float* dst = s_h + (ch * M + slot(a + i)) * HS + j0;
+      float* dst = s_h + ch * (M * HS + kChPad) + slot(a + i) * HS + j0;
 #pragma unroll
       for (int o = 0; o < OB; ++o) dst[o] = acc[o];
     }
@@ -537,7 +541,7 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
       const int i0 = blk * OB;
       const int b0 = slot(ys + i0 - R);
       float acc[OB];
-      conv16_ring(acc, s_tap, nt, s_h + ch * M * HS + col, b0, M);
+      conv16_ring(acc, s_tap, nt, s_h + ch * (M * HS + kChPad) + col, b0, M);
       if (col < ox) {
 #pragma unroll
         for (int o = 0; o < OB; ++o) {
