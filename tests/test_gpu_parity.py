@@ -200,6 +200,20 @@ def test_sad_extreme_costs(ctx):
         assert np.all(oc[anchor] == 63 * 63 * 255) and np.all(od[anchor] == 0)
 
 
+@pytest.mark.parametrize("h,w,D,B", [(60, 700, 40, 9), (50, 500, 71, 21)])
+def test_sad_every_anchor_pattern(ctx, h, w, D, B):
+    # every 8-bit anchor pattern, in every alignment to the box-sum's blocks of
+    # eight outputs: row y, columns 8j .. 8j+7 carry the bits of (y * 37 + j) mod 256
+    Ll = RNG.integers(0, 256, (h, w)).astype(np.uint8)
+    Lr = np.clip(np.roll(Ll, -3, axis=1).astype(int) + RNG.integers(-9, 10, (h, w)), 0, 255).astype(np.uint8)
+    ys, xs = np.mgrid[0:h, 0:w]
+    pattern = (ys * 37 + (xs + ys) // 8) % 256
+    bmap = ((pattern >> ((xs + ys) % 8)) & 1).astype(np.uint8)
+    disp, cost = sad(ctx, Ll, Lr, bmap, D, B, sb.SB_SAD_BOXSUM)
+    od, oc = oracle.boundary_sad(Ll, Lr, oracle.anchor_mask(bmap, D, B), D, B)
+    assert np.array_equal(disp, od) and np.array_equal(cost, oc)
+
+
 @pytest.mark.parametrize("density,B", [(0.0, 1), (0.0, 9), (0.01, 3), (0.03, 3), (0.5, 25), (0.2, 41)])
 def test_sad_auto_choice_is_exact(ctx, density, B):
     # the automatic choice is taken on the device from the map's own count;
