@@ -3,9 +3,11 @@
 //
 // Lightness: per pixel Y16 = (13933 lin[R] + 46871 lin[G] + 4732 lin[B] + 32768) >> 16
 // with lin[c] = round(65535 * sRGB^-1(c/255)), then L = round(2.55 L*(Y16/65535)).
-// The 65536-entry L table is held compressed in shared memory: coarse[Y>>4]
-// plus one threshold compare (L* rises by less than one level over 16
-// consecutive Y16 values, which the host checks when it builds the tables).
+// The 65536-entry L table is held compressed in shared memory: one 32-bit
+// entry per 16 consecutive Y16 values, the L of the first of them and the
+// Y16 at which L steps up by one (L* rises by less than one level over 16
+// consecutive Y16 values, which the host checks when it builds the table),
+// so a pixel takes one table read and one compare.
 // HBM-bound: 3 bytes in, 1 byte out per pixel, 16 pixels per thread step
 // with 16-byte loads and stores.
 #include "sb_common.cuh"
@@ -13,25 +15,21 @@
 namespace sb {
 
 __device__ __forceinline__ uint32_t lightness_px(uint32_t r, uint32_t g, uint32_t b, const uint16_t* s_lin,
-                                                 const uint8_t* s_coarse, const uint32_t* s_thr) {
-  uint32_t y = (13933u * s_lin[r] + 46871u * s_lin[g] + 4732u * s_lin[b] + 32768u) >> 16;
-  uint32_t l = s_coarse[y >> 4];
-  l += (y >= s_thr[l + 1]) ? 1u : 0u;
-  return l;
+                                                 const uint32_t* s_ct) {
+  const uint32_t y = (13933u * s_lin[r] + 46871u * s_lin[g] + 4732u * s_lin[b] + 32768u) >> 16;
+  const uint32_t e = s_ct[y >> 4];
+  return (e & 255u) + (y >= (e >> 8) ? 1u : 0u);
 }
 
 __global__ void __launch_bounds__(256) k_lightness(const LightJob* __restrict__ jobs, const uint16_t* __restrict__ lin,
-                                                   const uint8_t* __restrict__ coarse,
-                                                   const uint32_t* __restrict__ thr) {
+                                                   const uint32_t* __restrict__ ct) {
   __shared__ uint16_t s_lin[256];
-  __shared__ uint8_t s_coarse[4096];
-  __shared__ uint32_t s_thr[257];
+  __shared__ __align__(16) uint32_t s_ct[4096];
   __shared__ uint32_t s_hist[8][256];
   const LightJob J = jobs[blockIdx.y];
   const int tid = threadIdx.x, warp = tid >> 5;
   for (int i = tid; i < 256; i += 256) s_lin[i] = lin[i];
-  for (int i = tid; i < 4096 / 16; i += 256) reinterpret_cast<uint4*>(s_coarse)[i] = reinterpret_cast<const uint4*>(coarse)[i];
-  for (int i = tid; i < 257; i += 256) s_thr[i] = thr[i];
+  for (int i = tid; i < 4096 / 4; i += 256) reinterpret_cast<uint4*>(s_ct)[i] = reinterpret_cast<const uint4*>(ct)[i];
   for (int i = tid; i < 8 * 256; i += 256) (&s_hist[0][0])[i] = 0;
   __syncthreads();
 
@@ -55,7 +53,7 @@ __global__ void __launch_bounds__(256) k_lightness(const LightJob* __restrict__ 
         uint32_t rr = (w[byte0 >> 2] >> (8 * (byte0 & 3))) & 255u;
         uint32_t gg = (w[(byte0 + 1) >> 2] >> (8 * ((byte0 + 1) & 3))) & 255u;
         uint32_t bb = (w[(byte0 + 2) >> 2] >> (8 * ((byte0 + 2) & 3))) & 255u;
-        uint32_t l = lightness_px(rr, gg, bb, s_lin, s_coarse, s_thr);
+        uint32_t l = lightness_px(rr, gg, bb, s_lin, s_ct);
         if (want_hist) atomicAdd(&s_hist[warp][l], 1u);
         packed |= l << (8 * k);
       }
@@ -66,7 +64,7 @@ __global__ void __launch_bounds__(256) k_lightness(const LightJob* __restrict__ 
   // scalar tail (and the whole image when the pointers are not 16-byte aligned,
   // or when the rows are written mirrored)
   for (int64_t p = n16 * 16 + (int64_t)blockIdx.x * blockDim.x + tid; p < n; p += stride) {
-    uint32_t l = lightness_px(J.rgb[3 * p], J.rgb[3 * p + 1], J.rgb[3 * p + 2], s_lin, s_coarse, s_thr);
+    uint32_t l = lightness_px(J.rgb[3 * p], J.rgb[3 * p + 1], J.rgb[3 * p + 2], s_lin, s_ct);
     if (want_hist) atomicAdd(&s_hist[warp][l], 1u);
     int64_t q = p;
     if (J.mirror) {   // pixel x of row y goes to w-1-x
@@ -87,10 +85,10 @@ __global__ void __launch_bounds__(256) k_lightness(const LightJob* __restrict__ 
 }
 
 void launch_lightness(const LightJob* jobs, int n_jobs, int blocks_per_job, const uint16_t* lin,
-                      const uint8_t* coarse, const uint32_t* thr, cudaStream_t s) {
+                      const uint32_t* ct, cudaStream_t s) {
   if (n_jobs <= 0) return;
   dim3 grid(blocks_per_job, n_jobs);
-  k_lightness<<<grid, 256, 0, s>>>(jobs, lin, coarse, thr);
+  k_lightness<<<grid, 256, 0, s>>>(jobs, lin, ct);
 }
 
 __global__ void __launch_bounds__(256) k_labels(const LabelJob* __restrict__ jobs) {

@@ -168,7 +168,7 @@ struct sb_context {
   size_t budget = 0;
   std::string err;
   uint64_t launches = 0;
-  uint8_t* tables = nullptr;  // lin (512 B) | coarse (4096 B) | thr (257 x 4 B)
+  uint8_t* tables = nullptr;  // lin (512 B) | packed L table (4096 x 4 B)
   uint32_t* dev_err = nullptr;
   unsigned* sad_queue = nullptr;  // work-item cursors of the box-sum SAD and tail kernels
   uint8_t* ws = nullptr;
@@ -272,23 +272,25 @@ sb_status build_tables(sb_context* ctx) {
       if (lt[y] >= l) { t = (uint32_t)y; break; }
     thr[l] = t;
   }
+  // packed: entry i = coarse[i] | thr[coarse[i] + 1] << 8 (thresholds <= 65536 fit in 24 bits),
+  // so a pixel needs one lookup: L = (e & 255) + (Y16 >= e >> 8)
+  uint32_t ct[4096];
+  for (int i = 0; i < 4096; ++i) ct[i] = (uint32_t)coarse[i] | (thr[coarse[i] + 1] << 8);
   for (int y = 0; y < 65536; ++y) {  // the compressed form must reproduce the table
-    const int c = coarse[y >> 4];
-    const int v = c + ((uint32_t)y >= thr[c + 1] ? 1 : 0);
+    const uint32_t e = ct[y >> 4];
+    const int v = (int)(e & 255u) + ((uint32_t)y >= (e >> 8) ? 1 : 0);
     if (v != lt[y]) return fail(ctx, SB_ERR_UNSUPPORTED, "lightness table compression check failed at %d", y);
   }
-  uint8_t host[512 + 4096 + 257 * 4];
+  uint8_t host[512 + 4096 * 4];
   memcpy(host, lin, 512);
-  memcpy(host + 512, coarse, 4096);
-  memcpy(host + 512 + 4096, thr, 257 * 4);
+  memcpy(host + 512, ct, 4096 * 4);
   SB_CUDA(ctx, cudaMalloc(&ctx->tables, sizeof host));
   SB_CUDA(ctx, cudaMemcpy(ctx->tables, host, sizeof host, cudaMemcpyHostToDevice));
   return SB_OK;
 }
 
 const uint16_t* t_lin(sb_context* c) { return (const uint16_t*)c->tables; }
-const uint8_t* t_coarse(sb_context* c) { return c->tables + 512; }
-const uint32_t* t_thr(sb_context* c) { return (const uint32_t*)(c->tables + 512 + 4096); }
+const uint32_t* t_ct(sb_context* c) { return (const uint32_t*)(c->tables + 512); }
 
 sb_status ensure_ws(sb_context* ctx, size_t bytes) {
   if (bytes <= ctx->ws_bytes) return SB_OK;
@@ -581,7 +583,12 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
     SB_MEMSET(ctx, (r.ws.hist, 0, 256 * 4, s));
     SB_MEMSET(ctx, (r.ws.cut, 0, 8 * 8, s));
   }
-  const int bpj = (int)std::min<int64_t>(std::max<int64_t>(1, max_px / (256 * 16)), 592);
+  // CTAs per lightness job: one per 4096 pixels, but no more than 16 waves of the
+  // whole batch (8 CTAs per SM) in all: each CTA first copies 16.5 KB of tables into
+  // shared memory, which a large batch would otherwise repeat hundreds of thousands of times
+  const int64_t n_light = 2 * (int64_t)runs.size();
+  const int64_t light_cap = std::max<int64_t>(1, (16 * 8 * (int64_t)ctx->sms + n_light - 1) / n_light);
+  const int bpj = (int)std::min<int64_t>(std::min<int64_t>(std::max<int64_t>(1, max_px / (256 * 16)), 592), light_cap);
   SB_MARK(ctx, SB_STAGE_LIGHTNESS);
   // 1. lightness of both images (+ histogram of the left)
   {
@@ -596,7 +603,7 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
     const LightJob* d = upload(ctx, J, &st);
     if (!d) return st;
     if (!ctx->dry) {
-      launch_lightness(d, (int)J.size(), bpj, t_lin(ctx), t_coarse(ctx), t_thr(ctx), s);
+      launch_lightness(d, (int)J.size(), bpj, t_lin(ctx), t_ct(ctx), s);
       SB_LAUNCHED(ctx, 1);
     }
   }
@@ -904,7 +911,7 @@ sb_status sb_rgb_to_lightness(sb_context* ctx, const uint8_t* rgb, int32_t w, in
   const LightJob* d = upload(ctx, J, &st);
   if (!d) return st;
   const int bpj = (int)std::min<int64_t>(std::max<int64_t>(1, (int64_t)w * h / (256 * 16)), 592);
-  launch_lightness(d, 1, bpj, t_lin(ctx), t_coarse(ctx), t_thr(ctx), ctx->stream);
+  launch_lightness(d, 1, bpj, t_lin(ctx), t_ct(ctx), ctx->stream);
   SB_LAUNCHED(ctx, 1);
   return SB_OK;
 }

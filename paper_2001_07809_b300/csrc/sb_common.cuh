@@ -28,10 +28,11 @@ struct LightJob {
   int32_t w;           // row length (used when mirror is set)
   int32_t mirror;      // 1: write each row mirrored (pixel x of a row to w-1-x)
 };
-// lin: uint16[256] linear sRGB x 65535; coarse: uint8[4096] L of Y>>4; thr: uint32[257]
-// first Y with L >= l.  Both built on the host from FP64 libm.
+// lin: uint16[256] linear sRGB x 65535; ct: uint32[4096], entry i = L of Y = 16 i (low
+// byte) | the first Y with L above that (upper 24 bits).  Both built on the host from FP64
+// libm.
 void launch_lightness(const LightJob* jobs, int n_jobs, int blocks_per_job, const uint16_t* lin,
-                      const uint8_t* coarse, const uint32_t* thr, cudaStream_t s);
+                      const uint32_t* ct, cudaStream_t s);
 
 // ------------------------------------------------------------------ k-means
 struct KmeansJob {
