@@ -443,12 +443,18 @@ void launch_cca(const CcaJob* jobs, int n_jobs, int max_w, int max_h, uint32_t* 
 void launch_cc_filter(const CcaJob* jobs, int n_jobs, int max_w, int max_h, cudaStream_t s) {
   if (n_jobs <= 0) return;
   const int64_t n = (int64_t)max_w * max_h;
-  int bpj = (int)((n + 256 * 8 - 1) / (256 * 8));
-  if (bpj > 1184) bpj = 1184;
-  if (bpj < 1) bpj = 1;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // filter CTAs per job: one per 2048 pixels, at most 8 waves per SM, and no more
+  // than 16 waves of the whole batch in all (a large batch needs few per job)
+  int64_t bpj64 = std::min<int64_t>((n + 256 * 8 - 1) / (256 * 8), 8 * (int64_t)sms);
+  bpj64 = std::min<int64_t>(bpj64, (16 * 8 * (int64_t)sms + n_jobs - 1) / n_jobs);
+  const int bpj = (int)std::max<int64_t>(1, bpj64);
   const int tiles_x = (max_w + CT - 1) / CT;
   k_cc_count<<<dim3((tiles_x + kCountTiles - 1) / kCountTiles, (max_h + CT - 1) / CT, n_jobs), 256, 0, s>>>(jobs);
-  const int rpj = std::max(1, std::min(bpj, 148));   // root-list passes: roots are few
+  // root-list passes: roots are few; four waves of the batch in all
+  const int rpj = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(bpj, sms), (4 * 8 * (int64_t)sms + n_jobs - 1) / n_jobs));
   k_cc_hist<<<dim3(rpj, n_jobs), 256, 0, s>>>(jobs);
   k_cc_cut<<<n_jobs, 1024, 0, s>>>(jobs);
   k_cc_rowcount<<<dim3(rpj, n_jobs), 256, 0, s>>>(jobs);
