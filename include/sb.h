@@ -229,13 +229,21 @@ sb_status sb_run(sb_context* ctx, const sb_pair* pairs, int32_t n_pairs, uint32_
  * queues its work on cuda_stream (a cudaStream_t, NULL = legacy default
  * stream) and allocates nothing.  Its scratch (one 32-bit key per pixel plus
  * the launch descriptors, about 16.25 MB) is a static device array that
- * every GPU loading the library holds until the process exits; images above
- * SB_STATIC_MAX_PIXELS pixels are rejected with SB_ERR_INVALID_ARG.  The
- * first call on a device looks up the array's device address (make it before
- * any stream capture).  All calls share the array: calls that overlap on the
- * GPU (other streams, other threads) race and must be ordered by the caller.
+ * every GPU loading the library's device code holds until the process exits.
+ * CUDA loads that code lazily: the first call on a device (and the first in
+ * any other CUDA context) loads it, reserves the array and looks up its
+ * address, which can allocate and synchronise, so make one warm-up call
+ * before a real-time loop and before any stream capture.  Images above
+ * SB_STATIC_MAX_PIXELS pixels are rejected with SB_ERR_INVALID_ARG; a call
+ * needing more than SB_STATIC_MAX_ITEMS work items (strips of about 200
+ * columns times chunks of 64 disparities, times row bands for small images)
+ * is rejected with SB_ERR_UNSUPPORTED: a 4096 x 1024 image with block 41
+ * and max_disp 1023 needs about 1,000 on a 148-SM GPU, a 1048576 x 4 image
+ * with block 3 and max_disp 1023 would need 74,832.  All calls share the array: calls that overlap on the GPU (other
+ * streams, other threads) race and must be ordered by the caller.
  * errbuf: NULL or errbuf_len bytes that receive a message on failure. */
 #define SB_STATIC_MAX_PIXELS 4194304
+#define SB_STATIC_MAX_ITEMS 13094
 sb_status sb_boundary_sad_static(const uint8_t* L_left, const uint8_t* L_right, const uint8_t* boundary, int32_t w,
                                  int32_t h, int32_t max_disp, int32_t block, int32_t variant, uint16_t* disp,
                                  uint32_t* cost, void* cuda_stream, char* errbuf, size_t errbuf_len);

@@ -36,13 +36,15 @@ namespace sb {
 
 namespace {
 constexpr int kThreads = 256;
-constexpr int kGroup = 4;                       // output rows per Stage A -> Stage B hand-off
-constexpr int kVsCols = 248;                    // column slots per row: a zero column, then TX + 2r columns
-constexpr int kVsStride = 80;                   // bytes per column of 32 u16 sums (+16: conflict-free STS.128)
+constexpr int kG = 2;                           // output rows per Stage A -> Stage B hand-off
+constexpr int kSegs = 4;                        // Stage B segments per row: warp = (row of the group, segment)
+constexpr int kMaxCols = 248;                   // column slots per row: a zero column, then TX + 2r columns
+constexpr int kColBytes = 144;                  // bytes per column: 64 u16 sums + 16 (conflict-free STS.128)
 constexpr int kLBytes = 272;                    // staged L bytes per row (240 + 16-byte alignment slack)
-constexpr int kRBytes = 320;                    // staged R bytes per row (240 + 31 + slack + look-ahead)
-constexpr int kRowBytes = kLBytes + kRBytes;    // 592, a multiple of 16
+constexpr int kRBytes = 352;                    // staged R bytes per row (TX + 2r + 63 + look-ahead + slack)
+constexpr int kRowBytes = kLBytes + kRBytes;    // 624, a multiple of 16
 constexpr int kBBytes = 272;                    // staged boundary-map bytes per output row
+static_assert(kSadChunk == 64, "the box-sum kernel covers 64 disparities per item");
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
@@ -73,21 +75,33 @@ __device__ __forceinline__ void stage_chunk(uint8_t* dst, const uint8_t* img, in
 }
 }  // namespace
 
-__host__ __device__ int sad_boxsum_strip(int r) { return (kVsCols - 1 - 2 * r) & ~15; }
+__host__ __device__ int sad_boxsum_strip(int r) { return (kMaxCols - 1 - 2 * r) & ~31; }
+__host__ __device__ static inline int box_vcols(int r) { return sad_boxsum_strip(r) + 2 * r + 1; }
 
 namespace {
 // Anchor emission for four consecutive outputs K0 .. K0+3 of a block whose
-// anchor bits are the compile-time nibble NIB: the warp minimum of
-// (S << 10 | d) over the 32 disparities of each anchor first, then lane 0's
-// atomic minima into the argmin keys, so that the latencies of the
-// reductions overlap instead of each atomic waiting for its own.  Lanes past
-// D carry dbits = all ones, which makes their key all ones (never the minimum).
+// anchor bits are the compile-time nibble NIB.  Lane p holds the packed
+// running sums of its disparity pair (dlo, dhi) after output K: T = Slo +
+// 65536 Shi + n * 0x40004000 (mod 2^32) and H = Shi + n * 0x4000, n = K + 1
+// steps after the warm-up (n0 + K + 1), so Shi = H - n * 0x4000 and
+// Slo = T - (Shi << 16) - n * 0x40004000.  The lane's two keys
+// (S << 10 | d) are reduced in the lane, then over the warp (redux.sync) for
+// every anchor of the nibble first, then lane 0 keeps the minima with
+// atomicMin, so that the reductions' latencies overlap.  Disparities past D
+// carry all-ones low bits, which makes their key all ones (never the minimum).
 template <unsigned NIB, int K0>
-__device__ __forceinline__ void emit_nibble(const uint32_t (&Sv)[8], uint32_t dbits, uint32_t* kp, int lane) {
+__device__ __forceinline__ void emit_nibble(const uint32_t (&Tv)[8], const uint32_t (&Hv)[8], uint32_t n0,
+                                            uint32_t dlo, uint32_t dhi, uint32_t* kp, int lane) {
   uint32_t m[4];
 #pragma unroll
   for (int b = 0; b < 4; ++b)
-    if (NIB & (1u << b)) m[b] = __reduce_min_sync(0xffffffffu, (Sv[K0 + b] << SB_KEY_DBITS) | dbits);
+    if (NIB & (1u << b)) {
+      const uint32_t n = n0 + K0 + b + 1;
+      const uint32_t shi = Hv[K0 + b] - n * 0x4000u;
+      const uint32_t slo = Tv[K0 + b] - (shi << 16) - n * 0x40004000u;
+      const uint32_t k = min((slo << SB_KEY_DBITS) | dlo, (shi << SB_KEY_DBITS) | dhi);
+      m[b] = __reduce_min_sync(0xffffffffu, k);
+    }
   if (lane == 0) {
 #pragma unroll
     for (int b = 0; b < 4; ++b)
@@ -98,32 +112,51 @@ __device__ __forceinline__ void emit_nibble(const uint32_t (&Sv)[8], uint32_t db
 // one case per non-empty nibble value: the bits are warp-uniform, so the
 // switch is a uniform jump and every case's code is straight-line
 template <int K0>
-__device__ __forceinline__ void emit_block_half(unsigned nib, const uint32_t (&Sv)[8], uint32_t dbits, uint32_t* kp,
-                                                int lane) {
+__device__ __forceinline__ void emit_block_half(unsigned nib, const uint32_t (&Tv)[8], const uint32_t (&Hv)[8],
+                                                uint32_t n0, uint32_t dlo, uint32_t dhi, uint32_t* kp, int lane) {
   switch (nib) {
-    case 1: emit_nibble<1, K0>(Sv, dbits, kp, lane); break;
-    case 2: emit_nibble<2, K0>(Sv, dbits, kp, lane); break;
-    case 3: emit_nibble<3, K0>(Sv, dbits, kp, lane); break;
-    case 4: emit_nibble<4, K0>(Sv, dbits, kp, lane); break;
-    case 5: emit_nibble<5, K0>(Sv, dbits, kp, lane); break;
-    case 6: emit_nibble<6, K0>(Sv, dbits, kp, lane); break;
-    case 7: emit_nibble<7, K0>(Sv, dbits, kp, lane); break;
-    case 8: emit_nibble<8, K0>(Sv, dbits, kp, lane); break;
-    case 9: emit_nibble<9, K0>(Sv, dbits, kp, lane); break;
-    case 10: emit_nibble<10, K0>(Sv, dbits, kp, lane); break;
-    case 11: emit_nibble<11, K0>(Sv, dbits, kp, lane); break;
-    case 12: emit_nibble<12, K0>(Sv, dbits, kp, lane); break;
-    case 13: emit_nibble<13, K0>(Sv, dbits, kp, lane); break;
-    case 14: emit_nibble<14, K0>(Sv, dbits, kp, lane); break;
-    case 15: emit_nibble<15, K0>(Sv, dbits, kp, lane); break;
+#define SB_EMIT_CASE(v) \
+  case v: emit_nibble<v, K0>(Tv, Hv, n0, dlo, dhi, kp, lane); break;
+    SB_EMIT_CASE(1) SB_EMIT_CASE(2) SB_EMIT_CASE(3) SB_EMIT_CASE(4) SB_EMIT_CASE(5)
+    SB_EMIT_CASE(6) SB_EMIT_CASE(7) SB_EMIT_CASE(8) SB_EMIT_CASE(9) SB_EMIT_CASE(10)
+    SB_EMIT_CASE(11) SB_EMIT_CASE(12) SB_EMIT_CASE(13) SB_EMIT_CASE(14) SB_EMIT_CASE(15)
+#undef SB_EMIT_CASE
     default: break;
+  }
+}
+
+// Vertical step of one row for strip column tid: the entering row (L byte at
+// rin[li], R words from Ri at bit shift shi) is added and the leaving row (rout,
+// lo, Ro, sho) subtracted in the 32 packed u16 pairs.  Byte b of the realigned
+// R word g is disparity d0 + 63 - 4g - b; Ve[g] holds its even bytes (b = 0, 2),
+// Vo[g] its odd bytes (b = 1, 3), as u16 lanes: the sums stay in [0, 63 * 255],
+// so no carry or borrow crosses a lane.
+__device__ __forceinline__ void vertical_row(uint32_t (&Ve)[16], uint32_t (&Vo)[16], const uint8_t* rin, int li,
+                                             const uint32_t* Ri, int shi, const uint8_t* rout, int lo,
+                                             const uint32_t* Ro, int sho) {
+  const uint32_t Lin = (uint32_t)rin[li] * 0x01010101u;
+  const uint32_t Lout = (uint32_t)rout[lo] * 0x01010101u;
+  uint32_t wi = Ri[0], wo = Ro[0];
+#pragma unroll
+  for (int g = 0; g < 16; ++g) {
+    const uint32_t wi2 = Ri[g + 1], wo2 = Ro[g + 1];
+    const uint32_t ri = __funnelshift_r(wi, wi2, shi), ro = __funnelshift_r(wo, wo2, sho);
+    wi = wi2;
+    wo = wo2;
+    const uint32_t ai = __vabsdiffu4(Lin, ri), ao = __vabsdiffu4(Lout, ro);
+    Ve[g] = Ve[g] + (ai & 0x00FF00FFu) - (ao & 0x00FF00FFu);
+    Vo[g] = Vo[g] + __byte_perm(ai, 0u, 0x4341) - __byte_perm(ao, 0u, 0x4341);
   }
 }
 }  // namespace
 
 // Persistent: each CTA takes the next work item from the queue counter (zero
 // before the launch) until the list is exhausted; items come in the order of
-// the list, which the host sorts largest first.
+// the list, which the host sorts largest first.  W16: every job's width is a
+// multiple of 16, so the 16-byte phase of a strip column is the same in every
+// row and the vertical pass of the rows past the warm-up uses the item's
+// constant offsets.
+template <bool W16>
 __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __restrict__ jobs,
                                                             const SadItem* __restrict__ items, int n_items,
                                                             unsigned* __restrict__ queue) {
@@ -139,35 +172,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
     if (sad_use_direct(J)) continue;                        // the direct kernel serves this pair
     const int r = J.r, D = J.D, w = J.w;
     const int64_t npx = (int64_t)w * J.h;
-    const int ring = 2 * r + 1 + 2 * kGroup;                // + one group staged ahead
+    const int ring = 2 * r + 1 + 2 * kG;                    // + one group staged ahead
+    const int VC = box_vcols(r);
     uint8_t* s_ring = smem;                                 // ring rows: [L | R]
     uint8_t* s_zero = s_ring + ring * kRowBytes;            // zero row (warm-up leaving rows)
-    uint8_t* s_bm = s_zero + kRowBytes;                     // 2 x kGroup boundary-map rows
-    uint8_t* s_vs = s_bm + 2 * kGroup * kBBytes;            // kGroup x kVsCols x kVsStride
+    uint8_t* s_bm = s_zero + kRowBytes;                     // 2 x kG boundary-map rows
+    uint8_t* s_vs = s_bm + 2 * kG * kBBytes;                // kG x VC x kColBytes
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int TX = sad_boxsum_strip(r);
     const int NC = TX + 2 * r;
     const int x0 = it.x0, d0 = it.d0;
     const int xo0 = D + r, xo1 = w - 1 - r;                 // Omega columns
     const int cstart = x0 - r;                              // strip column 0
-    const int rstart = cstart - d0 - 31;                    // first R byte any thread needs
+    const int rstart = cstart - d0 - (kSadChunk - 1);       // first R byte any thread needs
     const int y_first = it.y0, y_last = it.y1;              // output rows of the band
     const bool fast = (((uintptr_t)J.Ll | (uintptr_t)J.Lr | (uintptr_t)J.bmap) & 15) == 0;
-    const int nchL = (15 + NC + 15) / 16, nchR = (15 + NC + 31 + 4 + 15) / 16, nchB = (15 + TX + 15) / 16;
+    const int nchL = (15 + NC + 15) / 16, nchR = (15 + NC + kSadChunk - 1 + 4 + 15) / 16, nchB = (15 + TX + 15) / 16;
 
     for (int i = tid; i < kRowBytes / 4; i += kThreads) reinterpret_cast<uint32_t*>(s_zero)[i] = 0u;
-    for (int i = tid; i < kGroup * (kVsStride / 4); i += kThreads)   // column 0 of every row slot is zero
-      reinterpret_cast<uint32_t*>(s_vs + (i / (kVsStride / 4)) * kVsCols * kVsStride)[i % (kVsStride / 4)] = 0u;
+    for (int i = tid; i < kG * (kColBytes / 4); i += kThreads)   // column 0 of every row slot is zero
+      reinterpret_cast<uint32_t*>(s_vs + (i / (kColBytes / 4)) * VC * kColBytes)[i % (kColBytes / 4)] = 0u;
 
     // stage the entering rows of the group starting at virtual output row yg, and
     // the boundary-map rows of its real output rows, into buffer `buf`; thread
-    // tid copies chunk (tid & 63) of ring row (tid >> 6) and chunk (tid & 15) of
-    // boundary row (tid >> 4): at most 35 chunks per ring row, 16 per map row
+    // tid copies chunk (tid & 127) of ring row (tid >> 7) and chunk (tid & 31) of
+    // boundary row (tid >> 5): at most 17 + 21 chunks per ring row, 16 per map row
     const int per = nchL + nchR;
     auto stage = [&](int yg, int slot_first, int buf) {
-      const int ng = min(kGroup, y_last - yg + 1);
+      const int ng = min(kG, y_last - yg + 1);
       {
-        const int k = tid >> 6, ch = tid & 63;
+        const int k = tid >> 7, ch = tid & 127;
         if (k < ng && ch < per) {
           const int yin = yg + k + r;
           const int sl = slot_first + k < ring ? slot_first + k : slot_first + k - ring;
@@ -178,135 +212,172 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
         }
       }
       {
-        const int k = tid >> 4, ch = tid & 15;
+        const int k = tid >> 5, ch = tid & 31;
         const int y = yg + k;
         if (k < ng && ch < nchB && y >= y_first)
-          stage_chunk(s_bm + (buf * kGroup + k) * kBBytes, J.bmap, npx, ((int64_t)y * w + x0) & ~(int64_t)15, ch, fast);
+          stage_chunk(s_bm + (buf * kG + k) * kBBytes, J.bmap, npx, ((int64_t)y * w + x0) & ~(int64_t)15, ch, fast);
       }
       cp_async_commit();
     };
 
-    // Stage A state: 32 vertical window sums as 16 packed u16 pairs.  For word g,
-    // Ve[g] holds disparities (d0+31-4g | d0+29-4g) and Vo[g] (d0+30-4g | d0+28-4g).
-    uint32_t Ve[8], Vo[8];
-  #pragma unroll
-    for (int g = 0; g < 8; ++g) Ve[g] = Vo[g] = 0u;
+    // Stage A state: 64 vertical window sums as 32 packed u16 pairs
+    uint32_t Ve[16], Vo[16];
+#pragma unroll
+    for (int g = 0; g < 16; ++g) Ve[g] = Vo[g] = 0u;
 
-    // Stage B: where lane (disparity d0 + lane) finds its u16 in a column
-    int lanepos;
+    // Stage B: lane p reads word p of a column slot.  Words 4m .. 4m+3 hold
+    // Ve[2m], Vo[2m], Ve[2m+1], Vo[2m+1], so lane p = 4m + q carries the pair
+    // dlo = d0 + 63 - 4g' - (q & 1), dhi = dlo - 2 with g' = 2m + (q >> 1)
+    uint32_t dlo, dhi;
     {
-      const int u = 31 - lane, g = u >> 2, b = u & 3;
-      lanepos = 4 * g + 2 * (b & 1) + (b >> 1);
+      const int m = lane >> 2, q = lane & 3, gp = 2 * m + (q >> 1);
+      const int lo = d0 + kSadChunk - 1 - 4 * gp - (q & 1), hi = lo - 2;
+      dlo = lo <= D ? (uint32_t)lo : 0xFFFFFFFFu;
+      dhi = hi <= D ? (uint32_t)hi : 0xFFFFFFFFu;
     }
 
     // ring slot and 16-byte alignment offsets of the first entering row of the
     // current group, advanced incrementally (no division in the row loop).  The
     // leaving row y - r - 1 is 2r + 1 rows before the entering row y + r, which
-    // is 2*kGroup slots ahead in the ring.
+    // is 2*kG slots ahead in the ring.
     const int wm = w & 15, back = ((2 * r + 1) * w) & 15;
-    int slot = (y_first - r) % ring;                            // entering row of the first group
+    int slot = (y_first - r) % ring;
     int offL = (int)(((int64_t)(y_first - r) * w + cstart) & 15);
     int offR = (int)(((int64_t)(y_first - r) * w + rstart) & 15);
+    // W16: the offsets of every row are these
+    const int aL = offL + tid, aR = kLBytes + ((offR + tid) >> 2) * 4, shA = ((offR + tid) & 3) * 8;
     int k_iter = 0;
     stage(y_first - 2 * r, slot, 0);
     // virtual output rows run from y_first - 2r (warm-up) to y_last
-    for (int yg = y_first - 2 * r; yg <= y_last; yg += kGroup, ++k_iter) {
-      const int ng = min(kGroup, y_last - yg + 1);
+    for (int yg = y_first - 2 * r; yg <= y_last; yg += kG, ++k_iter) {
+      const int ng = min(kG, y_last - yg + 1);
       const int buf = k_iter & 1;
       cp_async_wait_all();
       __syncthreads();  // this group's rows have landed; the previous Stage B is done
-      const int slot_next = slot + kGroup < ring ? slot + kGroup : slot + kGroup - ring;
-      if (yg + kGroup <= y_last) stage(yg + kGroup, slot_next, buf ^ 1);
+      const int slot_next = slot + kG < ring ? slot + kG : slot + kG - ring;
+      if (yg + kG <= y_last) stage(yg + kG, slot_next, buf ^ 1);
       // Stage A: ng row steps
       if (tid < NC) {
-        int sin = slot, offLi = offL, offRi = offR;
-  #pragma unroll 1
-        for (int k = 0; k < ng; ++k) {
-          const int y = yg + k;
-          const bool real_out = y - r - 1 >= y_first - r;
-          int sout = sin + 2 * kGroup;
-          if (sout >= ring) sout -= ring;
-          const uint8_t* rin = s_ring + sin * kRowBytes;
-          const uint8_t* rout = real_out ? s_ring + sout * kRowBytes : s_zero;
-          const int offLo = real_out ? ((offLi - back) & 15) : 0, offRo = real_out ? ((offRi - back) & 15) : 0;
-          const uint32_t Lin = (uint32_t)rin[offLi + tid] * 0x01010101u;
-          const uint32_t Lout = (uint32_t)rout[offLo + tid] * 0x01010101u;
-          const int ji = tid + offRi, jo = tid + offRo;
-          const uint32_t* Ri = reinterpret_cast<const uint32_t*>(rin + kLBytes) + (ji >> 2);
-          const uint32_t* Ro = reinterpret_cast<const uint32_t*>(rout + kLBytes) + (jo >> 2);
-          const int shi = (ji & 3) * 8, sho = (jo & 3) * 8;
-          uint32_t wi = Ri[0], wo = Ro[0];
-  #pragma unroll
-          for (int g = 0; g < 8; ++g) {
-            const uint32_t wi2 = Ri[g + 1], wo2 = Ro[g + 1];
-            const uint32_t ri = __funnelshift_r(wi, wi2, shi), ro = __funnelshift_r(wo, wo2, sho);
-            wi = wi2;
-            wo = wo2;
-            // byte b of ri/ro is disparity d0 + 31 - 4g - b
-            const uint32_t ai = __vabsdiffu4(Lin, ri), ao = __vabsdiffu4(Lout, ro);
-            // lane-wise u16 updates: sums stay in [0, 63*255], so no carry or
-            // borrow crosses the 16-bit lanes
-            Ve[g] = Ve[g] + (ai & 0x00FF00FFu) - (ao & 0x00FF00FFu);
-            Vo[g] = Vo[g] + __byte_perm(ai, 0u, 0x4341) - __byte_perm(ao, 0u, 0x4341);
+        if (W16 && yg >= y_first + 1) {
+          // every row of the group has a real leaving row and stores its sums
+          int sin = slot;
+#pragma unroll
+          for (int k = 0; k < kG; ++k) {
+            if (k < ng) {
+              int sout = sin + 2 * kG;
+              if (sout >= ring) sout -= ring;
+              const uint8_t* rin = s_ring + sin * kRowBytes;
+              const uint8_t* rout = s_ring + sout * kRowBytes;
+              vertical_row(Ve, Vo, rin, aL, reinterpret_cast<const uint32_t*>(rin + aR), shA, rout, aL,
+                           reinterpret_cast<const uint32_t*>(rout + aR), shA);
+              uint4* dst = reinterpret_cast<uint4*>(s_vs + (k * VC + tid + 1) * kColBytes);
+#pragma unroll
+              for (int m = 0; m < 8; ++m) dst[m] = make_uint4(Ve[2 * m], Vo[2 * m], Ve[2 * m + 1], Vo[2 * m + 1]);
+              sin = sin + 1 < ring ? sin + 1 : 0;
+            }
           }
-          if (y >= y_first) {
-            uint4* dst = reinterpret_cast<uint4*>(s_vs + (k * kVsCols + tid + 1) * kVsStride);
-  #pragma unroll
-            for (int m = 0; m < 4; ++m) dst[m] = make_uint4(Ve[2 * m], Vo[2 * m], Ve[2 * m + 1], Vo[2 * m + 1]);
+        } else {
+          int sin = slot, offLi = offL, offRi = offR;
+#pragma unroll 1
+          for (int k = 0; k < ng; ++k) {
+            const int y = yg + k;
+            const bool real_out = y - r - 1 >= y_first - r;
+            int sout = sin + 2 * kG;
+            if (sout >= ring) sout -= ring;
+            const uint8_t* rin = s_ring + sin * kRowBytes;
+            const uint8_t* rout = real_out ? s_ring + sout * kRowBytes : s_zero;
+            const int offLo = real_out ? ((offLi - back) & 15) : 0, offRo = real_out ? ((offRi - back) & 15) : 0;
+            const int ji = tid + offRi, jo = tid + offRo;
+            vertical_row(Ve, Vo, rin, offLi + tid, reinterpret_cast<const uint32_t*>(rin + kLBytes) + (ji >> 2),
+                         (ji & 3) * 8, rout, offLo + tid,
+                         reinterpret_cast<const uint32_t*>(rout + kLBytes) + (jo >> 2), (jo & 3) * 8);
+            if (y >= y_first) {
+              uint4* dst = reinterpret_cast<uint4*>(s_vs + (k * VC + tid + 1) * kColBytes);
+#pragma unroll
+              for (int m = 0; m < 8; ++m) dst[m] = make_uint4(Ve[2 * m], Vo[2 * m], Ve[2 * m + 1], Vo[2 * m + 1]);
+            }
+            sin = sin + 1 < ring ? sin + 1 : 0;
+            offLi = (offLi + wm) & 15;
+            offRi = (offRi + wm) & 15;
           }
-          sin = sin + 1 < ring ? sin + 1 : 0;
-          offLi = (offLi + wm) & 15;
-          offRi = (offRi + wm) & 15;
         }
       }
       slot = slot_next;
-      offL = (offL + kGroup * wm) & 15;
-      offR = (offR + kGroup * wm) & 15;
+      offL = (offL + kG * wm) & 15;
+      offR = (offR + kG * wm) & 15;
       if (yg + ng - 1 < y_first) continue;  // still warming up
       __syncthreads();
-      // Stage B: warp -> (row slot, half strip); lane -> disparity.  The warp
-      // slides the horizontal window along its half strip, 8 outputs per block.
+      // Stage B: warp -> (row g of the group, segment of TX / kSegs outputs);
+      // lane -> disparity pair.  The column sums of a pair are one 32-bit word
+      // (lo | hi << 16, each below 2^14), so one load serves two disparities.
+      // The horizontal window slides by delta = entering - leaving + 0x40004000:
+      // each u16 lane of delta is the lane's difference plus 0x4000, in
+      // [0x4000 - 16065, 0x4000 + 16065], so no borrow crosses lanes; T adds
+      // delta (mod 2^32) and H adds its upper lane, from which the emission
+      // recovers both window sums exactly.
       {
-        const int g = warp >> 1, half = warp & 1;
+        const int g = warp / kSegs, seg = warp % kSegs;
         const int y = yg + g;
         if (g < ng && y >= y_first) {
-          const int HW = TX / 2;
-          const int xa = half * HW, xb = min(half * HW + HW, TX);
-          const int d = d0 + lane;
-          const uint32_t dbits = d <= D ? (uint32_t)d : 0xFFFFFFFFu;  // invalid lanes never win
-          const uint16_t* vcol = reinterpret_cast<const uint16_t*>(s_vs + g * kVsCols * kVsStride) + lanepos;
-          constexpr int CS = kVsStride / 2;                              // u16 per column
-          const uint8_t* bm = s_bm + (buf * kGroup + g) * kBBytes + (int)(((int64_t)y * w + x0) & 15);
+          const int SW = TX / kSegs;                              // a multiple of 8
+          const int xa = seg * SW, xb = xa + SW;
+          constexpr int CW = kColBytes / 4;                       // words per column slot
+          const uint32_t* vcol = reinterpret_cast<const uint32_t*>(s_vs + g * VC * kColBytes) + lane;
+          const uint8_t* bm = s_bm + (buf * kG + g) * kBBytes + (int)(((int64_t)y * w + x0) & 15);
           uint32_t* krow = J.key + (int64_t)y * w + x0;
           // anchor test of strip-relative output column xi, given its map byte
           auto anchor = [&](int xi, uint8_t b) -> bool {
             const int xl = x0 + xi;
             return xi < xb && xl >= xo0 && xl <= xo1 && (xl == xo0 || xl == xo1 || b);
           };
-          // S starts as the window of output xa - 1 (column xa - 1 + j, shifted by
-          // the zero column: slot column xa + j), then every output adds its
-          // entering column and drops its leaving one; HW is a multiple of 8.
-          uint32_t S = 0;
-          for (int j = 0; j <= 2 * r; ++j) S += vcol[(xa + j) * CS];
+          // warm-up: the window of output xa - 1 (slot columns xa .. xa + 2r), in
+          // four independent partial sums
+          uint32_t T = 0, H = 0;
+          {
+            uint32_t T1 = 0, T2 = 0, T3 = 0, H1 = 0, H2 = 0, H3 = 0;
+            const uint32_t* p = vcol + xa * CW;
+            int j = 0;
+#pragma unroll 1
+            for (; j + 4 <= 2 * r + 1; j += 4, p += 4 * CW) {
+              const uint32_t v0 = p[0], v1 = p[CW], v2 = p[2 * CW], v3 = p[3 * CW];
+              T += v0; H += v0 >> 16;
+              T1 += v1; H1 += v1 >> 16;
+              T2 += v2; H2 += v2 >> 16;
+              T3 += v3; H3 += v3 >> 16;
+            }
+#pragma unroll 1
+            for (; j <= 2 * r; ++j, p += CW) {
+              const uint32_t v = p[0];
+              T += v;
+              H += v >> 16;
+            }
+            T += T1 + T2 + T3;
+            H += H1 + H2 + H3;
+          }
+          uint32_t n0 = 0;                                        // outputs done before the block
           // the map bytes of the next 32 outputs are read one chunk ahead
           uint8_t bcur = xa + lane < xb ? bm[xa + lane] : (uint8_t)0;
           for (int xbase = xa; xbase < xb; xbase += 32) {
             const uint8_t bnext = xbase + 32 + lane < xb ? bm[xbase + 32 + lane] : (uint8_t)0;
             const unsigned mask = __ballot_sync(0xffffffffu, anchor(xbase + lane, bcur));
             const int n = min(32, xb - xbase);
-            const uint16_t* pin = vcol + (xbase + 2 * r + 1) * CS;  // slot column of strip column x + 2r
-            const uint16_t* pout = vcol + xbase * CS;             // slot column of x - 1
-  #pragma unroll 1
+            const uint32_t* pin = vcol + (xbase + 2 * r + 1) * CW;  // slot column of strip column x + 2r
+            const uint32_t* pout = vcol + xbase * CW;             // slot column of x - 1
+#pragma unroll 1
             for (int i = 0; i < n; i += 8) {
-              uint32_t Sv[8];
-  #pragma unroll
+              uint32_t Tv[8], Hv[8];
+#pragma unroll
               for (int k = 0; k < 8; ++k) {
-                S += (uint32_t)pin[(i + k) * CS] - (uint32_t)pout[(i + k) * CS];
-                Sv[k] = S;
+                const uint32_t delta = pin[(i + k) * CW] - pout[(i + k) * CW] + 0x40004000u;
+                T += delta;
+                H += delta >> 16;
+                Tv[k] = T;
+                Hv[k] = H;
               }
               const unsigned bits = (mask >> i) & 0xFFu;
-              emit_block_half<0>(bits & 15u, Sv, dbits, krow + xbase + i, lane);
-              emit_block_half<4>(bits >> 4, Sv, dbits, krow + xbase + i, lane);
+              emit_block_half<0>(bits & 15u, Tv, Hv, n0, dlo, dhi, krow + xbase + i, lane);
+              emit_block_half<4>(bits >> 4, Tv, Hv, n0, dlo, dhi, krow + xbase + i, lane);
+              n0 += 8;
             }
             bcur = bnext;
           }
@@ -500,21 +571,28 @@ void launch_sad_tail(const SadJob* jobs, const SadItem* items, int n_items, int 
 }
 
 int sad_boxsum_smem_bytes(int r) {
-  const int ring = 2 * r + 1 + 2 * kGroup;
-  return (ring + 1) * kRowBytes + 2 * kGroup * kBBytes + kGroup * kVsCols * kVsStride;
+  const int ring = 2 * r + 1 + 2 * kG;
+  return (ring + 1) * kRowBytes + 2 * kG * kBBytes + kG * box_vcols(r) * kColBytes;
 }
 
-void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, unsigned* queue,
+template <bool W16>
+static void launch_box(const SadJob* jobs, const SadItem* items, int n_items, int smem, unsigned* queue,
                        cudaStream_t s) {
-  if (n_items <= 0) return;
-  const int smem = sad_boxsum_smem_bytes(max_r);
-  cudaFuncSetAttribute(k_sad_boxsum, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_sad_boxsum<W16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   int dev = 0, sms = 148, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sad_boxsum, kThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sad_boxsum<W16>, kThreads, smem);
   const int grid = std::min(n_items, sms * std::max(1, per_sm));
-  k_sad_boxsum<<<grid, kThreads, smem, s>>>(jobs, items, n_items, queue);
+  k_sad_boxsum<W16><<<grid, kThreads, smem, s>>>(jobs, items, n_items, queue);
+}
+
+void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, bool w16, unsigned* queue,
+                       cudaStream_t s) {
+  if (n_items <= 0) return;
+  const int smem = sad_boxsum_smem_bytes(max_r);
+  if (w16) launch_box<true>(jobs, items, n_items, smem, queue, s);
+  else launch_box<false>(jobs, items, n_items, smem, queue, s);
 }
 
 // ----------------------------------------------------------------- direct

@@ -127,11 +127,11 @@ struct SadItem {
   int32_t job, x0, d0, y0, y1;  // output rows y0..y1 inclusive, inside Omega
 };
 // Tail disparities: when 1..kTailMax disparities remain past the last whole
-// chunk of 32 (D + 1 = 257, 129, 65, ...), a chunk would leave most lanes idle;
+// chunk of 64 (D + 1 = 257, 129, 65, ...), a chunk would leave most lanes idle;
 // a separate kernel computes them (one box filter per disparity) and the
 // box-sum work list stops at the last whole chunk.
 constexpr int kTailMax = 8;
-__host__ __device__ inline int sad_tail_first(int D) { return ((D + 1) / 32) * 32; }   // 32: the box-sum chunk
+__host__ __device__ inline int sad_tail_first(int D) { return ((D + 1) / 64) * 64; }   // 64: the box-sum chunk
 __host__ __device__ inline bool sad_has_tail(int D) {
   const int rem = D + 1 - sad_tail_first(D);
   return rem > 0 && rem <= kTailMax;
@@ -141,9 +141,10 @@ __host__ __device__ inline int sad_tail_strip(int r) { return (256 - 2 * r) & ~3
 // tail disparities among the items' jobs (sizes shared memory); queue as below
 void launch_sad_tail(const SadJob* jobs, const SadItem* items, int n_items, int max_rem, unsigned* queue,
                      cudaStream_t s);
-// max_r: the largest block radius among the items (sizes shared memory)
+// max_r: the largest block radius among the items (sizes shared memory);
+// w16: every job's image width is a multiple of 16 (constant row phases);
 // queue: one device counter, zero before the launch (the kernel's work-item cursor)
-void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, unsigned* queue,
+void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, bool w16, unsigned* queue,
                        cudaStream_t s);
 // the direct kernel for the jobs whose window spans nw = sad_direct_words(block) words
 int sad_direct_words(int block);
@@ -154,7 +155,7 @@ int sad_boxsum_smem_bytes(int r);
 void launch_sad_finalize(const SadJob* jobs, int n_jobs, int max_w, int max_h, cudaStream_t s);
 // strip width of the box-sum kernel for radius r
 __host__ __device__ int sad_boxsum_strip(int r);
-constexpr int kSadChunk = 32;
+constexpr int kSadChunk = 64;   // disparities per box-sum work item
 
 // ----------------------------------------------------------- reconstruction
 struct ReconJob {

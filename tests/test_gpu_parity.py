@@ -151,11 +151,14 @@ SAD_CASES = [
     (40, 60, 0, 1), (40, 60, 5, 3), (61, 97, 31, 9), (61, 97, 32, 9), (61, 97, 33, 9),
     (70, 260, 64, 15), (90, 600, 40, 31), (80, 420, 100, 41), (70, 300, 64, 63), (47, 340, 255, 5),
     (65, 700, 256, 41),
-    # 1..8 disparities past the last whole chunk of 32 (the tail kernel's range)
+    # around the box sums' chunk of 64 disparities: a whole chunk, then 1 and 2
+    # disparities past it for the tail kernel, 8 (its largest), and 9 (a partial chunk)
+    (61, 97, 63, 9), (61, 97, 64, 9), (61, 97, 65, 9), (70, 320, 71, 15), (70, 320, 72, 15),
     (55, 330, 39, 11), (70, 360, 71, 63), (50, 300, 98, 1), (66, 520, 135, 25),
-    # the largest disparity range the 10-bit key holds (32 whole chunks), a tail
-    # of 8 at a large range, and a 9-disparity partial chunk with the largest block
-    (40, 1100, 1023, 5), (45, 1100, 999, 9), (70, 1200, 1000, 63),
+    # the largest disparity range the 10-bit key holds (16 whole chunks), a tail
+    # of 8 at a large range, partial chunks of 40 and 41 disparities (the last with
+    # the largest block); widths that are and are not multiples of 16
+    (40, 1100, 1023, 5), (40, 1104, 1023, 5), (45, 1100, 967, 9), (45, 1104, 999, 9), (70, 1200, 1000, 63),
 ]
 
 
@@ -557,7 +560,7 @@ def test_invalid_arguments_raise(ctx):
 
 def test_pipeline_large_disparity_range(ctx):
     # D = 600 on a 700-pixel-wide pair: the domain is 92 columns wide, the SAD
-    # runs 18 whole chunks of 32 and a partial one (601 = 18 * 32 + 25)
+    # runs 9 whole chunks of 64 and a partial one (601 = 9 * 64 + 25)
     w, h, D, B, K = 700, 90, 600, 9, 4
     r = synth.Rng(900)
     layers = synth._c2_style_layers(r, w, h, 120, contrast=60)

@@ -69,3 +69,36 @@ def test_static_entry_rejects_images_above_the_limit():
     t = torch.zeros(1, dtype=torch.uint8, device="cuda")
     st = f(t.data_ptr(), t.data_ptr(), t.data_ptr(), w, h, 16, 5, 0, t.data_ptr(), None, None, err, 256)
     assert st == 1 and b"static scratch limit" in err.value
+
+
+def test_static_entry_rejects_too_many_work_items():
+    # inside the pixel limit, but a very wide, short image with a large disparity
+    # range needs more work items than the static descriptor area holds
+    f = _static_fn()
+    h, w, D, B = 4, 1048576, 1023, 3        # 4,194,304 pixels; 74,832 work items
+    err = ctypes.create_string_buffer(256)
+    t = torch.zeros(1, dtype=torch.uint8, device="cuda")
+    st = f(t.data_ptr(), t.data_ptr(), t.data_ptr(), w, h, D, B, sb.SB_SAD_BOXSUM, t.data_ptr(), None, None, err, 256)
+    assert st == 5 and b"work items" in err.value
+
+
+def test_static_entry_in_two_driver_contexts():
+    import multiprocessing as mp
+
+    import noalloc_child
+    import oracle
+
+    rng = np.random.default_rng(5)
+    h, w, D, B = 80, 420, 64, 15
+    Ll = rng.integers(0, 256, (h, w)).astype(np.uint8)
+    Lr = np.clip(np.roll(Ll, -4, axis=1).astype(int) + rng.integers(-5, 6, (h, w)), 0, 255).astype(np.uint8)
+    bmap = (rng.random((h, w)) < 0.2).astype(np.uint8)
+    want_d, want_c = oracle.boundary_sad(Ll, Lr, oracle.anchor_mask(bmap, D, B), D, B)
+    q = mp.get_context("spawn").Queue()
+    p = mp.get_context("spawn").Process(target=noalloc_child.two_contexts, args=(sb.library_path(), Ll, Lr, bmap, D, B, q))
+    p.start()
+    status, res = q.get(timeout=300)
+    p.join(timeout=60)
+    assert status == "ok", res
+    for disp, cost in res:
+        assert np.array_equal(disp, want_d) and np.array_equal(cost, want_c)
