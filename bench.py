@@ -10,13 +10,21 @@ reconstruction, selective blur) over the 250 pairs.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--pairs P] [--sad-variant auto|boxsum|direct] [--no-e2e] [--no-cpu]
-                  [--no-serve] [--accuracy]
+                  [--no-serve] [--no-configs] [--accuracy] [--rank-dry-run]
+
+With --gpus N > 1 and no torchrun environment, the script re-runs itself as N
+ranks on this node (torch.distributed.run, 127.0.0.1 rendezvous); it stops
+with an error when fewer than N GPUs are visible.  --rank-dry-run runs only
+the ranks' bookkeeping (frames per rank, the max-over-ranks step time, the
+aggregate rate) on CPU over gloo, without a GPU.
 
 Prints one JSON line (rank 0).  ``value`` is pairs/s with inputs resident in
 HBM (batched form replayed from a CUDA graph); ``e2e`` is the same metric
 through sb_run with pinned HOST buffers (copies inside the timed region);
 ``per_pair_plain`` is the per-pair launch form on the same GPU;
 ``stage_ms`` splits the step by stage (CUDA events inside the graph);
+``per_config`` holds the single-pair workloads (320x240 and 1400x1100): the
+whole-image CPU oracle time (one thread) and the per-pair GPU latency;
 ``sad_gcell_s`` counts N_b (D+1) B^2 cells over the SAD kernels' time;
 ``roofline`` is for the SAD kernel the run uses (the box sums by default:
 integer ALU bound; ``--sad-variant direct`` reports the direct kernel
@@ -49,10 +57,10 @@ BOX_OPS_PER_PXD = 6
 # tail disparity d=256 runs in its own kernel (timed in the "sad_rest" stage)
 BOX_DISPARITIES_C3 = 256
 # DRAM bytes of k_sad_boxsum per 4096x2304 pair (D=256, block 41, d = 0..255): the ncu
-# capture of one 8-pair launch read 457.10 MB and wrote 169.55 MB (L maps and boundary map
+# capture of one 8-pair launch read 498.54 MB and wrote 191.32 MB (L maps and boundary map
 # in, argmin keys out); a launch over P pairs moves P times that, since each pair's data is
 # its own
-SAD_DRAM_BYTES_PER_PAIR = (457.103360e6 + 169.545984e6) / 8
+SAD_DRAM_BYTES_PER_PAIR = (498.537216e6 + 191.321344e6) / 8
 METRIC = "stereo pairs/s at 4096x2304 (batched vs per-pair), SAD Gcell/s, p99 latency"
 # --sad-variant: the library's per-pair choice (box sums at this workload's density), or either
 # SAD kernel forced (the roofline then describes that kernel)
@@ -299,12 +307,20 @@ def uneven_measure(sb, torch, n_pairs=64, steps=3):
     return res
 
 
-def serve_measure(sb, torch, rates=(50.0, 150.0, 300.0), n_requests=240, pool=32, seed=7):
-    """Served form: requests drawn like the mixed-resolution workload (c5),
-    Poisson arrivals at each rate into the continuous-batching server (40 GB
-    admission budget), p50/p99 latency and achieved pairs/s; beside it, the
-    same requests executed one by one (host copy in, sb_run per pair, copy
-    out) on the same GPU."""
+SERVE_RATES = (10.0, 25.0, 50.0, 100.0, 150.0, 200.0, 300.0, 400.0)
+
+
+def serve_measure(sb, torch, rates=SERVE_RATES, per_rate=250, pool=64, seed=7, saturate=2.0):
+    """Served form, workload c5: a stream of len(rates) * per_rate requests
+    (2000 by default; seed 7) in segments of per_rate Poisson arrivals at each
+    swept rate, into one continuous-batching server (40 GB admission budget),
+    each segment drained before the next; then one more segment at `saturate`
+    times the one-by-one rate.  Requests draw the mixed resolution, disparity,
+    block and K of the uneven batch from a pool of distinct pairs.  Reported
+    per segment: p50/p99 latency (arrival to result in pinned host memory),
+    achieved pairs/s and batches; beside it, requests executed one by one
+    (host copy in, sb_run per pair, copy out) on the same GPU."""
+    import numpy as np
     import synth
     from paper_2001_07809_b300.serve import Server, percentile
     reqs = []
@@ -318,7 +334,15 @@ def serve_measure(sb, torch, rates=(50.0, 150.0, 300.0), n_requests=240, pool=32
                                 sigma=p.sigma, ranges=p.ranges)
         reqs.append((dl.cpu().pin_memory(), dr.cpu().pin_memory(), params))
     torch.cuda.synchronize()
-    out = {"requests_per_rate": n_requests, "distinct_pairs": pool, "budget_gb": 40}
+    n_total = per_rate * len(rates)
+    out = {"stream": "%d requests (seed %d) in %d segments of %d Poisson arrivals at %s pairs/s, each drained "
+                     "before the next, then %d at %gx the one-by-one rate" % (n_total, seed, len(rates), per_rate,
+                                                                              "/".join("%g" % r for r in rates),
+                                                                              per_rate, saturate),
+           "distinct_pairs": pool, "budget_gb": 40}
+    # which pool pair each request of the stream is (seeded)
+    rng = np.random.default_rng(seed)
+    pick = rng.integers(pool, size=n_total + per_rate)
     # one by one: copy in, one sb_run, copy out into pinned buffers, per request
     ctx = sb.Context(0)
     hout = {}
@@ -328,8 +352,8 @@ def serve_measure(sb, torch, rates=(50.0, 150.0, 300.0), n_requests=240, pool=32
             hout[(h, w)] = (torch.empty((h, w, 3), dtype=torch.uint8, pin_memory=True),
                             torch.empty((h, w), dtype=torch.int16, pin_memory=True))
     lat = []
-    for i in range(-pool, min(n_requests, 3 * pool)):      # the first pool requests warm up
-        hl, hr, p = reqs[i % pool]
+    for i in range(-pool, per_rate):      # the first pool requests (every pair once) warm up
+        hl, hr, p = reqs[i % pool] if i < 0 else reqs[int(pick[i])]
         t0 = time.perf_counter()
         dl, dr = hl.cuda(non_blocking=True), hr.cuda(non_blocking=True)
         o = torch.empty_like(dl)
@@ -342,42 +366,92 @@ def serve_measure(sb, torch, rates=(50.0, 150.0, 300.0), n_requests=240, pool=32
         if i >= 0:
             lat.append(time.perf_counter() - t0)
     ctx.close()
-    out["one_by_one"] = {"p50_ms": 1e3 * percentile(lat, 50), "p99_ms": 1e3 * percentile(lat, 99),
-                         "pairs_s": len(lat) / sum(lat)}
-    rng = __import__("numpy").random.default_rng(seed)
-    for rate in rates:
-        srv = Server(0, mem_budget_bytes=40 << 30, max_batch=64)
-        pending = threading.Semaphore(0)
+    one_rate = len(lat) / sum(lat)
+    out["one_by_one"] = {"requests": len(lat), "p50_ms": 1e3 * percentile(lat, 50),
+                         "p99_ms": 1e3 * percentile(lat, 99), "pairs_s": one_rate}
+    srv = Server(0, mem_budget_bytes=40 << 30, max_batch=64)
+    pending = threading.Semaphore(0)
 
-        def done(f, srv=srv, pending=pending):
-            if f.exception() is None:
-                srv.recycle(f.result())
-            pending.release()
+    def done(f):
+        if not f.cancelled() and f.exception() is None:
+            srv.recycle(f.result())
+        pending.release()
 
-        # warm-up: every distinct pair twice, in one burst
-        for i in range(2 * pool):
-            srv.submit(*reqs[i % pool]).add_done_callback(done)
-        for _ in range(2 * pool):
-            pending.acquire(timeout=300)
+    # warm-up: every distinct pair twice, in one burst
+    for i in range(2 * pool):
+        srv.submit(*reqs[i % pool]).add_done_callback(done)
+    for _ in range(2 * pool):
+        pending.acquire(timeout=300)
+    segments = []
+    plan = [(r, i * per_rate) for i, r in enumerate(rates)] + [(saturate * one_rate, n_total)]
+    for rate, first in plan:
         srv.completed.clear()
         b0 = srv.batches
-        arrivals = synth.poisson_arrivals(n_requests, rate, seed)
+        arrivals = synth.poisson_arrivals(per_rate, rate, seed)
         t_start = time.perf_counter()
-        for i, ta in enumerate(arrivals):
+        for k, ta in enumerate(arrivals):
             now = time.perf_counter() - t_start
             if ta > now:
                 time.sleep(ta - now)
-            srv.submit(*reqs[int(rng.integers(pool))]).add_done_callback(done)
-        for _ in range(n_requests):
+            srv.submit(*reqs[int(pick[first + k])]).add_done_callback(done)
+        for _ in range(per_rate):
             if not pending.acquire(timeout=600):
                 raise RuntimeError("served request did not complete")
         t_end = time.perf_counter()
         lat = srv.latencies()
-        batches = srv.batches - b0
-        srv.close()
-        out["rate_%g" % rate] = {"p50_ms": 1e3 * percentile(lat, 50), "p99_ms": 1e3 * percentile(lat, 99),
-                                 "pairs_s": n_requests / (t_end - t_start), "batches": batches}
+        segments.append({"rate": rate, "requests": per_rate, "p50_ms": 1e3 * percentile(lat, 50),
+                         "p99_ms": 1e3 * percentile(lat, 99), "pairs_s": per_rate / (t_end - t_start),
+                         "batches": srv.batches - b0})
+    srv.close()
+    out["segments"] = segments[:-1]
+    out["saturating"] = segments[-1]
+    out["served_over_one_by_one_at_saturation"] = segments[-1]["pairs_s"] / one_rate
     return out
+
+
+def per_config_measure(sb, torch, steps=20, warmup=3):
+    """The single-pair workloads c1 (320x240, D 32, block 15) and c2
+    (1400x1100, D 128, block 31): the CPU oracle on the whole pair in one
+    thread (timed once), and the plain per-pair GPU pipeline (sb_run per
+    call, `steps` timed calls after `warmup`), outputs checked against the
+    oracle's (disparity bit-exact, blur within one level)."""
+    import numpy as np
+    import oracle
+    import synth
+    res = {}
+    ctx = sb.Context(0)
+    for name in ("c1", "c2"):
+        sc, p, frame = synth.workload(name)
+        left, right, _ = sc.render(frame=frame, want_gt=False)
+        h, w = left.shape[:2]
+        params = sb.make_params(k=p.k, max_disp=p.max_disp, block=p.block, disp_threshold=p.disp_threshold,
+                                sigma=p.sigma, ranges=p.ranges)
+        dl, dr = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+        o = torch.empty_like(dl)
+        d = torch.empty((h, w), dtype=torch.int16, device="cuda")
+        pair = [sb.Pair(dl, dr, params, o, d)]
+        for _ in range(warmup):
+            sb.sb_run(ctx, pair, sb.SB_RUN_PLAIN)
+        ctx.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            sb.sb_run(ctx, pair, sb.SB_RUN_PLAIN)
+        e1.record()
+        torch.cuda.synchronize()
+        gpu_ms = e0.elapsed_time(e1) / steps
+        t0 = time.perf_counter()
+        want = oracle.run(left, right, p)
+        oracle_s = time.perf_counter() - t0
+        got_d = d.cpu().numpy().view(np.uint16)
+        got_rgb = o.cpu().numpy()
+        res[name] = {"size": "%dx%d" % (w, h), "D": p.max_disp, "block": p.block, "K": p.k,
+                     "oracle_s": oracle_s, "oracle_threads": 1, "gpu_ms_per_pair": gpu_ms, "gpu_steps": steps,
+                     "gpu_over_oracle": oracle_s / (gpu_ms / 1000.0),
+                     "disparity_equal": bool(np.array_equal(got_d, want.disp)),
+                     "blur_max_diff": int(np.abs(got_rgb.astype(int) - want.out_rgb.astype(int)).max())}
+    ctx.close()
+    return res
 
 
 def run_ours(args):
@@ -452,7 +526,7 @@ def run_ours(args):
     ctx.profile_enable(False)
 
     # plain per-pair form on the same pairs (work split tuned for one pair, untimed)
-    plain_steps = 1
+    plain_steps = 3
     tune_plain = sb.sb_autotune(ctx, pairs[:1], sb.SB_RUN_PLAIN)
     sb.sb_run(ctx, pairs[:4], sb.SB_RUN_PLAIN)
     ctx.synchronize()
@@ -517,13 +591,16 @@ def run_ours(args):
                "d2h_bytes_per_step": P * H * W * 5, "ms_per_step": e2e_s * 1000.0}
         del hl, hr, ho, hd
 
-    serving = uneven = None
+    serving = uneven = per_config = None
     if rank == 0 and world == 1 and not args.no_serve:
         del lefts, rights, outs, disps, pairs
         torch.cuda.empty_cache()
         uneven = uneven_measure(sb, torch)
         torch.cuda.empty_cache()
         serving = serve_measure(sb, torch)
+
+    if rank == 0 and world == 1 and not args.no_configs:
+        per_config = per_config_measure(sb, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -560,7 +637,7 @@ def run_ours(args):
                     "measured_rates": rates,
                     "frac_of_measured_iadd": (achieved / rates["iadd_tops"]) if "iadd_tops" in rates else None,
                     "ops_per_launch": ops,
-                    "ops_note": "6 ops x |Omega| x 256 disparities (the box-sum chunks, d = 0..255) x pairs",
+                    "ops_note": "6 ops x |Omega| x 256 disparities (the box-sum chunks of 64, d = 0..255) x pairs",
                     "launch_ms": box_ms}
         if ul_mhz:
             roofline["peak_at_gemm_load_clock"] = {"sm_mhz": ul_mhz, "peak": alu_peak * ul_mhz / sm_max,
@@ -588,12 +665,51 @@ def run_ours(args):
                                        "then the blur forms: tiles of 112 and 64 rows, strips (32)"},
             "uneven_batch": uneven,
             "serving": serving,
+            "per_config": per_config,
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
     ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def launch_ranks(n: int, argv) -> int:
+    """Re-run this script as n ranks on this node through torch.distributed.run
+    (one process per GPU, 127.0.0.1 rendezvous on a free port); returns the
+    launcher's exit code."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", str(n),
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + list(argv)
+    return subprocess.call(cmd)
+
+
+def run_rank_dry(args):
+    """The multi-rank bookkeeping alone, on CPU over gloo: every rank takes its
+    frames, reports a step time, and rank 0 prints the frames of all ranks,
+    the max-over-ranks step time and the aggregate rate."""
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        dist.init_process_group("gloo")
+    frames = rank_frames(rank, args.pairs)
+    ms = 100.0 + 10.0 * rank                       # a stand-in step time per rank
+    ms_max = max_over_ranks(ms, world, "cpu")
+    gathered = [None] * world
+    if world > 1:
+        dist.all_gather_object(gathered, frames)
+    else:
+        gathered = [frames]
+    if rank == 0:
+        print(json.dumps({"dry_run": True, "n_gpus": world, "frames": gathered, "ms_per_step": ms_max,
+                          "value": aggregate_rate(args.pairs, world, ms_max)}))
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -687,10 +803,27 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the single-pair workloads (c1, c2)")
+    ap.add_argument("--rank-dry-run", action="store_true",
+                    help="only the multi-rank bookkeeping, on CPU over gloo (no GPU)")
     ap.add_argument("--accuracy", action="store_true", help="Eq. 3 study of the open readings, then exit")
     ap.add_argument("--sad-variant", choices=sorted(SAD_VARIANTS), default="auto",
                     help="SAD kernel: the per-pair automatic choice (default) or one forced")
     args = ap.parse_args()
+    world_env = os.environ.get("WORLD_SIZE")
+    if world_env is None and args.gpus > 1:
+        if not args.rank_dry_run:
+            import torch
+            if torch.cuda.device_count() < args.gpus:
+                sys.stderr.write("bench.py: --gpus %d needs %d visible GPUs, found %d\n"
+                                 % (args.gpus, args.gpus, torch.cuda.device_count()))
+                return 2
+        return launch_ranks(args.gpus, sys.argv[1:])
+    if world_env is not None and int(world_env) != args.gpus:
+        sys.stderr.write("bench.py: WORLD_SIZE=%s but --gpus %d\n" % (world_env, args.gpus))
+        return 2
+    if args.rank_dry_run:
+        return run_rank_dry(args)
     if args.accuracy:
         return run_accuracy(args)
     if args.impl == "reference":

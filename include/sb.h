@@ -44,7 +44,7 @@ typedef enum {
   SB_ERR_INVALID_ARG = 1,
   SB_ERR_CUDA = 2,
   SB_ERR_OOM = 3,
-  SB_ERR_TIMEOUT = 4,
+  SB_ERR_TIMEOUT = 4,       /* a bounded device-side loop gave up (see sb_set_union_limit) */
   SB_ERR_UNSUPPORTED = 5
 } sb_status;
 
@@ -197,6 +197,28 @@ sb_status sb_selective_blur(sb_context* ctx, const uint8_t* rgb, const uint16_t*
  * SB_ERR_INVALID_ARG for any other value. */
 enum { SB_BLUR_AUTO = 0, SB_BLUR_STRIP = 32, SB_BLUR_TILES_64 = 64, SB_BLUR_TILES_112 = 112 };
 sb_status sb_set_blur_form(sb_context* ctx, int32_t form);
+
+/* Chunking of SB_RUN_HOST_IO | SB_RUN_BATCHED runs on this context: pairs
+ * stream through three device staging slots in chunks whose input bytes
+ * (left + right RGB) start near first_bytes at both ends of the batch and
+ * double towards the middle up to max_bytes (at least one pair per chunk), so
+ * the first upload and the last download, which nothing overlaps, stay short.
+ * Defaults 256 MB and 3 GB; (0, 0) restores them; 0 < first_bytes <=
+ * max_bytes, else SB_ERR_INVALID_ARG.  Smaller chunks need less staging
+ * memory (three times the largest chunk's inputs and outputs). */
+sb_status sb_set_host_chunk(sb_context* ctx, size_t first_bytes, size_t max_bytes);
+/* Number of chunks the last SB_RUN_HOST_IO run on this context used. */
+int32_t sb_host_io_chunks(const sb_context* ctx);
+
+/* Bound of the connected-components union-find (Section III's component
+ * clean-up; the paper states no bound): every root search follows at most
+ * `limit` parent links and every union makes at most `limit` attempts, for
+ * later sb_refine_boundaries and sb_run calls on this context.  A run that
+ * reaches the bound is not valid: the next sb_synchronize returns
+ * SB_ERR_TIMEOUT (and clears the flag; the context stays usable).  0 restores
+ * the default, 2^22, far above any chain an image of up to 2^31 pixels
+ * builds; a negative limit returns SB_ERR_INVALID_ARG. */
+sb_status sb_set_union_limit(sb_context* ctx, int32_t limit);
 
 /* One stereo pair for sb_run. */
 typedef struct {

@@ -18,7 +18,7 @@ __all__ = [
     "SbError", "Context", "Pair", "sb_default_params", "make_params", "sb_create", "sb_destroy",
     "sb_rgb_to_lightness", "sb_kmeans_segment", "sb_refine_boundaries", "sb_boundary_sad",
     "sb_reconstruct_disparity", "sb_selective_blur", "sb_run", "sb_synchronize", "sb_launch_count",
-    "sb_lr_consistency", "sb_autotune", "sb_set_blur_form", "SB_BLUR_AUTO", "SB_BLUR_STRIP", "SB_BLUR_TILES_64",
+    "sb_lr_consistency", "sb_autotune", "sb_set_blur_form", "sb_set_union_limit", "sb_set_host_chunk", "sb_host_io_chunks", "SB_BLUR_AUTO", "SB_BLUR_STRIP", "SB_BLUR_TILES_64",
     "SB_BLUR_TILES_112", "SB_PEEK_SNAPSHOT", "SB_PEEK_INPLACE", "SB_VIEW_LEFT", "SB_VIEW_RIGHT",
     "SB_RUN_PLAIN", "SB_RUN_BATCHED", "SB_RUN_GRAPH", "SB_RUN_HOST_IO", "SB_SAD_AUTO", "SB_SAD_DIRECT",
     "SB_SAD_BOXSUM", "SB_MORPH_FILL_REMOVE", "SB_MORPH_OPEN_CLOSE", "UNDETERMINED", "library_path",
@@ -92,6 +92,9 @@ def _load():
         "sb_lr_consistency": ([V, V, V, I32, I32, I32, V, V], ctypes.c_int),
         "sb_autotune": ([V, V, I32, ctypes.c_uint32, V, V, V], ctypes.c_int),
         "sb_set_blur_form": ([V, I32], ctypes.c_int),
+        "sb_set_union_limit": ([V, I32], ctypes.c_int),
+        "sb_set_host_chunk": ([V, ctypes.c_size_t, ctypes.c_size_t], ctypes.c_int),
+        "sb_host_io_chunks": ([V], ctypes.c_int32),
         "sb_selective_blur": ([V, V, V, I32, I32, V, I32, ctypes.c_float, V], ctypes.c_int),
         "sb_run": ([V, ctypes.POINTER(sb_pair), I32, U32], ctypes.c_int),
         "sb_profile_enable": ([V, ctypes.c_int], ctypes.c_int),
@@ -167,6 +170,17 @@ class Context:
 
     def synchronize(self):
         _check(self, _lib.sb_synchronize(self.handle))
+
+    def set_host_chunk(self, first_bytes: int, max_bytes: int):
+        """Input bytes of the first and the largest chunk of host-buffer runs ((0, 0): defaults)."""
+        _check(self, _lib.sb_set_host_chunk(self.handle, int(first_bytes), int(max_bytes)))
+
+    def host_io_chunks(self) -> int:
+        return int(_lib.sb_host_io_chunks(self.handle))
+
+    def set_union_limit(self, limit: int):
+        """Bound of the connected-components union-find (0: the default)."""
+        _check(self, _lib.sb_set_union_limit(self.handle, int(limit)))
 
     def workspace_bytes(self) -> int:
         return int(_lib.sb_workspace_bytes(self.handle))
@@ -297,6 +311,18 @@ def sb_autotune(ctx: Context, pairs: List[Pair], flags: int = SB_RUN_PLAIN):
     items, rows = ctypes.c_int32(0), ctypes.c_int32(0)
     _check(ctx, _lib.sb_autotune(ctx.handle, arr, len(pairs), flags, ms, ctypes.byref(items), ctypes.byref(rows)))
     return int(items.value), int(rows.value), [float(v) for v in ms]
+
+
+def sb_set_host_chunk(ctx: Context, first_bytes: int, max_bytes: int):
+    ctx.set_host_chunk(first_bytes, max_bytes)
+
+
+def sb_host_io_chunks(ctx: Context) -> int:
+    return ctx.host_io_chunks()
+
+
+def sb_set_union_limit(ctx: Context, limit: int):
+    ctx.set_union_limit(limit)
 
 
 def sb_set_blur_form(ctx: Context, form: int):

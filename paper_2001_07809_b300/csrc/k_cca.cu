@@ -22,22 +22,29 @@ namespace sb {
 
 namespace {
 constexpr int CT = 32;                 // CCA tile side
-constexpr int kUnionLimit = 1 << 22;   // retries of one union before flagging an error
 
-__device__ __forceinline__ int find_root(const int* P, int x) {
-  int guard = 0;
-  while (true) {
-    int p = P[x];
-    if (p == x || ++guard > kUnionLimit) return x;
+// Root of x: follows at most `limit` parent links (CcaJob::union_limit); a
+// chain that is longer clears ok (the run is reported as SB_ERR_TIMEOUT) and
+// returns the node reached.  Every link points to a smaller index, so the walk
+// always stays inside the image and ends.
+__device__ __forceinline__ int find_root(const int* P, int x, int limit, bool& ok) {
+  for (int guard = 0;; ++guard) {
+    const int p = P[x];
+    if (p == x) return x;
+    if (guard >= limit) {
+      ok = false;
+      return x;
+    }
     x = p;
   }
 }
 
-// Lock-free union (both roots hang the larger index under the smaller).
-__device__ __forceinline__ bool unite(int* P, int a, int b) {
-  for (int it = 0; it < kUnionLimit; ++it) {
-    a = find_root(P, a);
-    b = find_root(P, b);
+// Lock-free union (both roots hang the larger index under the smaller), at
+// most `limit` attempts.
+__device__ __forceinline__ bool unite(int* P, int a, int b, int limit, bool& ok) {
+  for (int it = 0; it < limit; ++it) {
+    a = find_root(P, a, limit, ok);
+    b = find_root(P, b, limit, ok);
     if (a == b) return true;
     if (a < b) {
       int old = atomicMin(&P[b], a);
@@ -115,13 +122,13 @@ __global__ void __launch_bounds__(kCcaWarps * 32) k_cca_local(const CcaJob* __re
           P[C] = C;
         } else {
           const int s1 = run_start(prev, __ffs(T) - 1);
-          const int r1 = find_root(P, (y - 1) * CT + s1);
+          const int r1 = find_root(P, (y - 1) * CT + s1, J.union_limit, ok);
           P[C] = r1;   // r1 < C: the smaller index stays the root
           unsigned others = T & (prev & ~(prev << 1)) & ~(1u << s1);   // starts of the other runs above
           while (others) {
             const int b = __ffs(others) - 1;
             others &= others - 1u;
-            ok &= unite(P, r1, (y - 1) * CT + b);
+            ok &= unite(P, r1, (y - 1) * CT + b, J.union_limit, ok);
           }
         }
       }
@@ -135,7 +142,7 @@ __global__ void __launch_bounds__(kCcaWarps * 32) k_cca_local(const CcaJob* __re
     if (x >= w) continue;
     int v = -1;
     if ((cur >> lane) & 1u) {
-      const int root = find_root(P, y * CT + run_start(cur, lane));
+      const int root = find_root(P, y * CT + run_start(cur, lane), J.union_limit, ok);
       v = (ty0 + (root >> 5)) * w + tx0 + (root & (CT - 1));
     }
     J.lab[(int64_t)(ty0 + y) * w + x] = v;
@@ -170,7 +177,7 @@ __global__ void __launch_bounds__(128) k_cca_merge(const CcaJob* __restrict__ jo
       if (qx < 0 || qy < 0 || qx >= w) continue;
       if (qx >= tx0 && qx < tx0 + CT && qy >= ty0) continue;  // same tile: done locally
       const int q = qy * w + qx;
-      if (J.b[q]) ok &= unite(J.lab, p, q);
+      if (J.b[q]) ok &= unite(J.lab, p, q, J.union_limit, ok);
     }
   }
   if (!ok) atomicOr(dev_err, DEV_ERR_CCA_ITER);
@@ -198,7 +205,7 @@ __device__ __forceinline__ int tile_local(int v, int base, int w, float inv_w) {
 }
 
 constexpr int kCountTiles = 2;   // tiles per CTA of k_cc_count (along x)
-__global__ void __launch_bounds__(256) k_cc_count(const CcaJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(256) k_cc_count(const CcaJob* __restrict__ jobs, uint32_t* dev_err) {
   constexpr int kPer = CT * CT / 256;   // pixels per thread and tile
   __shared__ unsigned s_cnt[kCountTiles][CT * CT];   // pixels per local root
   __shared__ int s_root[kCountTiles][CT * CT];       // component root of each referenced local root
@@ -213,6 +220,7 @@ __global__ void __launch_bounds__(256) k_cc_count(const CcaJob* __restrict__ job
   __syncthreads();
   int u[kCountTiles][kPer], v[kCountTiles][kPer];
   unsigned mine = 0;
+  bool ok = true;
 #pragma unroll
   for (int tt = 0; tt < kCountTiles; ++tt)
 #pragma unroll
@@ -247,7 +255,7 @@ __global__ void __launch_bounds__(256) k_cc_count(const CcaJob* __restrict__ job
       const unsigned c = s_cnt[tt][i];
       if (c) {   // pixel i is a local root some pixel of the tile refers to
         const int g = (ty0 + (i >> 5)) * w + tx0 + (i & (CT - 1));
-        const int R = find_root(J.lab, g);
+        const int R = find_root(J.lab, g, J.union_limit, ok);
         s_root[tt][i] = R;
         atomicAdd(&J.size[R], c);
         if (R == g) J.roots[atomicAdd(reinterpret_cast<unsigned long long*>(&J.cut[5]), 1ull)] = R;
@@ -271,6 +279,7 @@ __global__ void __launch_bounds__(256) k_cc_count(const CcaJob* __restrict__ job
     }
   }
   if (threadIdx.x == 0 && s_total) atomicAdd(reinterpret_cast<unsigned long long*>(&J.cut[0]), (unsigned long long)s_total);
+  if (!ok) atomicOr(dev_err, DEV_ERR_CCA_ITER);
 }
 
 __device__ __forceinline__ int64_t removal_limit(const CcaJob& J) {
@@ -440,7 +449,7 @@ void launch_cca(const CcaJob* jobs, int n_jobs, int max_w, int max_h, uint32_t* 
   k_cca_merge<<<dim3((tiles_x + kMergeTiles - 1) / kMergeTiles, tiles.y, n_jobs), 128, 0, s>>>(jobs, dev_err);
 }
 
-void launch_cc_filter(const CcaJob* jobs, int n_jobs, int max_w, int max_h, cudaStream_t s) {
+void launch_cc_filter(const CcaJob* jobs, int n_jobs, int max_w, int max_h, uint32_t* dev_err, cudaStream_t s) {
   if (n_jobs <= 0) return;
   const int64_t n = (int64_t)max_w * max_h;
   int dev = 0, sms = 148;
@@ -452,7 +461,7 @@ void launch_cc_filter(const CcaJob* jobs, int n_jobs, int max_w, int max_h, cuda
   bpj64 = std::min<int64_t>(bpj64, (16 * 8 * (int64_t)sms + n_jobs - 1) / n_jobs);
   const int bpj = (int)std::max<int64_t>(1, bpj64);
   const int tiles_x = (max_w + CT - 1) / CT;
-  k_cc_count<<<dim3((tiles_x + kCountTiles - 1) / kCountTiles, (max_h + CT - 1) / CT, n_jobs), 256, 0, s>>>(jobs);
+  k_cc_count<<<dim3((tiles_x + kCountTiles - 1) / kCountTiles, (max_h + CT - 1) / CT, n_jobs), 256, 0, s>>>(jobs, dev_err);
   // root-list passes: roots are few; four waves of the batch in all
   const int rpj = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(bpj, sms), (4 * 8 * (int64_t)sms + n_jobs - 1) / n_jobs));
   k_cc_hist<<<dim3(rpj, n_jobs), 256, 0, s>>>(jobs);

@@ -206,6 +206,10 @@ struct sb_context {
   std::map<std::string, int> tuned_blur;   // same shapes -> blur tile height (112 or 64)
   int sad_target_override = 0;   // set while sb_autotune times a candidate
   int blur_by_override = 0;
+  int union_limit = kUnionLimitDefault;   // connected components: parent links / union attempts
+  size_t host_first = (size_t)256 << 20;  // host-buffer streaming: first chunk's input bytes (ramp start)
+  size_t host_cap = (size_t)3072 << 20;   // and the largest chunk
+  int host_chunks = 0;                    // chunks of the last host-buffer run
   int sms = 148;
 };
 
@@ -648,7 +652,7 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
       SB_MEMSET(ctx, (r.ws.shist, 0, (size_t)r.ws.shist_len * 4, s));
       SB_MEMSET(ctx, (r.ws.rowcnt, 0, (size_t)r.g.h * 4, s));
       J.push_back(CcaJob{r.ws.refined, r.ws.lab, r.ws.size_key, r.ws.shist, r.ws.rowcnt, r.ws.cut, r.ws.filtered,
-                         r.ws.roots, r.g.w, r.g.h, r.ws.shist_len, r.g.p.cc_remove_fraction});
+                         r.ws.roots, r.g.w, r.g.h, r.ws.shist_len, r.g.p.cc_remove_fraction, ctx->union_limit});
     }
     const CcaJob* d = upload(ctx, J, &st);
     if (!d) return st;
@@ -657,7 +661,7 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
       SB_LAUNCHED(ctx, 2);
     }
     if (!ctx->dry) {
-      launch_cc_filter(d, n, max_w, max_h, s);
+      launch_cc_filter(d, n, max_w, max_h, ctx->dev_err, s);
       SB_LAUNCHED(ctx, 6);
     }
   }
@@ -898,7 +902,9 @@ sb_status sb_synchronize(sb_context* ctx) {
   SB_CUDA(ctx, cudaMemcpy(&e, ctx->dev_err, 4, cudaMemcpyDeviceToHost));
   if (e) {
     cudaMemset(ctx->dev_err, 0, 4);
-    if (e & DEV_ERR_TIMEOUT) return fail(ctx, SB_ERR_TIMEOUT, "a device-side wait gave up (flags 0x%x)", e);
+    if (e & DEV_ERR_CCA_ITER)
+      return fail(ctx, SB_ERR_TIMEOUT, "connected components: a union-find search or union reached its limit of %d "
+                  "(sb_set_union_limit); the run's results are not valid", ctx->union_limit);
     return fail(ctx, SB_ERR_CUDA, "device-side check failed (flags 0x%x)", e);
   }
   return SB_OK;
@@ -986,12 +992,12 @@ sb_status sb_refine_boundaries(sb_context* ctx, const uint8_t* labels, int32_t w
   SB_CUDA(ctx, cudaMemsetAsync(cut, 0, 64, s));
   SB_CUDA(ctx, cudaMemsetAsync(rowcnt, 0, (size_t)h * 4, s));
   std::vector<CcaJob> CJ{CcaJob{ref, lab, size, sh, rowcnt, cut, boundary, roots, w, h, (int32_t)shist,
-                                cc_remove_fraction}};
+                                cc_remove_fraction, ctx->union_limit}};
   const CcaJob* dc = upload(ctx, CJ, &st);
   if (!dc) return st;
   launch_cca(dc, 1, w, h, ctx->dev_err, s);
   SB_LAUNCHED(ctx, 2);
-  launch_cc_filter(dc, 1, w, h, s);
+  launch_cc_filter(dc, 1, w, h, ctx->dev_err, s);
   SB_LAUNCHED(ctx, 6);
   return SB_OK;
 }
@@ -1120,6 +1126,30 @@ sb_status sb_selective_blur(sb_context* ctx, const uint8_t* rgb, const uint16_t*
   if (!d) return st;
   launch_blur(d, 1, w, h, R, ctx->blur_by_override > 0 ? ctx->blur_by_override : 112, ctx->stream);
   SB_LAUNCHED(ctx, 1);
+  return SB_OK;
+}
+
+sb_status sb_set_host_chunk(sb_context* ctx, size_t first_bytes, size_t max_bytes) {
+  if (!ctx) return SB_ERR_INVALID_ARG;
+  if (first_bytes == 0 && max_bytes == 0) {
+    ctx->host_first = (size_t)256 << 20;
+    ctx->host_cap = (size_t)3072 << 20;
+    return SB_OK;
+  }
+  if (first_bytes == 0 || max_bytes < first_bytes)
+    return fail(ctx, SB_ERR_INVALID_ARG, "host chunk sizes: need 0 < first_bytes <= max_bytes (got %zu, %zu)",
+                first_bytes, max_bytes);
+  ctx->host_first = first_bytes;
+  ctx->host_cap = max_bytes;
+  return SB_OK;
+}
+
+int32_t sb_host_io_chunks(const sb_context* ctx) { return ctx ? ctx->host_chunks : 0; }
+
+sb_status sb_set_union_limit(sb_context* ctx, int32_t limit) {
+  if (!ctx) return SB_ERR_INVALID_ARG;
+  if (limit < 0) return fail(ctx, SB_ERR_INVALID_ARG, "union limit must be >= 0 (0: the default), got %d", limit);
+  ctx->union_limit = limit == 0 ? kUnionLimitDefault : limit;
   return SB_OK;
 }
 
@@ -1281,9 +1311,9 @@ sb_status run_host_io(sb_context* ctx, const sb_pair* pairs, int n, bool batched
   } else {
     std::vector<std::pair<int, int>> head, tail;
     int lo = 0, hi = n;
-    const size_t cap = (size_t)3072 << 20;
+    const size_t cap = ctx->host_cap;
     for (int k = 0; lo < hi; ++k) {
-      const size_t target = std::min(cap, ((size_t)256 << 20) << std::min(k, 8));
+      const size_t target = std::min(cap, ctx->host_first << std::min(k, 8));
       size_t acc = 0;
       const int a = lo;
       while (lo < hi && (acc < target || lo == a)) acc += (size_t)pairs[lo].w * pairs[lo].h * 6, ++lo;
@@ -1297,6 +1327,7 @@ sb_status run_host_io(sb_context* ctx, const sb_pair* pairs, int n, bool batched
     chunks = head;
     chunks.insert(chunks.end(), tail.rbegin(), tail.rend());
   }
+  ctx->host_chunks = (int)chunks.size();
   // staging per slot: left, right, out_rgb, out_disp for the largest chunk
   size_t slot = 0;
   for (auto& c : chunks) {

@@ -16,8 +16,10 @@
 
 namespace sb {
 
-// Device-side error word (bit flags) written by bounded waits and checks.
-enum : uint32_t { DEV_ERR_CCA_ITER = 1u, DEV_ERR_SAD_RANGE = 2u, DEV_ERR_TIMEOUT = 4u };
+// Device-side error word (bit flags) written by bounded loops: the
+// connected-components union-find gave up after its link / retry limit.
+enum : uint32_t { DEV_ERR_CCA_ITER = 1u };
+constexpr int kUnionLimitDefault = 1 << 22;   // parent links and union retries (sb_set_union_limit)
 
 // ---------------------------------------------------------------- lightness
 struct LightJob {
@@ -78,9 +80,11 @@ struct CcaJob {
   int32_t w, h;
   int32_t shist_len;
   double frac;
+  int32_t union_limit;   // most parent links one root search follows, and attempts of one union
 };
+// A union-find search or union that reaches the limit sets DEV_ERR_CCA_ITER in *dev_err.
 void launch_cca(const CcaJob* jobs, int n_jobs, int max_w, int max_h, uint32_t* dev_err, cudaStream_t s);
-void launch_cc_filter(const CcaJob* jobs, int n_jobs, int max_w, int max_h, cudaStream_t s);
+void launch_cc_filter(const CcaJob* jobs, int n_jobs, int max_w, int max_h, uint32_t* dev_err, cudaStream_t s);
 
 // ---------------------------------------------------------------------- SAD
 struct SadJob {

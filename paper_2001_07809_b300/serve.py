@@ -15,6 +15,11 @@ fills; a client that is done with a result hands its buffers back with
 ``Server.recycle`` so that steady-state serving pins no new host memory (a
 fresh pinned allocation costs milliseconds and holds the interpreter lock).
 
+The scheduler never polls: it sleeps on a condition variable that new
+requests and batch completions signal (one waiter thread per stream blocks
+on its batch's completion event).  ``Server.cancel`` drops a request that is
+still waiting for admission.
+
 The pipeline is deterministic per pair, so a request's result does not depend
 on what it was batched with.
 """
@@ -22,6 +27,7 @@ from __future__ import annotations
 
 import collections
 import concurrent.futures as cf
+import queue as _queue
 import threading
 import time
 from typing import Dict, List, Tuple
@@ -65,8 +71,14 @@ class Server:
         self.running = True
         self.completed: List[Tuple[float, float]] = []   # (arrival, done) per finished request
         self.batches = 0
+        self.cancelled = 0
         self._free: Dict[Tuple[int, int], list] = collections.defaultdict(list)
         self._free_lock = threading.Lock()
+        self._ready: collections.deque = collections.deque()   # streams whose batch has completed
+        self._events = [_queue.Queue() for _ in range(n_streams)]
+        self.waiters = [threading.Thread(target=self._wait_loop, args=(i,), daemon=True) for i in range(n_streams)]
+        for t in self.waiters:
+            t.start()
         self.thread = threading.Thread(target=self._loop, daemon=True)
         self.thread.start()
 
@@ -83,11 +95,27 @@ class Server:
             self.cv.notify()
         return req.future
 
+    def cancel(self, future: cf.Future) -> bool:
+        """Drop the request of ``future`` if it is still waiting for admission
+        (the future is then cancelled); False once it is admitted or done."""
+        with self.cv:
+            for r in self.queue:
+                if r.future is future:
+                    self.queue.remove(r)
+                    self.cancelled += 1
+                    r.future.cancel()
+                    return True
+        return False
+
     def close(self):
         with self.cv:
             self.running = False
             self.cv.notify()
         self.thread.join()
+        for q in self._events:
+            q.put(None)
+        for t in self.waiters:
+            t.join()
         for c in self.ctxs:
             c.close()
 
@@ -149,17 +177,40 @@ class Server:
             ev.record(s)
         self.busy[i] = (ev, reqs, keep)
         self.batches += 1
+        self._events[i].put(ev)
+
+    def _wait_loop(self, i: int):
+        # blocks (without the interpreter lock) until stream i's batch is done
+        while True:
+            ev = self._events[i].get()
+            if ev is None:
+                return
+            try:
+                ev.synchronize()
+            except Exception:   # a failed batch: _finish reports the error on its requests
+                pass
+            with self.cv:
+                self._ready.append(i)
+                self.cv.notify()
+
+    def _admissible(self) -> bool:
+        return bool(self.queue) and self.used + self.queue[0].bytes <= self.budget
 
     def _loop(self):
         while True:
             with self.cv:
-                if not self.running and not self.queue and all(b is None for b in self.busy):
-                    return
-            for i, b in enumerate(self.busy):
-                if b is not None and b[0].query():
-                    self._finish(i)
+                while True:
+                    free = any(b is None for b in self.busy)
+                    if self._ready or (free and self._admissible()):
+                        break
+                    if not self.running and not self.queue and all(b is None for b in self.busy):
+                        return
+                    self.cv.wait()
+                ready = list(self._ready)
+                self._ready.clear()
+            for i in ready:
+                self._finish(i)
             free = [i for i, b in enumerate(self.busy) if b is None]
-            launched = False
             if free:
                 with self.cv:
                     batch = []
@@ -169,14 +220,6 @@ class Server:
                         batch.append(r)
                 if batch:
                     self._launch(free[0], batch)
-                    launched = True
-            if not launched:
-                with self.cv:
-                    if self.running and not self.queue:
-                        self.cv.wait(timeout=0.0005)
-                    elif not free:
-                        pass
-                time.sleep(0.0001)
 
 
 def percentile(vals, q):

@@ -145,6 +145,57 @@ def test_cca_long_snake_spans_many_tiles(ctx):
     assert np.array_equal(ref, o_ref) and np.array_equal(lab, o_lab)
 
 
+def _snake_labels():
+    h, w = 130, 200
+    b = np.zeros((h, w), np.uint8)
+    for y in range(0, h, 4):
+        b[y, :] = 1
+        b[y:y + 4, (w - 1) if (y // 4) % 2 == 0 else 0] = 1
+    return b
+
+
+def test_union_limit_reports_timeout_then_recovers():
+    # a union-find bound of one parent link cannot label the snake (its chains
+    # cross many tiles): the run is flagged and sb_synchronize reports
+    # SB_ERR_TIMEOUT; with the default bound the same context labels it exactly
+    labels = _snake_labels()
+    with sb.Context(0) as c:
+        c.set_union_limit(1)
+        refine(c, labels)
+        with pytest.raises(sb.SbError) as ei:
+            c.synchronize()
+        assert ei.value.status == sb.SB_ERR_TIMEOUT and "union" in str(ei.value)
+        c.synchronize()                       # the flag was cleared
+        c.set_union_limit(0)
+        ref, lab, _ = refine(c, labels)
+        c.synchronize()
+        o_ref = oracle.refine(oracle.boundary(labels), 0)
+        assert np.array_equal(ref, o_ref) and np.array_equal(lab, oracle.cca(o_ref)[0])
+        with pytest.raises(sb.SbError) as ei:
+            c.set_union_limit(-1)
+        assert ei.value.status == sb.SB_ERR_INVALID_ARG
+
+
+def test_workspace_budget_reports_oom_and_context_stays_usable():
+    # a 1 MB budget cannot hold a 320x240 pair's workspace (about 18 bytes per
+    # pixel): sb_run returns SB_ERR_OOM; a pair that fits
+    # then runs on the same context and matches the oracle
+    sc, p, _ = synth.workload("c1")
+    left, right, _ = sc.render()
+    with sb.Context(0, mem_budget_bytes=1 << 20) as c:
+        with pytest.raises(sb.SbError) as ei:
+            run_pairs(c, [(left, right, p)], sb.SB_RUN_BATCHED)
+        assert ei.value.status == sb.SB_ERR_OOM
+        r = synth.Rng(321)
+        w, h, D = 160, 96, 16
+        small = synth.Scene(w, h, synth._c2_style_layers(r, w, h, D, contrast=60), noise_q8=256, noise_seed=r.u64())
+        sl, sr, _ = small.render()
+        ps = synth.Params(k=4, max_disp=D, block=7, sigma=2.0, ranges=[(8, D)])
+        (o_rgb, o_disp), = run_pairs(c, [(sl, sr, ps)], sb.SB_RUN_BATCHED)
+        assert c.workspace_bytes() <= 1 << 20
+        _compare_full(o_rgb, o_disp, sl, sr, ps)
+
+
 # ------------------------------------------------------------------------ SAD
 SAD_CASES = [
     # (h, w, D, B)
@@ -538,6 +589,47 @@ def test_host_io_equals_device(ctx):
         ctx.synchronize()
         assert np.array_equal(ho.numpy(), d_rgb)
         assert np.array_equal(hd.numpy().view(np.uint16), d_disp)
+
+
+def test_host_io_batched_across_chunks_and_slots(ctx):
+    # twelve mixed pairs streamed from pinned host memory in chunks that ramp from
+    # 1 MB to 4 MB of inputs: six chunks, so every one of the three staging slots is
+    # used twice, with uploads, compute and downloads of different chunks in flight
+    # together; every pair equals the device-resident batched run, and two are
+    # checked against the oracle
+    from gpu_helpers import params_of
+    items = []
+    for i in range(12):
+        w, h = (640, 480) if i % 3 else (320, 240)
+        D, B = (32, 9) if i % 2 else (48, 15)
+        r = synth.Rng(700 + i)
+        sc = synth.Scene(w, h, synth._c2_style_layers(r, w, h, D, contrast=60), noise_q8=256, noise_seed=r.u64())
+        left, right, _ = sc.render()
+        items.append((left, right, synth.Params(k=4 + i % 3, max_disp=D, block=B, sigma=1.5 + i % 4,
+                                                ranges=[(D // 3, D)])))
+    want = run_pairs(ctx, items, sb.SB_RUN_BATCHED)
+    ctx.set_host_chunk(1 << 20, 4 << 20)
+    try:
+        pairs, outs = [], []
+        for left, right, p in items:
+            hl, hr = torch.from_numpy(left).pin_memory(), torch.from_numpy(right).pin_memory()
+            ho = torch.empty(left.shape, dtype=torch.uint8).pin_memory()
+            hd = torch.empty(left.shape[:2], dtype=torch.int16).pin_memory()
+            pairs.append(sb.Pair(hl, hr, params_of(p), ho, hd))
+            outs.append((ho, hd))
+        sb.sb_run(ctx, pairs, sb.SB_RUN_HOST_IO | sb.SB_RUN_BATCHED)
+        ctx.synchronize()
+        assert ctx.host_io_chunks() == 6
+        for (ho, hd), (w_rgb, w_disp) in zip(outs, want):
+            assert np.array_equal(ho.numpy(), w_rgb)
+            assert np.array_equal(hd.numpy().view(np.uint16), w_disp)
+        for i in (0, 7):
+            left, right, p = items[i]
+            _compare_full(outs[i][0].numpy(), outs[i][1].numpy().view(np.uint16), left, right, p)
+    finally:
+        ctx.set_host_chunk(0, 0)
+    with pytest.raises(sb.SbError):
+        ctx.set_host_chunk(4 << 20, 1 << 20)
 
 
 def test_invalid_arguments_raise(ctx):

@@ -69,6 +69,24 @@ def test_budget_rejects_oversized_request_and_keeps_serving():
     assert out_rgb.shape == left.shape
 
 
+def test_cancel_drops_a_waiting_request():
+    # a budget that admits one request at a time keeps the later ones queued:
+    # the last one is cancelled while it waits, the others complete, and the
+    # server keeps serving
+    reqs = _requests(4)
+    srv = Server(0, mem_budget_bytes=request_bytes(720, 1280) + 1000, max_batch=4)
+    pinned = [(torch.from_numpy(l).pin_memory(), torch.from_numpy(r).pin_memory(), params_of(p)) for l, r, p in reqs]
+    futs = [srv.submit(*q) for q in pinned]
+    assert srv.cancel(futs[-1]) and futs[-1].cancelled()
+    for f in futs[:-1]:
+        f.result(timeout=120)
+    assert not srv.cancel(futs[0])          # already done
+    g = srv.submit(*pinned[0])
+    g.result(timeout=120)
+    srv.close()
+    assert srv.cancelled == 1 and len(srv.latencies()) == len(reqs)
+
+
 @pytest.mark.slow
 def test_c5_sample_alone_and_in_the_mix():
     # 50 requests of the serving stream (mixed sizes, disparity ranges,

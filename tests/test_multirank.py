@@ -45,3 +45,31 @@ def test_two_gloo_ranks_shard_frames_and_take_the_slowest_step():
     assert (a0, b0, a1, b1) == (0, 249, 250, 499)        # disjoint consecutive frames
     assert m0 == m1 == 125.0                            # both ranks see the slowest step
     assert v0 == v1 == pytest.approx(500 / 0.125)       # 500 pairs over 125 ms
+
+
+def _bench(*args):
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    return subprocess.run([sys.executable, os.path.join(root, "bench.py")] + list(args), capture_output=True,
+                          text=True, timeout=300, env=env)
+
+
+def test_bench_gpus_2_launches_two_ranks_through_torchrun():
+    # bench.py --gpus 2 without a torchrun environment re-runs itself as two
+    # ranks (torch.distributed.run, 127.0.0.1); the dry run does the ranks'
+    # bookkeeping over gloo on CPU
+    import json
+    r = _bench("--gpus", "2", "--pairs", "3", "--rank-dry-run")
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+    assert line["n_gpus"] == 2 and line["frames"] == [[0, 1, 2], [3, 4, 5]]
+    assert line["ms_per_step"] == 110.0 and line["value"] == pytest.approx(6 / 0.110)
+
+
+def test_bench_gpus_n_needs_n_visible_gpus():
+    import torch
+    n = max(2, torch.cuda.device_count() + 1)
+    r = _bench("--gpus", str(n), "--steps", "1")
+    assert r.returncode == 2 and "needs %d visible GPUs" % n in r.stderr
