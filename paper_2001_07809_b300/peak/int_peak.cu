@@ -37,6 +37,12 @@ __global__ void __launch_bounds__(256) k_peak(uint32_t* out, uint32_t seed) {
       if (OP == 2) asm volatile("fma.rn.f32 %0, %0, %1, %1;" : "+f"(f[i]) : "f"(fb));
       if (OP == 3) asm volatile("prmt.b32 %0, %0, %1, 0x5140;" : "+r"(a[i]) : "r"(b[i]));
       if (OP == 4) asm volatile("fma.rn.f32x2 %0, %0, %1, %1;" : "+l"(f2[i]) : "l"(fb2));
+      if (OP == 5) asm volatile("shf.r.wrap.b32 %0, %0, %1, %2;" : "+r"(a[i]) : "r"(b[i]), "r"(c & 24u));
+      if (OP == 6) asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a[i]) : "r"(b[i]), "r"(c));
+      if (OP == 7) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a[i]) : "r"(b[i]), "r"(c));
+      if (OP == 8) asm volatile("mad.hi.u32 %0, %0, %1, %2;" : "+r"(a[i]) : "r"(b[i]), "r"(c));
+      if (OP == 9) asm volatile("redux.sync.min.u32 %0, %1, 0xffffffff;" : "=r"(a[i]) : "r"(a[i] ^ b[i]));
+      if (OP == 10) asm volatile("vabsdiff4.u32.u32.u32 %0.b20, %0, %1, %0;" : "+r"(a[i]) : "r"(b[i]));
     }
   }
   uint32_t s = 0;
@@ -64,9 +70,11 @@ int time_op(int blocks, uint32_t* out, double* per_s) {
 }
 }  // namespace
 
-// rates[0..4]: thread-instructions per second of add.u32, vabsdiff4 (4 byte
-// cells each), fma.f32, prmt and fma.f32x2 (two FMAs each) on the current
-// device.  Returns 0 on success.
+// rates[0..10]: thread-instructions per second of add.u32, vabsdiff4 (4 byte
+// cells each), fma.f32, prmt, fma.f32x2 (two FMAs each), shf.r.wrap, lop3,
+// mad.lo.u32, mad.hi.u32, redux.sync.min.u32 (per participating thread) and
+// vabsdiff4 with a destination byte mask, on the current device.  Returns 0
+// on success.
 extern "C" int sb_peak_measure(double* rates) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
@@ -79,6 +87,12 @@ extern "C" int sb_peak_measure(double* rates) {
   rc |= time_op<2>(blocks, out, &rates[2]);
   rc |= time_op<3>(blocks, out, &rates[3]);
   rc |= time_op<4>(blocks, out, &rates[4]);
+  rc |= time_op<5>(blocks, out, &rates[5]);
+  rc |= time_op<6>(blocks, out, &rates[6]);
+  rc |= time_op<7>(blocks, out, &rates[7]);
+  rc |= time_op<8>(blocks, out, &rates[8]);
+  rc |= time_op<9>(blocks, out, &rates[9]);
+  rc |= time_op<10>(blocks, out, &rates[10]);
   cudaFree(out);
   return rc;
 }
