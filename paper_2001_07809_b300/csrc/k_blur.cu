@@ -319,7 +319,7 @@ constexpr int kMaxSteps = kBandRows / kSB;
 constexpr int kChPad = 4;
 
 struct StripGeo {
-  int nt, F, M, iw, sr, h_off, in_off, bytes;
+  int nt, F, M, iw, sr, h_off, in_off, out_off, bytes;
 };
 // F: filtered rows one step reads (2R + kSB + 1); M: ring rows, F rounded up
 // to a multiple of OB so that a block of OB consecutive ring rows starting at
@@ -334,7 +334,8 @@ __host__ __device__ inline StripGeo strip_geo(int R) {
   g.h_off = ((g.nt + 3) & ~3) * 4;                                   // taps first
   g.in_off = (g.h_off + (3 * g.M * HS + 2 * kChPad) * 4 + 15) & ~15;  // then the ring, 3 channels (cp.async
                                                                      // destinations need 16-byte alignment)
-  g.bytes = g.in_off + 2 * kSB * g.sr;                               // then two input buffers
+  g.out_off = g.in_off + 2 * kSB * g.sr;                             // then two input buffers
+  g.bytes = g.out_off + kSB * BX * 3;                                // then one step's output rows
   return g;
 }
 }  // namespace
@@ -402,10 +403,18 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
   float* s_tap = fsm;
   float* s_h = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(fsm) + G.h_off);
   uint8_t* s_in = reinterpret_cast<uint8_t*>(fsm) + G.in_off;
+  uint8_t* s_out = reinterpret_cast<uint8_t*>(fsm) + G.out_off;   // one step's output rows (BX * 3 bytes each)
   const int xs = tx0 - R;
   const bool interior = xs >= 0 && xs + iw <= w;
   const int64_t nbytes = (int64_t)w * h * 3;
   const bool fast = interior && ((reinterpret_cast<uintptr_t>(J.rgb) & 15) == 0);
+  // whole strips of a 16-byte aligned image whose rows are multiples of 16 bytes: a step's
+  // output rows are assembled in shared memory (original rows copied in, blurred bytes
+  // written over them) and stored 16 bytes at a time
+  const bool vout = ox == BX && ((w * 3) & 15) == 0 &&
+                    ((reinterpret_cast<uintptr_t>(J.rgb) | reinterpret_cast<uintptr_t>(J.out)) & 15) == 0;
+  constexpr int kRowChunks = BX * 3 / 16;   // 16-byte chunks of an output row
+  static_assert(kSB * kRowChunks == kStripThreads, "one output chunk per thread and step");
   if (tid < 8) { s_lo[tid] = jobs[blockIdx.z].lo[tid]; s_hi[tid] = jobs[blockIdx.z].hi[tid]; }
   for (int t = tid; t < nt; t += kStripThreads) s_tap[t] = J.taps[t];
   __syncthreads();
@@ -457,6 +466,14 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
   int any_step = 0;
   for (int st = 0; st < nsteps; ++st) any_step |= s_flag[st];
   if (!any_step) {   // nothing to blur in the band: copy it
+    if (vout) {
+      for (int c = tid; c < rows * kRowChunks; c += kStripThreads) {
+        const int i = c / kRowChunks, q = c - i * kRowChunks;
+        const int64_t at = ((int64_t)(yb0 + i) * w + tx0) * 3 + 16 * q;
+        *reinterpret_cast<uint4*>(J.out + at) = *reinterpret_cast<const uint4*>(J.rgb + at);
+      }
+      return;
+    }
     for (int i = warp; i < rows; i += kWarps) {
       const int64_t row = ((int64_t)(yb0 + i) * w + tx0) * 3;
       for (int b = lane; b < ox * 3; b += 32) J.out[row + b] = J.rgb[row + b];
@@ -511,6 +528,15 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
     asm volatile("cp.async.commit_group;\n" ::);
   };
   auto slot = [&](int y) { return (y - (yb0 - R)) % M; };   // ring row of image row y >= yb0 - R
+  // vout: the original rows of step st into s_out, as a cp.async group of its own
+  // (committed before the next horizontal batch's group, so that waiting for all
+  // groups but the newest completes it while that batch is still in flight)
+  auto prefetch = [&](int st) {
+    const int ys = yb0 + kSB * st, nrow = min(kSB, rows - kSB * st);
+    const int i = tid / kRowChunks, q = tid - i * kRowChunks;
+    if (i < nrow) cp_async16(s_out + i * (BX * 3) + 16 * q, J.rgb + ((int64_t)(ys + i) * w + tx0) * 3 + 16 * q);
+    asm volatile("cp.async.commit_group;\n" ::);
+  };
   auto hpass = [&](int k, int buf) {
     const int a = batch_row0(k), n = batch_rows(k);
     const uint8_t* base = s_in + buf * kSB * sr;
@@ -529,10 +555,13 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
   for (int k = 0; k < nfill; ++k) {
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
+    if (vout && k == nfill - 1) prefetch(0);
     if (k + 1 < nbatch) stage(k + 1, (k + 1) & 1);
+    else if (vout && k == nfill - 1) asm volatile("cp.async.commit_group;\n" ::);   // (an empty group)
     hpass(k, k & 1);
   }
   for (int st = 0; st < nsteps; ++st) {
+    if (vout) asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // this step's original rows
     __syncthreads();   // the ring holds every row step st reads
     const int ys = yb0 + kSB * st, nrow = min(kSB, rows - kSB * st);
     if (s_flag[st]) {
@@ -542,7 +571,16 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
       const int b0 = slot(ys + i0 - R);
       float acc[OB];
       conv16_ring(acc, s_tap, nt, s_h + ch * (M * HS + kChPad) + col, b0, M);
-      if (col < ox) {
+      if (vout) {
+#pragma unroll
+        for (int o = 0; o < OB; ++o) {
+          const int i = i0 + o;
+          if (i < nrow && ((s_mbits[((kSB * st + i) * BX + col) >> 5] >> (col & 31)) & 1u)) {
+            const int q = __float2int_rd(acc[o] + 0.5f);
+            s_out[i * (BX * 3) + col * 3 + ch] = (uint8_t)min(max(q, 0), 255);
+          }
+        }
+      } else if (col < ox) {
 #pragma unroll
         for (int o = 0; o < OB; ++o) {
           const int i = i0 + o;
@@ -560,17 +598,26 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
           }
         }
       }
-    } else {
+    } else if (!vout) {
       for (int i = warp; i < nrow; i += kWarps) {
         const int64_t row = ((int64_t)(ys + i) * w + tx0) * 3;
         for (int b = lane; b < ox * 3; b += 32) J.out[row + b] = J.rgb[row + b];
       }
     }
+    if (vout) {
+      __syncthreads();   // the step's blurred bytes are in s_out
+      const int i = tid / kRowChunks, q = tid - i * kRowChunks;
+      if (i < nrow)
+        *reinterpret_cast<uint4*>(J.out + ((int64_t)(ys + i) * w + tx0) * 3 + 16 * q) =
+            *reinterpret_cast<const uint4*>(s_out + i * (BX * 3) + 16 * q);
+    }
     const int k = nfill + st;   // the batch step st + 1 reads first
     if (k < nbatch) {
       asm volatile("cp.async.wait_group 0;\n" ::: "memory");
       __syncthreads();   // batch k staged; every vertical read of the ring slots it replaces is done
+      if (vout) prefetch(st + 1);   // s_out was stored before the barrier
       if (k + 1 < nbatch) stage(k + 1, (k + 1) & 1);
+      else if (vout) asm volatile("cp.async.commit_group;\n" ::);   // (an empty group)
       if (batch_needed(k)) hpass(k, k & 1);
     }
   }
