@@ -1,12 +1,18 @@
 // Connected components analysis and small-component removal (Section III).
 //
-// Labelling (8-connectivity) is union-find: a warp labels each 32x32 tile by
-// sweeping its rows in order with one node per horizontal run (in shared
-// memory), then pixels on tile borders unite across tiles in global memory,
-// then every tile-local root is chased to its component root while the sizes
-// are counted.  Unions always hang the larger root under the smaller
-// (atomicMin), so a component's final root is its smallest linear index: the
-// same label a raster-order flood fill gives.
+// Labelling (8-connectivity) is union-find at two levels.  A warp labels each
+// 32x32 tile in shared memory, sweeping its rows in order with one node per
+// horizontal run, and writes every pixel's tile-local root as a 16-bit index
+// (y * 32 + x within the tile, 0xFFFF off the map).  Only the tile-local roots
+// have a node in the image-level forest: at the linear index g of a local
+// root, J.node[2g] is its parent and J.node[2g + 1] the component's size once g
+// is a component root; no other slot is read or written, so nothing has to
+// clear the table.  Pixels on tile borders then unite the nodes of their local
+// roots across tiles, and every local root is chased to its component root
+// while the sizes are counted.  Unions always hang the larger root under the
+// smaller (atomicMin), and a local root is the smallest index of its piece of
+// the tile, so a component's final root is its smallest linear index: the same
+// label a raster-order flood fill gives.
 //
 // Removal: the components are ordered by (size, label) and the longest
 // prefix holding at most floor(frac * N_b) pixels is removed.  On the device
@@ -15,21 +21,35 @@
 // of component sizes, and the cut label T found from per-row counts; both
 // counts run over the list of roots rather than over every pixel.  No host
 // round-trip, so the whole sequence can be captured in a CUDA graph.
+//
+// Traffic per pixel: the map is read once (1 byte), the 16-bit labels are
+// written once and read twice (counting, filtering), the filtered map is
+// written once (1 byte); the node table is touched at local roots only.
 #include <algorithm>
 #include "sb_common.cuh"
 
 namespace sb {
 
 namespace {
-constexpr int CT = 32;                 // CCA tile side
+constexpr int CT = 32;                  // CCA tile side
+constexpr uint16_t kOffMap = 0xFFFF;    // tile-local label of a pixel off the map
+
+// Parent of node x: P[x] in a tile's shared-memory forest (S = 1), P[2x] in
+// the image-level node table (S = 2).
+template <int S>
+__device__ __forceinline__ int* parent_of(int* P, int x) {
+  if constexpr (S == 1) return P + x;
+  else return P + 2 * (int64_t)x;
+}
 
 // Root of x: follows at most `limit` parent links (CcaJob::union_limit); a
 // chain that is longer clears ok (the run is reported as SB_ERR_TIMEOUT) and
 // returns the node reached.  Every link points to a smaller index, so the walk
 // always stays inside the image and ends.
-__device__ __forceinline__ int find_root(const int* P, int x, int limit, bool& ok) {
+template <int S>
+__device__ __forceinline__ int find_root(int* P, int x, int limit, bool& ok) {
   for (int guard = 0;; ++guard) {
-    const int p = P[x];
+    const int p = *parent_of<S>(P, x);
     if (p == x) return x;
     if (guard >= limit) {
       ok = false;
@@ -41,37 +61,56 @@ __device__ __forceinline__ int find_root(const int* P, int x, int limit, bool& o
 
 // Lock-free union (both roots hang the larger index under the smaller), at
 // most `limit` attempts.
+template <int S>
 __device__ __forceinline__ bool unite(int* P, int a, int b, int limit, bool& ok) {
   for (int it = 0; it < limit; ++it) {
-    a = find_root(P, a, limit, ok);
-    b = find_root(P, b, limit, ok);
+    a = find_root<S>(P, a, limit, ok);
+    b = find_root<S>(P, b, limit, ok);
     if (a == b) return true;
     if (a < b) {
-      int old = atomicMin(&P[b], a);
+      int old = atomicMin(parent_of<S>(P, b), a);
       if (old == b) return true;
       b = old;
     } else {
-      int old = atomicMin(&P[a], b);
+      int old = atomicMin(parent_of<S>(P, a), b);
       if (old == a) return true;
       a = old;
     }
   }
   return false;
 }
+
+// Bit i set when byte i of v is nonzero (i = 0..3): the high bit of each
+// nonzero byte is gathered by a carry-free multiply.
+__device__ __forceinline__ unsigned nz_bits(unsigned v) {
+  const unsigned t = (((v & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | v) & 0x80808080u;
+  return ((t >> 7) * 0x01020408u) >> 24;
+}
+
+// Linear index of the local root named by label li of pixel (x, y).
+__device__ __forceinline__ int64_t local_root_at(int x, int y, int li, int w) {
+  return (int64_t)((y & ~(CT - 1)) + (li >> 5)) * w + (x & ~(CT - 1)) + (li & (CT - 1));
+}
+
+__device__ __forceinline__ uint32_t comp_size(const CcaJob& J, int64_t r) {
+  return (uint32_t)J.node[2 * r + 1];
+}
 }  // namespace
 
 // Tile-local labelling, one warp per 32x32 tile, rows in order (the classic
 // raster two-pass scheme with a warp holding one row): lane x of the warp is
-// tile column x.  The 32 row masks are ballots of the map (all rows loaded up
-// front); each horizontal run of a row is one union-find node, named by its
-// first pixel (tile-local index y * 32 + start), which is the smallest index
-// of the run.  A run of row y touches the runs of row y - 1 that cross its
-// columns widened by one on each side (8-connectivity); the lane at its start
-// hangs the new node under the root of the first of them and unites that
-// tree with the trees of the others (rare: where two branches meet).  Every
-// link goes from a larger index to a smaller one, so a component's root is
-// its smallest index, the label the raster flood fill gives.  A last pass
-// finds every pixel's root from the row masks and writes the labels.
+// tile column x.  Lane y first holds the mask of tile row y; each horizontal
+// run of a row is one union-find node, named by its first pixel (tile-local
+// index y * 32 + start), which is the smallest index of the run.  A run of row
+// y touches the runs of row y - 1 that cross its columns widened by one on
+// each side (8-connectivity); the lane at its start hangs the new node under
+// the root of the first of them and unites that tree with the trees of the
+// others (rare: where two branches meet).  Every link goes from a larger index
+// to a smaller one, so a piece's root is its smallest index.  A last sweep,
+// again rows in order, finds every pixel's root, writes it as the pixel's
+// label and points each run's node straight at it (so the searches of later
+// rows take one or two links), and gives every local root its node in the
+// image-level table (parent itself, size 0).
 constexpr int kCcaWarps = 8;   // tiles per CTA (along x)
 
 __device__ __forceinline__ int run_start(unsigned mask, int c) {
@@ -88,20 +127,28 @@ __global__ void __launch_bounds__(kCcaWarps * 32) k_cca_local(const CcaJob* __re
   const int w = J.w, h = J.h;
   int* P = s_par[warp];
   const int x = tx0 + lane;
-  // the tile's 32 bytes of column `lane`, then lane y keeps the mask of row y
-  unsigned colbits = 0;
-  {
+  unsigned rowmask = 0;   // lane y: bit c set when pixel (tx0 + c, ty0 + y) is on the map
+  if (tx0 + CT <= w && (w & 15) == 0 && (reinterpret_cast<uintptr_t>(J.b) & 15) == 0) {
+    // whole tile rows: lane y reads its row's 32 bytes as two 16-byte loads
+    if (ty0 + lane < h) {
+      const uint4* row = reinterpret_cast<const uint4*>(J.b + (int64_t)(ty0 + lane) * w + tx0);
+      const uint4 a = row[0], c = row[1];
+      rowmask = nz_bits(a.x) | nz_bits(a.y) << 4 | nz_bits(a.z) << 8 | nz_bits(a.w) << 12 |
+                nz_bits(c.x) << 16 | nz_bits(c.y) << 20 | nz_bits(c.z) << 24 | nz_bits(c.w) << 28;
+    }
+  } else {
+    // ragged tile: the 32 bytes of column `lane`, then one ballot per row
+    unsigned colbits = 0;
     uint8_t v[CT];
 #pragma unroll
     for (int y = 0; y < CT; ++y) v[y] = (x < w && ty0 + y < h) ? J.b[(int64_t)(ty0 + y) * w + x] : (uint8_t)0;
 #pragma unroll
     for (int y = 0; y < CT; ++y) colbits |= (v[y] ? 1u : 0u) << y;
-  }
-  unsigned rowmask = 0;
 #pragma unroll
-  for (int y = 0; y < CT; ++y) {
-    const unsigned m = __ballot_sync(0xffffffffu, (colbits >> y) & 1u);
-    if (lane == y) rowmask = m;
+    for (int y = 0; y < CT; ++y) {
+      const unsigned m = __ballot_sync(0xffffffffu, (colbits >> y) & 1u);
+      if (lane == y) rowmask = m;
+    }
   }
   bool ok = true;
   unsigned prev = 0;
@@ -122,13 +169,13 @@ __global__ void __launch_bounds__(kCcaWarps * 32) k_cca_local(const CcaJob* __re
           P[C] = C;
         } else {
           const int s1 = run_start(prev, __ffs(T) - 1);
-          const int r1 = find_root(P, (y - 1) * CT + s1, J.union_limit, ok);
+          const int r1 = find_root<1>(P, (y - 1) * CT + s1, J.union_limit, ok);
           P[C] = r1;   // r1 < C: the smaller index stays the root
           unsigned others = T & (prev & ~(prev << 1)) & ~(1u << s1);   // starts of the other runs above
           while (others) {
             const int b = __ffs(others) - 1;
             others &= others - 1u;
-            ok &= unite(P, r1, (y - 1) * CT + b, J.union_limit, ok);
+            ok &= unite<1>(P, r1, (y - 1) * CT + b, J.union_limit, ok);
           }
         }
       }
@@ -136,20 +183,33 @@ __global__ void __launch_bounds__(kCcaWarps * 32) k_cca_local(const CcaJob* __re
     }
     prev = cur;
   }
-  // labels: every pixel's root, as a linear index of the image
+  // labels, rows in order (a node another lane is re-pointing still leads to
+  // the same root, whichever value a search reads)
   for (int y = 0; y < CT && ty0 + y < h; ++y) {
     const unsigned cur = __shfl_sync(0xffffffffu, rowmask, y);
-    if (x >= w) continue;
-    int v = -1;
+    uint16_t v = kOffMap;
     if ((cur >> lane) & 1u) {
-      const int root = find_root(P, y * CT + run_start(cur, lane), J.union_limit, ok);
-      v = (ty0 + (root >> 5)) * w + tx0 + (root & (CT - 1));
+      const int C = y * CT + run_start(cur, lane);
+      const int root = find_root<1>(P, C, J.union_limit, ok);
+      v = (uint16_t)root;
+      if (C == y * CT + lane) {   // the run's first lane
+        if (root != C) {
+          P[C] = root;
+        } else {
+          const int64_t g = (int64_t)(ty0 + y) * w + x;
+          reinterpret_cast<int2*>(J.node)[g] = make_int2((int)g, 0);
+        }
+      }
     }
-    J.lab[(int64_t)(ty0 + y) * w + x] = v;
+    if (x < w) J.lab[(int64_t)(ty0 + y) * w + x] = v;
   }
   if (!ok) atomicOr(dev_err, DEV_ERR_CCA_ITER);
 }
 
+// Border merge: every map pixel on a tile's top row or left or right column
+// unites the node of its local root with the node of each 8-neighbour's local
+// root in another tile (neighbours above and to the left; the pixels below and
+// to the right of a border are the next tiles' border pixels).
 constexpr int kMergeTiles = 4;   // tiles per CTA of k_cca_merge (along x)
 __global__ void __launch_bounds__(128) k_cca_merge(const CcaJob* __restrict__ jobs, uint32_t* dev_err) {
   const CcaJob J = jobs[blockIdx.z];
@@ -168,83 +228,59 @@ __global__ void __launch_bounds__(128) k_cca_merge(const CcaJob* __restrict__ jo
     else continue;
     const int x = tx0 + lx, y = ty0 + ly;
     if (x >= w || y >= h) continue;
-    const int p = y * w + x;
-    if (!J.b[p]) continue;
+    const int lp = J.lab[(int64_t)y * w + x];
+    if (lp == kOffMap) continue;
+    const int a = (int)local_root_at(x, y, lp, w);
     const int nx[4] = {x - 1, x - 1, x, x + 1}, ny[4] = {y, y - 1, y - 1, y - 1};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int qx = nx[k], qy = ny[k];
       if (qx < 0 || qy < 0 || qx >= w) continue;
       if (qx >= tx0 && qx < tx0 + CT && qy >= ty0) continue;  // same tile: done locally
-      const int q = qy * w + qx;
-      if (J.b[q]) ok &= unite(J.lab, p, q, J.union_limit, ok);
+      const int lq = J.lab[(int64_t)qy * w + qx];
+      if (lq != kOffMap) ok &= unite<2>(J.node, a, (int)local_root_at(qx, qy, lq, w), J.union_limit, ok);
     }
   }
   if (!ok) atomicOr(dev_err, DEV_ERR_CCA_ITER);
 }
 
-// Final labels and component sizes.  After the tile labelling every pixel's
-// label is its tile-local root; the border merge then re-points some of those
-// roots (to a root in this tile or another).  So a pixel p's local root u is
-// its label when that lies in the tile, else p itself (a local root whose
-// label the merge changed to another tile).  A 32x32 tile counts its pixels
-// per local root in shared memory, then only the referenced local roots
-// follow their parent chains in global memory (one to a few hops) to the
-// component root R, add their counts to size[R] and, when a local root is R
-// itself, append it to the job's root list; a last pass writes R as every
-// pixel's label.  The tile's boundary pixels are added to N_b.
-__device__ __forceinline__ int tile_local(int v, int base, int w, float inv_w) {
-  const int d = v - base;   // v = base + dy * w + dx for a pixel of the tile
-  if (d < 0) return -1;
-  int dy = (int)((float)d * inv_w);
-  if (dy * w > d) --dy;
-  else if ((dy + 1) * w <= d) ++dy;   // exact for dy < 32, where it matters
-  if (dy >= CT) return -1;
-  const int dx = d - dy * w;
-  return dx < CT && dx < w ? dy * CT + dx : -1;
-}
-
+// Component sizes.  A 32x32 tile counts its pixels per local root in shared
+// memory; then each local root some pixel refers to follows its parent chain
+// in the node table (one to a few links) to the component root R, adds its
+// count to R's size, points its own node straight at R (so the filter needs
+// one link) and, when it is R itself, appends R to the job's root list.  The
+// tile's map pixels are added to N_b.
 constexpr int kCountTiles = 2;   // tiles per CTA of k_cc_count (along x)
 __global__ void __launch_bounds__(256) k_cc_count(const CcaJob* __restrict__ jobs, uint32_t* dev_err) {
   constexpr int kPer = CT * CT / 256;   // pixels per thread and tile
   __shared__ unsigned s_cnt[kCountTiles][CT * CT];   // pixels per local root
-  __shared__ int s_root[kCountTiles][CT * CT];       // component root of each referenced local root
   __shared__ unsigned s_total;
   const CcaJob J = jobs[blockIdx.z];
   const int w = J.w, h = J.h;
   const int ty0 = blockIdx.y * CT;
   if (blockIdx.x * kCountTiles * CT >= w || ty0 >= h) return;
-  const float inv_w = 1.0f / (float)w;
   for (int i = threadIdx.x; i < kCountTiles * CT * CT; i += blockDim.x) (&s_cnt[0][0])[i] = 0u;
   if (threadIdx.x == 0) s_total = 0;
-  __syncthreads();
-  int u[kCountTiles][kPer], v[kCountTiles][kPer];
-  unsigned mine = 0;
-  bool ok = true;
+  int li[kCountTiles][kPer];
 #pragma unroll
   for (int tt = 0; tt < kCountTiles; ++tt)
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       const int i = threadIdx.x + 256 * k;
       const int x = (blockIdx.x * kCountTiles + tt) * CT + (i & (CT - 1)), y = ty0 + (i >> 5);
-      v[tt][k] = (x < w && y < h) ? J.lab[(int64_t)y * w + x] : -1;
+      li[tt][k] = (x < w && y < h) ? J.lab[(int64_t)y * w + x] : kOffMap;
     }
+  __syncthreads();
+  unsigned mine = 0;
+  bool ok = true;
 #pragma unroll
-  for (int tt = 0; tt < kCountTiles; ++tt) {
-    const int tx0 = (blockIdx.x * kCountTiles + tt) * CT;
-    const int base = ty0 * w + tx0;
+  for (int tt = 0; tt < kCountTiles; ++tt)
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      u[tt][k] = -1;
-      if (v[tt][k] >= 0) {
-        const int i = threadIdx.x + 256 * k;
-        const int t = tile_local(v[tt][k], base, w, inv_w);
-        u[tt][k] = t >= 0 ? t : i;
-        atomicAdd(&s_cnt[tt][u[tt][k]], 1u);
+    for (int k = 0; k < kPer; ++k)
+      if (li[tt][k] != kOffMap) {
+        atomicAdd(&s_cnt[tt][li[tt][k]], 1u);
         ++mine;
       }
-    }
-  }
   __syncthreads();
 #pragma unroll
   for (int tt = 0; tt < kCountTiles; ++tt) {
@@ -255,29 +291,16 @@ __global__ void __launch_bounds__(256) k_cc_count(const CcaJob* __restrict__ job
       const unsigned c = s_cnt[tt][i];
       if (c) {   // pixel i is a local root some pixel of the tile refers to
         const int g = (ty0 + (i >> 5)) * w + tx0 + (i & (CT - 1));
-        const int R = find_root(J.lab, g, J.union_limit, ok);
-        s_root[tt][i] = R;
-        atomicAdd(&J.size[R], c);
+        const int R = find_root<2>(J.node, g, J.union_limit, ok);
+        atomicAdd(reinterpret_cast<unsigned*>(&J.node[2 * (int64_t)R + 1]), c);
         if (R == g) J.roots[atomicAdd(reinterpret_cast<unsigned long long*>(&J.cut[5]), 1ull)] = R;
+        else J.node[2 * (int64_t)g] = R;   // another tile's search through g still reaches R
       }
     }
   }
   for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
   if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&s_total, mine);
   __syncthreads();
-#pragma unroll
-  for (int tt = 0; tt < kCountTiles; ++tt) {
-    const int tx0 = (blockIdx.x * kCountTiles + tt) * CT;
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      if (u[tt][k] < 0) continue;
-      const int R = s_root[tt][u[tt][k]];
-      if (R != v[tt][k]) {
-        const int i = threadIdx.x + 256 * k;
-        J.lab[(int64_t)(ty0 + (i >> 5)) * w + tx0 + (i & (CT - 1))] = R;   // other tiles may follow it: R is an ancestor
-      }
-    }
-  }
   if (threadIdx.x == 0 && s_total) atomicAdd(reinterpret_cast<unsigned long long*>(&J.cut[0]), (unsigned long long)s_total);
   if (!ok) atomicOr(dev_err, DEV_ERR_CCA_ITER);
 }
@@ -292,7 +315,7 @@ __global__ void __launch_bounds__(256) k_cc_hist(const CcaJob* __restrict__ jobs
   const int64_t limit = removal_limit(J);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nroots; i += stride) {
-    const uint32_t s = J.size[J.roots[i]];
+    const uint32_t s = comp_size(J, J.roots[i]);
     if ((int64_t)s <= limit && (int64_t)s < J.shist_len) atomicAdd(&J.shist[s], 1u);
   }
 }
@@ -352,7 +375,7 @@ __global__ void __launch_bounds__(256) k_cc_rowcount(const CcaJob* __restrict__ 
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nroots; i += stride) {
     const int v = J.roots[i];
-    if (J.size[v] == sstar) atomicAdd(&J.rowcnt[v / J.w], 1u);
+    if (comp_size(J, v) == sstar) atomicAdd(&J.rowcnt[v / J.w], 1u);
   }
 }
 
@@ -393,11 +416,16 @@ __global__ void __launch_bounds__(1024) k_cc_select(const CcaJob* __restrict__ j
   __syncthreads();
   if (tid < 32 && s_row != INT_MAX) {  // warp 0 walks the row 32 pixels at a time
     long long k = m - s_before;
-    const int64_t base = (int64_t)s_row * J.w;
+    const int y = s_row;
+    const int64_t base = (int64_t)y * J.w;
     for (int x0 = 0; x0 < J.w; x0 += 32) {
       const int x = x0 + tid;
       const int64_t p = base + x;
-      const bool hit = x < J.w && J.lab[p] == (int)p && J.size[p] == sstar;
+      // p is a component root of size s*: a local root (its label names
+      // itself) whose node is its own parent
+      bool hit = false;
+      if (x < J.w && J.lab[p] == (((y & (CT - 1)) << 5) | (x & (CT - 1))))
+        hit = J.node[2 * p] == (int)p && comp_size(J, p) == sstar;
       const unsigned mask = __ballot_sync(0xffffffffu, hit);
       const int c = __popc(mask);
       if (k < c) {
@@ -412,41 +440,77 @@ __global__ void __launch_bounds__(1024) k_cc_select(const CcaJob* __restrict__ j
   }
 }
 
+// The filtered map (and, when asked for, every pixel's component label): a
+// pixel's local root points straight at its component root R after counting,
+// and R's component stays unless it is smaller than s*, or of size s* with a
+// label below T.
 __global__ void __launch_bounds__(256) k_cc_filter(const CcaJob* __restrict__ jobs) {
   const CcaJob J = jobs[blockIdx.y];
-  const int64_t n = (int64_t)J.w * J.h;
+  const int w = J.w, h = J.h;
   const uint32_t sstar = (uint32_t)J.cut[2];
   const long long T = J.cut[4];
-  auto keep = [&](int v) -> uint32_t {
-    if (v < 0) return 0u;
-    const uint32_t sz = J.size[v];
-    return sz < sstar || (sz == sstar && (long long)v < T) ? 0u : 1u;
+  auto comp = [&](int x, int y, int li) -> int { return J.node[2 * local_root_at(x, y, li, w)]; };
+  auto keep = [&](int R) -> uint8_t {
+    const uint32_t sz = comp_size(J, R);
+    return sz < sstar || (sz == sstar && (long long)R < T) ? 0 : 1;
   };
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // four pixels per step (16-byte label loads, one size lookup per distinct
-  // label: neighbours mostly share their root), then the last n % 4 pixels
-  const int64_t n4 = n / 4;
-  const bool vec = ((reinterpret_cast<uintptr_t>(J.lab) | reinterpret_cast<uintptr_t>(J.out)) & 15) == 0;
+  const bool vec = (w & 7) == 0 && ((reinterpret_cast<uintptr_t>(J.lab) | reinterpret_cast<uintptr_t>(J.labels_out)) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(J.out) & 7) == 0;
   if (vec) {
-    for (int64_t q = t0; q < n4; q += stride) {
-      const int4 v = reinterpret_cast<const int4*>(J.lab)[q];
-      const uint32_t k0 = keep(v.x);
-      const uint32_t k1 = v.y == v.x ? k0 : keep(v.y);
-      const uint32_t k2 = v.z == v.y ? k1 : keep(v.z);
-      const uint32_t k3 = v.w == v.z ? k2 : keep(v.w);
-      reinterpret_cast<uint32_t*>(J.out)[q] = k0 | (k1 << 8) | (k2 << 16) | (k3 << 24);
+    // eight pixels of one row per step (one 16-byte label load; neighbours
+    // mostly share their local root, so one lookup serves a run of them)
+    const unsigned cw = (unsigned)w >> 3;
+    const int64_t nq = (int64_t)cw * h;
+    for (int64_t q = t0; q < nq; q += stride) {
+      const unsigned y = (unsigned)q / cw, x0 = ((unsigned)q - y * cw) * 8;
+      const uint4 v = reinterpret_cast<const uint4*>(J.lab)[q];
+      const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
+      uint32_t o[2] = {0u, 0u};
+      int R[8];
+      int prev = -1, prevR = -1;
+      uint8_t prevk = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int li = (int)((wd[j >> 1] >> (16 * (j & 1))) & 0xFFFFu);
+        uint8_t k = 0;
+        R[j] = -1;
+        if (li != kOffMap) {
+          if (li != prev) {
+            prev = li;
+            prevR = comp((int)x0 + j, (int)y, li);
+            prevk = keep(prevR);
+          }
+          R[j] = prevR;
+          k = prevk;
+        }
+        o[j >> 2] |= (uint32_t)k << (8 * (j & 3));
+      }
+      reinterpret_cast<uint2*>(J.out)[q] = make_uint2(o[0], o[1]);
+      if (J.labels_out) {
+        int4* lo = reinterpret_cast<int4*>(J.labels_out) + 2 * q;
+        lo[0] = make_int4(R[0], R[1], R[2], R[3]);
+        lo[1] = make_int4(R[4], R[5], R[6], R[7]);
+      }
+    }
+  } else {
+    const int64_t n = (int64_t)w * h;
+    for (int64_t p = t0; p < n; p += stride) {
+      const int y = (int)(p / w), x = (int)(p - (int64_t)y * w);
+      const int li = J.lab[p];
+      const int R = li == kOffMap ? -1 : comp(x, y, li);
+      J.out[p] = R < 0 ? 0 : keep(R);
+      if (J.labels_out) J.labels_out[p] = R;
     }
   }
-  for (int64_t p = (vec ? 4 * n4 : 0) + t0; p < n; p += stride) J.out[p] = (uint8_t)keep(J.lab[p]);
 }
 
 void launch_cca(const CcaJob* jobs, int n_jobs, int max_w, int max_h, uint32_t* dev_err, cudaStream_t s) {
   if (n_jobs <= 0) return;
-  dim3 tiles((max_w + CT - 1) / CT, (max_h + CT - 1) / CT, n_jobs);
-  const int tiles_x = (max_w + CT - 1) / CT;
-  k_cca_local<<<dim3((tiles_x + kCcaWarps - 1) / kCcaWarps, tiles.y, n_jobs), kCcaWarps * 32, 0, s>>>(jobs, dev_err);
-  k_cca_merge<<<dim3((tiles_x + kMergeTiles - 1) / kMergeTiles, tiles.y, n_jobs), 128, 0, s>>>(jobs, dev_err);
+  const int tiles_x = (max_w + CT - 1) / CT, tiles_y = (max_h + CT - 1) / CT;
+  k_cca_local<<<dim3((tiles_x + kCcaWarps - 1) / kCcaWarps, tiles_y, n_jobs), kCcaWarps * 32, 0, s>>>(jobs, dev_err);
+  k_cca_merge<<<dim3((tiles_x + kMergeTiles - 1) / kMergeTiles, tiles_y, n_jobs), 128, 0, s>>>(jobs, dev_err);
 }
 
 void launch_cc_filter(const CcaJob* jobs, int n_jobs, int max_w, int max_h, uint32_t* dev_err, cudaStream_t s) {

@@ -88,7 +88,8 @@ struct PairWs {
   uint32_t *hist, *size_key, *shist, *rowcnt;
   int32_t* roots;   // component roots of the CCA (at most ceil(w/2) ceil(h/2) with 8-connectivity)
   double* centroids;
-  int32_t *lab, *iters;
+  int32_t *node, *iters;   // node: the CCA's node table (2 ints per pixel), later the SAD argmin keys (size_key)
+  uint16_t* lab16;         // the CCA's tile-local labels, in the buffer the SAD writes later (sparse)
   int64_t* cut;
   uint16_t *sparse, *filled, *disp, *seg_top, *seg_bot;
   float* taps;
@@ -107,7 +108,7 @@ size_t pair_ws_bytes(const Geo& g, bool need_disp) {
   size_t b = 0;
   b += al(N) * 4;                        // Ll, Lr, refined, filtered
   b += al(256) + al(256 * 4) + al(256 * 8) + al(8) + al(8 * 8);
-  b += al(N * 4) * 2;                    // size/key, lab
+  b += al(N * 8);                        // CCA node table, then the SAD argmin keys
   b += al(shist * 4) + al((size_t)g.h * 4) + al(N + g.w + g.h + 1);   // + root list
   b += al(N * 2) * (need_disp ? 3 : 2);  // sparse, filled (+ disp)
   b += al((size_t)nseg * g.w * 2) * 2;
@@ -131,12 +132,13 @@ PairWs carve(uint8_t* base, const Geo& g, bool need_disp) {
   s.centroids = (double*)take(256 * 8);
   s.iters = (int32_t*)take(8);
   s.cut = (int64_t*)take(8 * 8);
-  s.size_key = (uint32_t*)take(N * 4);
-  s.lab = (int32_t*)take(N * 4);
+  s.node = (int32_t*)take(N * 8);
+  s.size_key = (uint32_t*)s.node;   // free once the CCA's filter has run
   s.shist = (uint32_t*)take(shist * 4);
   s.rowcnt = (uint32_t*)take((size_t)g.h * 4);
   s.roots = (int32_t*)take(N + g.w + g.h + 1);   // 4 ceil(w/2) ceil(h/2) <= (w+1)(h+1) bytes
   s.sparse = (uint16_t*)take(N * 2);
+  s.lab16 = s.sparse;   // the CCA is done with its labels before the SAD writes here
   s.filled = (uint16_t*)take(N * 2);
   s.disp = need_disp ? (uint16_t*)take(N * 2) : nullptr;
   s.seg_top = (uint16_t*)take((size_t)nseg * g.w * 2);
@@ -647,12 +649,11 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
   {
     std::vector<CcaJob> J;
     for (auto& r : runs) {
-      const size_t N = (size_t)r.g.w * r.g.h;
-      SB_MEMSET(ctx, (r.ws.size_key, 0, N * 4, s));
       SB_MEMSET(ctx, (r.ws.shist, 0, (size_t)r.ws.shist_len * 4, s));
       SB_MEMSET(ctx, (r.ws.rowcnt, 0, (size_t)r.g.h * 4, s));
-      J.push_back(CcaJob{r.ws.refined, r.ws.lab, r.ws.size_key, r.ws.shist, r.ws.rowcnt, r.ws.cut, r.ws.filtered,
-                         r.ws.roots, r.g.w, r.g.h, r.ws.shist_len, r.g.p.cc_remove_fraction, ctx->union_limit});
+      J.push_back(CcaJob{r.ws.refined, r.ws.lab16, r.ws.node, r.ws.shist, r.ws.rowcnt, r.ws.cut, r.ws.filtered,
+                         r.ws.roots, nullptr, r.g.w, r.g.h, r.ws.shist_len, r.g.p.cc_remove_fraction,
+                         ctx->union_limit});
     }
     const CcaJob* d = upload(ctx, J, &st);
     if (!d) return st;
@@ -964,16 +965,16 @@ sb_status sb_refine_boundaries(sb_context* ctx, const uint8_t* labels, int32_t w
   if ((int64_t)w * h >= (int64_t)1 << 31) return fail(ctx, SB_ERR_INVALID_ARG, "image too large");
   const size_t N = (size_t)w * h;
   const size_t shist = (size_t)floor(cc_remove_fraction * (double)N) + 2;
-  const size_t need = al(N) + al(N * 4) * 2 + al(shist * 4) + al((size_t)h * 4) + al(64) + al(N + w + h + 1);
+  const size_t need = al(N) + al(N * 8) + al(N * 2) + al(shist * 4) + al((size_t)h * 4) + al(64) + al(N + w + h + 1);
   sb_status st = ensure_ws(ctx, need);
   if (st != SB_OK) return st;
   uint8_t* o = ctx->ws;
   uint8_t* ref = refined ? refined : o;
   o += al(N);
-  int32_t* lab = cc_labels ? cc_labels : (int32_t*)o;
-  o += al(N * 4);
-  uint32_t* size = (uint32_t*)o;
-  o += al(N * 4);
+  int32_t* node = (int32_t*)o;
+  o += al(N * 8);
+  uint16_t* lab16 = (uint16_t*)o;
+  o += al(N * 2);
   uint32_t* sh = (uint32_t*)o;
   o += al(shist * 4);
   uint32_t* rowcnt = (uint32_t*)o;
@@ -987,11 +988,10 @@ sb_status sb_refine_boundaries(sb_context* ctx, const uint8_t* labels, int32_t w
   if (!dm) return st;
   launch_boundary_morph(dm, 1, w, h, morph_mode, s);
   SB_LAUNCHED(ctx, 1);
-  SB_CUDA(ctx, cudaMemsetAsync(size, 0, N * 4, s));
   SB_CUDA(ctx, cudaMemsetAsync(sh, 0, shist * 4, s));
   SB_CUDA(ctx, cudaMemsetAsync(cut, 0, 64, s));
   SB_CUDA(ctx, cudaMemsetAsync(rowcnt, 0, (size_t)h * 4, s));
-  std::vector<CcaJob> CJ{CcaJob{ref, lab, size, sh, rowcnt, cut, boundary, roots, w, h, (int32_t)shist,
+  std::vector<CcaJob> CJ{CcaJob{ref, lab16, node, sh, rowcnt, cut, boundary, roots, cc_labels, w, h, (int32_t)shist,
                                 cc_remove_fraction, ctx->union_limit}};
   const CcaJob* dc = upload(ctx, CJ, &st);
   if (!dc) return st;

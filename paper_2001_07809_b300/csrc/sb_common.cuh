@@ -70,13 +70,14 @@ void launch_boundary_morph(const MorphJob* jobs, int n_jobs, int max_w, int max_
 // ---------------------------------------------------------------------- CCA
 struct CcaJob {
   const uint8_t* b;      // refined map
-  int32_t* lab;          // parent / label array (output: min linear index, -1 background)
-  uint32_t* size;        // per-root sizes (zeroed before k_cc_count)
+  uint16_t* lab;         // tile-local labels: the pixel's local root as y * 32 + x within its 32x32 tile, 0xFFFF off the map
+  int32_t* node;         // 2 per pixel, used at tile-local roots g only: [2g] parent, [2g + 1] component size
   uint32_t* shist;       // size histogram, shist_len entries (zeroed)
-  uint32_t* rowcnt;      // h entries
+  uint32_t* rowcnt;      // h entries (zeroed)
   int64_t* cut;          // [0] N_b, [1] limit, [2] s*, [3] m, [4] T, [5] number of roots
   uint8_t* out;          // filtered boundary map
   int32_t* roots;        // component roots, appended by k_cc_count (count in cut[5]); room for ceil(w/2) ceil(h/2)
+  int32_t* labels_out;   // nullptr or h*w component labels out (smallest linear index, -1 off the map)
   int32_t w, h;
   int32_t shist_len;
   double frac;
