@@ -538,12 +538,12 @@ def run_ours(args):
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1) / plain_steps
     plain_value = aggregate_rate(P, world, max_ranks(plain_ms))
-    # identical outputs batched vs plain (spot check of one pair)
-    spot = min(7, P - 1)
-    ref_out, ref_disp = outs[spot].clone(), disps[spot].clone()
+    # identical outputs batched vs plain, every pair (outputs and disparities)
+    ref = [(o.clone(), d.clone()) for o, d in zip(outs, disps)]
     sb.sb_run(ctx, pairs, flags)
     ctx.synchronize()
-    same = bool(torch.equal(ref_out, outs[spot]) and torch.equal(ref_disp, disps[spot]))
+    same = all(bool(torch.equal(ro, o) and torch.equal(rd, d)) for (ro, rd), o, d in zip(ref, outs, disps))
+    del ref
 
     # anchors -> SAD cell rate and roofline of the box-sum kernel
     nb = anchor_counts(ctx, sb, torch, lefts, rights, params)
@@ -586,7 +586,8 @@ def run_ours(args):
         t1 = time.perf_counter()
         barrier()
         e2e_s = max_ranks((t1 - t0) / e2e_steps)
-        same = same and bool(torch.equal(ho[spot].cuda(), outs[spot]))
+        same = same and all(bool(torch.equal(ho[i].cuda(), outs[i]) and torch.equal(hd[i].cuda(), disps[i]))
+                            for i in range(P))
         e2e = {"value": P * world / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": P * H * W * 6,
                "d2h_bytes_per_step": P * H * W * 5, "ms_per_step": e2e_s * 1000.0}
         del hl, hr, ho, hd
@@ -653,6 +654,7 @@ def run_ours(args):
                        "sad_variant": args.sad_variant},
             "per_pair_plain": {"value": plain_value, "unit": "pairs/s", "ms_per_step": plain_ms},
             "batched_equals_plain": same,
+            "batched_equals_plain_pairs": P,   # pairs compared (every pair; also the host-buffer run's outputs)
             "sad_gcell_s": cells / (sad_ms / 1000.0) / 1e9,
             "stage_ms": dict(zip(sb.STAGES, stage_avg)),
             "anchors_per_pair": sum(nb) / len(nb),

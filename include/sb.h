@@ -45,7 +45,8 @@ typedef enum {
   SB_ERR_CUDA = 2,
   SB_ERR_OOM = 3,
   SB_ERR_TIMEOUT = 4,       /* a bounded device-side loop gave up (see sb_set_union_limit) */
-  SB_ERR_UNSUPPORTED = 5
+  SB_ERR_UNSUPPORTED = 5,
+  SB_ERR_CHECK = 6          /* bounds-checked build only: a device index check failed (see sb_check_probe) */
 } sb_status;
 
 typedef struct sb_context sb_context;
@@ -219,6 +220,19 @@ int32_t sb_host_io_chunks(const sb_context* ctx);
  * the default, 2^22, far above any chain an image of up to 2^31 pixels
  * builds; a negative limit returns SB_ERR_INVALID_ARG. */
 sb_status sb_set_union_limit(sb_context* ctx, int32_t limit);
+
+/* Bounds-checked build.  libsb_checks.so is the same library compiled with
+ * -DSB_CHECKS: before every access whose index comes from data (labels,
+ * parent links, root lists, work-item tables, anchor positions) a kernel
+ * checks the index; a failed check records its site number, skips the access
+ * and lets the kernel finish, and the next sb_synchronize returns
+ * SB_ERR_CHECK naming the first site (the record is then cleared and the
+ * context stays usable).  sb_checks_built returns 1 in that library, 0 in
+ * libsb.so.  sb_check_probe enqueues a kernel whose only check fails when
+ * trip is nonzero (site 1), to test the reporting path; in libsb.so it
+ * returns SB_ERR_UNSUPPORTED. */
+int32_t sb_checks_built(void);
+sb_status sb_check_probe(sb_context* ctx, int32_t trip);
 
 /* One stereo pair for sb_run. */
 typedef struct {

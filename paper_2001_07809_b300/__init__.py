@@ -5,6 +5,9 @@ built in-tree for sm_103a by ``build.py``).  The functions keep the C names
 and only marshal arguments: torch tensors supply device memory and streams,
 every step of the method runs in the library's CUDA kernels.  There is no
 CPU fallback: if the library cannot be loaded, importing this package fails.
+With ``SB_LIBRARY=checks`` in the environment the bounds-checked build
+(``libsb_checks.so``, see ``sb_check_probe`` in include/sb.h) is loaded
+instead.
 """
 from __future__ import annotations
 
@@ -18,13 +21,13 @@ __all__ = [
     "SbError", "Context", "Pair", "sb_default_params", "make_params", "sb_create", "sb_destroy",
     "sb_rgb_to_lightness", "sb_kmeans_segment", "sb_refine_boundaries", "sb_boundary_sad",
     "sb_reconstruct_disparity", "sb_selective_blur", "sb_run", "sb_synchronize", "sb_launch_count",
-    "sb_lr_consistency", "sb_autotune", "sb_set_blur_form", "sb_set_union_limit", "sb_set_host_chunk", "sb_host_io_chunks", "SB_BLUR_AUTO", "SB_BLUR_STRIP", "SB_BLUR_TILES_64",
+    "sb_lr_consistency", "sb_autotune", "sb_set_blur_form", "sb_set_union_limit", "sb_checks_built", "sb_check_probe", "sb_set_host_chunk", "sb_host_io_chunks", "SB_BLUR_AUTO", "SB_BLUR_STRIP", "SB_BLUR_TILES_64",
     "SB_BLUR_TILES_112", "SB_PEEK_SNAPSHOT", "SB_PEEK_INPLACE", "SB_VIEW_LEFT", "SB_VIEW_RIGHT",
     "SB_RUN_PLAIN", "SB_RUN_BATCHED", "SB_RUN_GRAPH", "SB_RUN_HOST_IO", "SB_SAD_AUTO", "SB_SAD_DIRECT",
     "SB_SAD_BOXSUM", "SB_MORPH_FILL_REMOVE", "SB_MORPH_OPEN_CLOSE", "UNDETERMINED", "library_path",
 ]
 
-SB_OK, SB_ERR_INVALID_ARG, SB_ERR_CUDA, SB_ERR_OOM, SB_ERR_TIMEOUT, SB_ERR_UNSUPPORTED = range(6)
+SB_OK, SB_ERR_INVALID_ARG, SB_ERR_CUDA, SB_ERR_OOM, SB_ERR_TIMEOUT, SB_ERR_UNSUPPORTED, SB_ERR_CHECK = range(7)
 SB_MORPH_FILL_REMOVE, SB_MORPH_OPEN_CLOSE = 0, 1
 SB_SAD_AUTO, SB_SAD_DIRECT, SB_SAD_BOXSUM = 0, 1, 2
 SB_PEEK_SNAPSHOT, SB_PEEK_INPLACE = 0, 1
@@ -61,18 +64,26 @@ class sb_pair(ctypes.Structure):
                 ("h", ctypes.c_int32), ("p", sb_params), ("out_rgb", ctypes.c_void_p), ("out_disp", ctypes.c_void_p)]
 
 
+def _variant() -> str:
+    v = os.environ.get("SB_LIBRARY", "")
+    if v not in ("", "checks"):
+        raise ImportError("SB_LIBRARY must be unset or 'checks', not %r" % v)
+    return v
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKS if _variant() == "checks" else _build.LIB
 
 
 def _load():
-    path = _build.LIB
-    if _build.needs_build():
+    checks = _variant() == "checks"
+    path = library_path()
+    if _build.needs_build(checks):
         try:
-            _build.build()
+            _build.build(checks=checks)
         except Exception as e:  # no toolkit: fail loudly, there is no fallback
             if not os.path.exists(path):
-                raise ImportError("libsb.so is missing and could not be built: %s" % e) from e
+                raise ImportError("%s is missing and could not be built: %s" % (os.path.basename(path), e)) from e
     lib = ctypes.CDLL(path)
     V, I32, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32
     sig = {
@@ -93,6 +104,8 @@ def _load():
         "sb_autotune": ([V, V, I32, ctypes.c_uint32, V, V, V], ctypes.c_int),
         "sb_set_blur_form": ([V, I32], ctypes.c_int),
         "sb_set_union_limit": ([V, I32], ctypes.c_int),
+        "sb_checks_built": ([], ctypes.c_int32),
+        "sb_check_probe": ([V, I32], ctypes.c_int),
         "sb_set_host_chunk": ([V, ctypes.c_size_t, ctypes.c_size_t], ctypes.c_int),
         "sb_host_io_chunks": ([V], ctypes.c_int32),
         "sb_selective_blur": ([V, V, V, I32, I32, V, I32, ctypes.c_float, V], ctypes.c_int),
@@ -181,6 +194,10 @@ class Context:
     def set_union_limit(self, limit: int):
         """Bound of the connected-components union-find (0: the default)."""
         _check(self, _lib.sb_set_union_limit(self.handle, int(limit)))
+
+    def check_probe(self, trip: bool):
+        """Enqueue the bounds-check probe (bounds-checked library only)."""
+        _check(self, _lib.sb_check_probe(self.handle, 1 if trip else 0))
 
     def workspace_bytes(self) -> int:
         return int(_lib.sb_workspace_bytes(self.handle))
@@ -323,6 +340,15 @@ def sb_host_io_chunks(ctx: Context) -> int:
 
 def sb_set_union_limit(ctx: Context, limit: int):
     ctx.set_union_limit(limit)
+
+
+def sb_checks_built() -> bool:
+    """True when the loaded library is the bounds-checked build."""
+    return bool(_lib.sb_checks_built())
+
+
+def sb_check_probe(ctx: Context, trip: bool):
+    ctx.check_probe(trip)
 
 
 def sb_set_blur_form(ctx: Context, form: int):

@@ -3,7 +3,9 @@
 Each translation unit is compiled with nvcc for
 ``-gencode arch=compute_103a,code=sm_103a`` (``-lineinfo`` for profiling),
 in parallel, then linked with the shared CUDA runtime.  A rebuild happens
-only when a source or header is newer than the library.
+only when a source or header is newer than the library.  ``checks=True``
+builds the bounds-checked variant, libsb_checks.so (``-DSB_CHECKS``: index
+checks that record a failure and skip the access; see include/sb.h).
 """
 from __future__ import annotations
 
@@ -18,6 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libsb.so")
+LIB_CHECKS = os.path.join(HERE, "libsb_checks.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -37,24 +40,27 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "sb.h")]
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB):
+def needs_build(checks: bool = False) -> bool:
+    lib = LIB_CHECKS if checks else LIB
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not needs_build():
+def build(force: bool = False, verbose: bool = False, checks: bool = False) -> str:
+    lib = LIB_CHECKS if checks else LIB
+    if not force and not needs_build(checks):
         build_peak()
-        return LIB
+        return lib
     nvcc = _nvcc()
-    os.makedirs(BUILD_DIR, exist_ok=True)
+    obj_dir = os.path.join(BUILD_DIR, "checks") if checks else BUILD_DIR
+    os.makedirs(obj_dir, exist_ok=True)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v" if verbose else "-O3",
-                    "-I", os.path.join(ROOT, "include")]
+                    "-I", os.path.join(ROOT, "include")] + (["-DSB_CHECKS"] if checks else [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src).replace(".cu", ".o"))
+        obj = os.path.join(obj_dir, os.path.basename(src).replace(".cu", ".o"))
         cmd = [nvcc] + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -65,14 +71,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
         objs = list(ex.map(compile_one, _sources()))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     build_peak(force)
-    return LIB
+    return lib
 
 
 PEAK_SRC = os.path.join(HERE, "peak", "int_peak.cu")
@@ -94,4 +100,4 @@ def build_peak(force: bool = False) -> str:
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checks="--checks" in sys.argv))

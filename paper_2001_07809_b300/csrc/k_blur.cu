@@ -649,4 +649,6 @@ void launch_blur(const BlurJob* jobs, int n_jobs, int max_w, int max_h, int max_
     launch_blur_by<112>(jobs, n_jobs, max_w, max_h, max_R, s);
 }
 
+SB_CHECKS_UNIT(blur)
+
 }  // namespace sb

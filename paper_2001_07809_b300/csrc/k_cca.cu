@@ -50,7 +50,7 @@ template <int S>
 __device__ __forceinline__ int find_root(int* P, int x, int limit, bool& ok) {
   for (int guard = 0;; ++guard) {
     const int p = *parent_of<S>(P, x);
-    if (p == x) return x;
+    if (p == x || !SB_CHECK(p >= 0 && p < x, 301u)) return x;
     if (guard >= limit) {
       ok = false;
       return x;
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kCcaWarps * 32) k_cca_local(const CcaJob* __re
           P[C] = root;
         } else {
           const int64_t g = (int64_t)(ty0 + y) * w + x;
-          reinterpret_cast<int2*>(J.node)[g] = make_int2((int)g, 0);
+          if (SB_CHECK(x < w, 302u)) reinterpret_cast<int2*>(J.node)[g] = make_int2((int)g, 0);
         }
       }
     }
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(128) k_cca_merge(const CcaJob* __restrict__ jo
     const int x = tx0 + lx, y = ty0 + ly;
     if (x >= w || y >= h) continue;
     const int lp = J.lab[(int64_t)y * w + x];
-    if (lp == kOffMap) continue;
+    if (lp == kOffMap || !SB_CHECK(lp < CT * CT, 303u)) continue;
     const int a = (int)local_root_at(x, y, lp, w);
     const int nx[4] = {x - 1, x - 1, x, x + 1}, ny[4] = {y, y - 1, y - 1, y - 1};
 #pragma unroll
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(128) k_cca_merge(const CcaJob* __restrict__ jo
       if (qx < 0 || qy < 0 || qx >= w) continue;
       if (qx >= tx0 && qx < tx0 + CT && qy >= ty0) continue;  // same tile: done locally
       const int lq = J.lab[(int64_t)qy * w + qx];
-      if (lq != kOffMap) ok &= unite<2>(J.node, a, (int)local_root_at(qx, qy, lq, w), J.union_limit, ok);
+      if (lq != kOffMap && SB_CHECK(lq < CT * CT, 303u)) ok &= unite<2>(J.node, a, (int)local_root_at(qx, qy, lq, w), J.union_limit, ok);
     }
   }
   if (!ok) atomicOr(dev_err, DEV_ERR_CCA_ITER);
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(256) k_cc_count(const CcaJob* __restrict__ job
   for (int tt = 0; tt < kCountTiles; ++tt)
 #pragma unroll
     for (int k = 0; k < kPer; ++k)
-      if (li[tt][k] != kOffMap) {
+      if (li[tt][k] != kOffMap && SB_CHECK(li[tt][k] < CT * CT, 304u)) {
         atomicAdd(&s_cnt[tt][li[tt][k]], 1u);
         ++mine;
       }
@@ -293,8 +293,12 @@ __global__ void __launch_bounds__(256) k_cc_count(const CcaJob* __restrict__ job
         const int g = (ty0 + (i >> 5)) * w + tx0 + (i & (CT - 1));
         const int R = find_root<2>(J.node, g, J.union_limit, ok);
         atomicAdd(reinterpret_cast<unsigned*>(&J.node[2 * (int64_t)R + 1]), c);
-        if (R == g) J.roots[atomicAdd(reinterpret_cast<unsigned long long*>(&J.cut[5]), 1ull)] = R;
-        else J.node[2 * (int64_t)g] = R;   // another tile's search through g still reaches R
+        if (R == g) {
+          const unsigned long long at = atomicAdd(reinterpret_cast<unsigned long long*>(&J.cut[5]), 1ull);
+          if (SB_CHECK(at < (unsigned long long)((w + 1) / 2) * ((h + 1) / 2), 305u)) J.roots[at] = R;
+        } else {
+          J.node[2 * (int64_t)g] = R;   // another tile's search through g still reaches R
+        }
       }
     }
   }
@@ -315,7 +319,9 @@ __global__ void __launch_bounds__(256) k_cc_hist(const CcaJob* __restrict__ jobs
   const int64_t limit = removal_limit(J);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nroots; i += stride) {
-    const uint32_t s = comp_size(J, J.roots[i]);
+    const int v = J.roots[i];
+    if (!SB_CHECK(v >= 0 && v < J.w * J.h, 306u)) continue;
+    const uint32_t s = comp_size(J, v);
     if ((int64_t)s <= limit && (int64_t)s < J.shist_len) atomicAdd(&J.shist[s], 1u);
   }
 }
@@ -375,6 +381,7 @@ __global__ void __launch_bounds__(256) k_cc_rowcount(const CcaJob* __restrict__ 
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nroots; i += stride) {
     const int v = J.roots[i];
+    if (!SB_CHECK(v >= 0 && v < J.w * J.h, 306u)) continue;
     if (comp_size(J, v) == sstar) atomicAdd(&J.rowcnt[v / J.w], 1u);
   }
 }
@@ -440,68 +447,86 @@ __global__ void __launch_bounds__(1024) k_cc_select(const CcaJob* __restrict__ j
   }
 }
 
-// The filtered map (and, when asked for, every pixel's component label): a
-// pixel's local root points straight at its component root R after counting,
-// and R's component stays unless it is smaller than s*, or of size s* with a
-// label below T.
+// The filtered map (and, when asked for, every pixel's component label),
+// kFilterTiles 32x32 tiles per CTA.  Thread t holds eight pixels of one tile
+// row; the tile's pixels first mark the local roots they refer to, then each
+// marked local root is resolved once (its node points straight at its
+// component root R after counting; R's component stays unless it is smaller
+// than s*, or of size s* with a label below T), all of them in parallel, and
+// the pixels take their local root's result from shared memory.
+constexpr int kFilterTiles = 2;
 __global__ void __launch_bounds__(256) k_cc_filter(const CcaJob* __restrict__ jobs) {
-  const CcaJob J = jobs[blockIdx.y];
+  constexpr int kMark = -2;
+  __shared__ int s_R[kFilterTiles][CT * CT];          // component root per local root (-1: unused)
+  __shared__ uint8_t s_keep[kFilterTiles][CT * CT];
+  const CcaJob J = jobs[blockIdx.z];
   const int w = J.w, h = J.h;
+  const int ty0 = blockIdx.y * CT;
+  if (blockIdx.x * kFilterTiles * CT >= w || ty0 >= h) return;
   const uint32_t sstar = (uint32_t)J.cut[2];
   const long long T = J.cut[4];
-  auto comp = [&](int x, int y, int li) -> int { return J.node[2 * local_root_at(x, y, li, w)]; };
-  auto keep = [&](int R) -> uint8_t {
-    const uint32_t sz = comp_size(J, R);
-    return sz < sstar || (sz == sstar && (long long)R < T) ? 0 : 1;
-  };
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool vec = (w & 7) == 0 && ((reinterpret_cast<uintptr_t>(J.lab) | reinterpret_cast<uintptr_t>(J.labels_out)) & 15) == 0 &&
-                   (reinterpret_cast<uintptr_t>(J.out) & 7) == 0;
+  const int tid = threadIdx.x, tt = tid >> 7, ly = (tid >> 2) & (CT - 1), c8 = (tid & 3) * 8;
+  const int tx0 = (blockIdx.x * kFilterTiles + tt) * CT, x0 = tx0 + c8, y = ty0 + ly;
+  for (int i = tid; i < kFilterTiles * CT * CT; i += blockDim.x) (&s_R[0][0])[i] = -1;
+  // this thread's eight labels (one 16-byte load where the row allows it)
+  uint16_t li[8];
+  const int64_t p0 = (int64_t)y * w + x0;
+  const bool inside = y < h && x0 + 8 <= w;
+  const bool vec = inside && (w & 7) == 0 && (reinterpret_cast<uintptr_t>(J.lab) & 15) == 0;
   if (vec) {
-    // eight pixels of one row per step (one 16-byte label load; neighbours
-    // mostly share their local root, so one lookup serves a run of them)
-    const unsigned cw = (unsigned)w >> 3;
-    const int64_t nq = (int64_t)cw * h;
-    for (int64_t q = t0; q < nq; q += stride) {
-      const unsigned y = (unsigned)q / cw, x0 = ((unsigned)q - y * cw) * 8;
-      const uint4 v = reinterpret_cast<const uint4*>(J.lab)[q];
-      const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
-      uint32_t o[2] = {0u, 0u};
-      int R[8];
-      int prev = -1, prevR = -1;
-      uint8_t prevk = 0;
+    const uint4 v = *reinterpret_cast<const uint4*>(J.lab + p0);
+    const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int li = (int)((wd[j >> 1] >> (16 * (j & 1))) & 0xFFFFu);
-        uint8_t k = 0;
-        R[j] = -1;
-        if (li != kOffMap) {
-          if (li != prev) {
-            prev = li;
-            prevR = comp((int)x0 + j, (int)y, li);
-            prevk = keep(prevR);
-          }
-          R[j] = prevR;
-          k = prevk;
-        }
-        o[j >> 2] |= (uint32_t)k << (8 * (j & 3));
-      }
-      reinterpret_cast<uint2*>(J.out)[q] = make_uint2(o[0], o[1]);
-      if (J.labels_out) {
-        int4* lo = reinterpret_cast<int4*>(J.labels_out) + 2 * q;
-        lo[0] = make_int4(R[0], R[1], R[2], R[3]);
-        lo[1] = make_int4(R[4], R[5], R[6], R[7]);
-      }
-    }
+    for (int j = 0; j < 8; ++j) li[j] = (uint16_t)(wd[j >> 1] >> (16 * (j & 1)));
   } else {
-    const int64_t n = (int64_t)w * h;
-    for (int64_t p = t0; p < n; p += stride) {
-      const int y = (int)(p / w), x = (int)(p - (int64_t)y * w);
-      const int li = J.lab[p];
-      const int R = li == kOffMap ? -1 : comp(x, y, li);
-      J.out[p] = R < 0 ? 0 : keep(R);
-      if (J.labels_out) J.labels_out[p] = R;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) li[j] = (y < h && x0 + j < w) ? J.lab[p0 + j] : kOffMap;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    if (li[j] != kOffMap && SB_CHECK(li[j] < CT * CT, 307u)) s_R[tt][li[j]] = kMark;
+  __syncthreads();
+  for (int i = tid; i < kFilterTiles * CT * CT; i += blockDim.x) {
+    if ((&s_R[0][0])[i] != kMark) continue;
+    const int ti = i >> 10, l = i & (CT * CT - 1);
+    const int64_t g = (int64_t)(ty0 + (l >> 5)) * w + (blockIdx.x * kFilterTiles + ti) * CT + (l & (CT - 1));
+    int R = J.node[2 * g];
+    if (!SB_CHECK(R >= 0 && R < w * h, 308u)) R = -1;
+    uint8_t k = 0;
+    if (R >= 0) {
+      const uint32_t sz = comp_size(J, R);
+      k = sz < sstar || (sz == sstar && (long long)R < T) ? 0 : 1;
+    }
+    (&s_R[0][0])[i] = R;
+    (&s_keep[0][0])[i] = k;
+  }
+  __syncthreads();
+  if (y >= h || x0 >= w) return;
+  uint32_t o[2] = {0u, 0u};
+  int R[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const bool on = li[j] != kOffMap && li[j] < CT * CT;
+    R[j] = on ? s_R[tt][li[j]] : -1;
+    o[j >> 2] |= (uint32_t)(on ? s_keep[tt][li[j]] : 0) << (8 * (j & 3));
+  }
+  if (vec && (reinterpret_cast<uintptr_t>(J.out) & 7) == 0) {
+    *reinterpret_cast<uint2*>(J.out + p0) = make_uint2(o[0], o[1]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (x0 + j < w) J.out[p0 + j] = (uint8_t)(o[j >> 2] >> (8 * (j & 3)));
+  }
+  if (J.labels_out) {
+    if (vec && (reinterpret_cast<uintptr_t>(J.labels_out) & 15) == 0) {
+      int4* lo = reinterpret_cast<int4*>(J.labels_out + p0);
+      lo[0] = make_int4(R[0], R[1], R[2], R[3]);
+      lo[1] = make_int4(R[4], R[5], R[6], R[7]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (x0 + j < w) J.labels_out[p0 + j] = R[j];
     }
   }
 }
@@ -519,20 +544,19 @@ void launch_cc_filter(const CcaJob* jobs, int n_jobs, int max_w, int max_h, uint
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // filter CTAs per job: one per 2048 pixels, at most 8 waves per SM, and no more
-  // than 16 waves of the whole batch in all (a large batch needs few per job)
-  int64_t bpj64 = std::min<int64_t>((n + 256 * 8 - 1) / (256 * 8), 8 * (int64_t)sms);
-  bpj64 = std::min<int64_t>(bpj64, (16 * 8 * (int64_t)sms + n_jobs - 1) / n_jobs);
-  const int bpj = (int)std::max<int64_t>(1, bpj64);
   const int tiles_x = (max_w + CT - 1) / CT;
   k_cc_count<<<dim3((tiles_x + kCountTiles - 1) / kCountTiles, (max_h + CT - 1) / CT, n_jobs), 256, 0, s>>>(jobs, dev_err);
-  // root-list passes: roots are few; four waves of the batch in all
-  const int rpj = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(bpj, sms), (4 * 8 * (int64_t)sms + n_jobs - 1) / n_jobs));
+  // root-list passes: roots are few; one CTA per 2048 pixels of a job, at most one
+  // per SM, and four waves of the batch in all
+  const int64_t per_job = std::min<int64_t>((n + 2047) / 2048, sms);
+  const int rpj = (int)std::max<int64_t>(1, std::min<int64_t>(per_job, (4 * 8 * (int64_t)sms + n_jobs - 1) / n_jobs));
   k_cc_hist<<<dim3(rpj, n_jobs), 256, 0, s>>>(jobs);
   k_cc_cut<<<n_jobs, 1024, 0, s>>>(jobs);
   k_cc_rowcount<<<dim3(rpj, n_jobs), 256, 0, s>>>(jobs);
   k_cc_select<<<n_jobs, 1024, 0, s>>>(jobs);
-  k_cc_filter<<<dim3(bpj, n_jobs), 256, 0, s>>>(jobs);
+  k_cc_filter<<<dim3((tiles_x + kFilterTiles - 1) / kFilterTiles, (max_h + CT - 1) / CT, n_jobs), 256, 0, s>>>(jobs);
 }
+
+SB_CHECKS_UNIT(cca)
 
 }  // namespace sb

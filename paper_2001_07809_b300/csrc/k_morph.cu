@@ -208,4 +208,6 @@ void launch_boundary_morph(const MorphJob* jobs, int n_jobs, int max_w, int max_
     k_boundary_bits<1><<<grid, kBitThreads, 0, s>>>(jobs);
 }
 
+SB_CHECKS_UNIT(morph)
+
 }  // namespace sb

@@ -317,4 +317,6 @@ void launch_lr_consistency(const uint16_t* dL, const uint16_t* dR, int w, int h,
 // kernels launch_recon issues for the given peek_modes
 int recon_launches(int peek_modes) { return 1 + ((peek_modes & 1) ? 2 : 0) + ((peek_modes & 2) ? 1 : 0); }
 
+SB_CHECKS_UNIT(recon)
+
 }  // namespace sb

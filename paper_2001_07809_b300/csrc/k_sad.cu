@@ -170,6 +170,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
     const SadItem it = items[s_item];
     const SadJob J = jobs[it.job];
     if (sad_use_direct(J)) continue;                        // the direct kernel serves this pair
+    // a work item inside Omega, on a chunk of the disparity range
+    if (!SB_CHECK(it.y0 >= J.r && it.y0 <= it.y1 && it.y1 <= J.h - 1 - J.r && it.x0 >= J.D + J.r &&
+                  it.x0 < J.w - J.r && it.d0 >= 0 && it.d0 <= J.D && it.d0 % kSadChunk == 0, 401u))
+      continue;
     const int r = J.r, D = J.D, w = J.w;
     const int64_t npx = (int64_t)w * J.h;
     const int ring = 2 * r + 1 + 2 * kG;                    // + one group staged ahead
@@ -428,6 +432,10 @@ __global__ void __launch_bounds__(256, 6) k_sad_tail(const SadJob* __restrict__ 
     const SadItem it = items[s_item];
     const SadJob J = jobs[it.job];
     if (sad_use_direct(J)) continue;
+    // a work item inside Omega, on the disparities past the last whole chunk
+    if (!SB_CHECK(it.y0 >= J.r && it.y0 <= it.y1 && it.y1 <= J.h - 1 - J.r && it.x0 >= J.D + J.r &&
+                  it.x0 < J.w - J.r && it.d0 == sad_tail_first(J.D) && J.D + 1 - it.d0 <= kTailMax, 402u))
+      continue;
     const int r = J.r, D = J.D, w = J.w, w15 = w & 15;
     const int64_t npx = (int64_t)w * J.h;
     const int dt0 = it.d0, rem = D + 1 - dt0;
@@ -728,7 +736,7 @@ __device__ __forceinline__ void direct_anchor(const SadJob& J, int y0, int x0, c
     if (last && p1 && 64 * n2 + lane <= D) best = min(best, (acc1 << SB_KEY_DBITS) | (uint32_t)(64 * n2 + lane));
   }
   best = __reduce_min_sync(0xffffffffu, best);
-  if (lane == 0) J.key[(int64_t)y * w + xa] = best;
+  if (lane == 0 && SB_CHECK(y >= 0 && y < J.h && xa >= 0 && xa < w, 403u)) J.key[(int64_t)y * w + xa] = best;
 }
 
 // Persistent grid over the tiles of the jobs whose window spans NW words and
@@ -886,5 +894,7 @@ void launch_sad_finalize(const SadJob* jobs, int n_jobs, int max_w, int max_h, c
   if (n_jobs <= 0) return;
   k_sad_finalize<<<dim3((max_w + 255) / 256, max_h, n_jobs), 256, 0, s>>>(jobs);
 }
+
+SB_CHECKS_UNIT(sad)
 
 }  // namespace sb

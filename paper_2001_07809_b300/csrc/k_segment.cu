@@ -128,17 +128,25 @@ void launch_labels(const LabelJob* jobs, int n_jobs, int blocks_per_job, cudaStr
 
 // Histogram K-means: one CTA of 256 threads per image, thread b owns bin b.
 // FP64 with explicit round-to-nearest intrinsics so no multiply-add is fused
-// (the CPU computes the same expressions in the same order).
+// (the CPU computes the same expressions in the same order).  A cluster's
+// pixel count and sum of lightness are integers, so the order in which they
+// are added does not change them: each warp sums the bins of every cluster it
+// holds with redux.sync, and one lane per (warp, cluster) adds the result in
+// shared memory (at most eight adds to one address, instead of one per bin).
 __global__ void __launch_bounds__(256) k_kmeans(const KmeansJob* __restrict__ jobs) {
   __shared__ double s_c[256];
   __shared__ unsigned long long s_num[256], s_den[256];
   __shared__ int s_lmin, s_lmax;
   const KmeansJob J = jobs[blockIdx.x];
-  const int b = threadIdx.x, K = J.k;
+  const int b = threadIdx.x, K = J.k, lane = b & 31;
   const uint32_t hb = J.hist[b];
   if (b == 0) { s_lmin = 256; s_lmax = -1; }
   __syncthreads();
-  if (hb) { atomicMin(&s_lmin, b); atomicMax(&s_lmax, b); }
+  {
+    const int wmin = (int)__reduce_min_sync(0xffffffffu, hb ? (unsigned)b : 256u);
+    const int wmax = (int)__reduce_max_sync(0xffffffffu, hb ? (unsigned)b + 1u : 0u) - 1;
+    if (lane == 0 && wmax >= 0) { atomicMin(&s_lmin, wmin); atomicMax(&s_lmax, wmax); }
+  }
   __syncthreads();
   const int lmin = s_lmin, lmax = s_lmax;
   if (lmax < 0) {  // empty image
@@ -161,15 +169,28 @@ __global__ void __launch_bounds__(256) k_kmeans(const KmeansJob* __restrict__ jo
     }
     return best;
   };
+  // exact sum of v over the lanes where `in` (v < 2^39: 24-bit pieces, so no
+  // 32-bit partial sum of 32 lanes overflows)
+  auto warp_sum = [&](uint64_t v, bool in) -> unsigned long long {
+    const unsigned lo = in ? (unsigned)(v & 0xFFFFFFu) : 0u, hi = in ? (unsigned)(v >> 24) : 0u;
+    return ((unsigned long long)__reduce_add_sync(0xffffffffu, hi) << 24) + __reduce_add_sync(0xffffffffu, lo);
+  };
   int a = assign();
   int it = 0;
   while (it < J.max_iter) {
     ++it;
     if (b < K) { s_num[b] = 0ull; s_den[b] = 0ull; }
     __syncthreads();
-    if (hb) {
-      atomicAdd(&s_num[a], (unsigned long long)hb * (unsigned long long)b);
-      atomicAdd(&s_den[a], (unsigned long long)hb);
+    for (unsigned todo = __ballot_sync(0xffffffffu, hb != 0); todo;) {   // clusters this warp holds
+      const int k = __shfl_sync(0xffffffffu, a, __ffs(todo) - 1);
+      const bool in = hb != 0 && a == k;
+      const unsigned grp = __ballot_sync(0xffffffffu, in);
+      const unsigned long long num = warp_sum((uint64_t)hb * (uint64_t)b, in), den = warp_sum(hb, in);
+      if (lane == __ffs(grp) - 1) {
+        atomicAdd(&s_num[k], num);
+        atomicAdd(&s_den[k], den);
+      }
+      todo &= ~grp;
     }
     __syncthreads();
     if (b < K && s_den[b] > 0ull) s_c[b] = __ddiv_rn(__ull2double_rn(s_num[b]), __ull2double_rn(s_den[b]));
@@ -188,5 +209,7 @@ void launch_kmeans(const KmeansJob* jobs, int n_jobs, cudaStream_t s) {
   if (n_jobs <= 0) return;
   k_kmeans<<<n_jobs, 256, 0, s>>>(jobs);
 }
+
+SB_CHECKS_UNIT(segment)
 
 }  // namespace sb

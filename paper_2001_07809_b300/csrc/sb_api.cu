@@ -4,6 +4,7 @@
 // in the kernels of the other translation units; this file only sizes,
 // places and orders the work.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -200,6 +201,7 @@ struct sb_context {
   bool prof_on = false;
   cudaEvent_t prof_ev[SB_N_STAGES + 1] = {};
   bool prof_recorded = false;
+  bool nvtx_open = false;   // a stage's NVTX range is pushed
   bool capturing = false;
   uint64_t graph_kernels = 0;
   // autotune cache: launch-group shape (each pair's w, h, D, block) -> the
@@ -515,8 +517,32 @@ void sad_items(const std::vector<std::pair<int, Geo>>& pairs, int64_t target, in
   for (auto& it : tail_parts) items->push_back(it);
 }
 
-// Stage boundary marks for sb_profile_read (external records inside captures).
+// NVTX ranges (host side, the default domain): "sb:run" around each sb_run
+// and one range per pipeline stage, "sb:<stage>", open while the stage's
+// work is enqueued, so a profiler that follows NVTX (ncu --nvtx) attributes
+// the stage's launches to it.  In the graph form they mark the capture; a
+// replay is a single graph launch inside "sb:run".
+const char* const kStageRange[SB_N_STAGES] = {"sb:lightness", "sb:kmeans", "sb:refine", "sb:cca",
+                                              "sb:sad",       "sb:sad_rest", "sb:recon", "sb:blur"};
+
+void nvtx_stage(sb_context* ctx, int i) {
+  if (ctx->nvtx_open) nvtxRangePop();
+  ctx->nvtx_open = i < SB_N_STAGES;
+  if (ctx->nvtx_open) nvtxRangePushA(kStageRange[i]);
+}
+
+// Closes a stage range still open when the enqueuing returns early.
+struct StageRanges {
+  sb_context* ctx;
+  ~StageRanges() {
+    if (ctx->nvtx_open) nvtx_stage(ctx, SB_N_STAGES);
+  }
+};
+
+// Stage boundary marks: the NVTX stage ranges, and for sb_profile_read CUDA
+// events (external records inside captures).
 sb_status mark(sb_context* ctx, int i) {
+  if (!ctx->dry) nvtx_stage(ctx, i);
   if (!ctx->prof_on || ctx->dry) return SB_OK;
   cudaError_t e = ctx->capturing ? cudaEventRecordWithFlags(ctx->prof_ev[i], ctx->stream, cudaEventRecordExternal)
                                  : cudaEventRecord(ctx->prof_ev[i], ctx->stream);
@@ -572,6 +598,7 @@ int64_t sad_target(const sb_context* ctx, const std::string& key) {
 // them).  Job descriptors go to `jobs_dev` when given (graph form), else
 // through the upload ring.
 sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
+  StageRanges ranges{ctx};
   cudaStream_t s = ctx->stream;
   sb_status st = SB_OK;
   const int n = (int)runs.size();
@@ -788,6 +815,42 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
 }  // namespace
 
 // =================================================================== C ABI
+namespace sb {
+SB_CHECKS_UNIT(api)
+}  // namespace sb
+
+// The first failed bounds check of any unit (each unit's word is read and
+// cleared); 0 when none failed or the build has no checks.
+static uint32_t first_check_site() {
+  uint32_t (*const units[])() = {checks_api, checks_noalloc, checks_segment, checks_morph,
+                                 checks_cca, checks_sad, checks_recon, checks_blur};
+  uint32_t first = 0;
+  for (auto u : units) {
+    const uint32_t v = u();
+    if (v && !first) first = v;
+  }
+  return first;
+}
+
+static const char* check_site_stage(uint32_t site) {
+  switch (site / 100) {
+    case 0: return "probe";
+    case 1: return "lightness / k-means";
+    case 2: return "boundary refinement";
+    case 3: return "connected components";
+    case 4: return "SAD";
+    case 5: return "reconstruction";
+    case 6: return "blur";
+    default: return "allocation-free SAD";
+  }
+}
+
+namespace {
+__global__ void k_check_probe(int trip) {
+  if (SB_CHECK(trip == 0, 1u)) return;
+}
+}  // namespace
+
 extern "C" {
 
 void sb_default_params(sb_params* p) {
@@ -908,7 +971,31 @@ sb_status sb_synchronize(sb_context* ctx) {
                   "(sb_set_union_limit); the run's results are not valid", ctx->union_limit);
     return fail(ctx, SB_ERR_CUDA, "device-side check failed (flags 0x%x)", e);
   }
+  const uint32_t site = first_check_site();
+  if (site)
+    return fail(ctx, SB_ERR_CHECK, "bounds check failed at site %u (%s); the run's results are not valid", site,
+                check_site_stage(site));
   return SB_OK;
+}
+
+sb_status sb_check_probe(sb_context* ctx, int32_t trip) {
+  if (!ctx) return SB_ERR_INVALID_ARG;
+#ifdef SB_CHECKS
+  k_check_probe<<<1, 32, 0, ctx->stream>>>(trip);
+  SB_LAUNCHED(ctx, 1);
+  return SB_OK;
+#else
+  (void)trip;
+  return fail(ctx, SB_ERR_UNSUPPORTED, "check_probe: this library was built without SB_CHECKS (libsb_checks.so has them)");
+#endif
+}
+
+int32_t sb_checks_built(void) {
+#ifdef SB_CHECKS
+  return 1;
+#else
+  return 0;
+#endif
 }
 
 sb_status sb_rgb_to_lightness(sb_context* ctx, const uint8_t* rgb, int32_t w, int32_t h, uint8_t* L, uint32_t* hist) {
@@ -1523,7 +1610,11 @@ extern "C" sb_status sb_run(sb_context* ctx, const sb_pair* pairs, int32_t n_pai
   }
   if (n_pairs == 0) return SB_OK;
   cudaSetDevice(ctx->device);
-  if (flags & SB_RUN_HOST_IO) return run_host_io(ctx, pairs, n_pairs, (flags & SB_RUN_BATCHED) != 0);
-  if (flags & SB_RUN_GRAPH) return run_graph(ctx, pairs, n_pairs);
-  return run_device(ctx, pairs, n_pairs, (flags & SB_RUN_BATCHED) != 0);
+  nvtxRangePushA("sb:run");
+  sb_status st;
+  if (flags & SB_RUN_HOST_IO) st = run_host_io(ctx, pairs, n_pairs, (flags & SB_RUN_BATCHED) != 0);
+  else if (flags & SB_RUN_GRAPH) st = run_graph(ctx, pairs, n_pairs);
+  else st = run_device(ctx, pairs, n_pairs, (flags & SB_RUN_BATCHED) != 0);
+  nvtxRangePop();
+  return st;
 }

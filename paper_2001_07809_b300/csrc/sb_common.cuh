@@ -21,6 +21,46 @@ namespace sb {
 enum : uint32_t { DEV_ERR_CCA_ITER = 1u };
 constexpr int kUnionLimitDefault = 1 << 22;   // parent links and union retries (sb_set_union_limit)
 
+// ------------------------------------------------------------ bounds checks
+// The bounds-checked build (-DSB_CHECKS, libsb_checks.so) evaluates
+// SB_CHECK(cond, site) before the accesses whose index comes from data
+// (labels, parent links, root lists, work-item tables, anchor positions): a
+// false condition records `site` in the translation unit's check word (the
+// first failure wins), and the caller skips the access, so the kernel runs on
+// without touching memory out of range.  sb_synchronize reads and clears the
+// words and reports SB_ERR_CHECK with the site.  Sites: 1 the probe
+// (sb_check_probe), 1xx lightness / k-means, 2xx refinement, 3xx components,
+// 4xx SAD, 5xx reconstruction, 6xx blur.  In the normal build
+// SB_CHECK(cond, site) is `true` and cond is not evaluated.
+#ifdef SB_CHECKS
+static __device__ uint32_t g_check_site;   // one per translation unit
+__device__ __forceinline__ bool sb_check(bool ok, uint32_t site) {
+  if (!ok) atomicCAS(&g_check_site, 0u, site);
+  return ok;
+}
+#define SB_CHECK(cond, site) ::sb::sb_check((cond), (site))
+// checks_<unit>(): this unit's check word, cleared (0: no check failed)
+#define SB_CHECKS_UNIT(unit)                                                  \
+  uint32_t checks_##unit() {                                                  \
+    uint32_t v = 0, z = 0;                                                    \
+    if (cudaMemcpyFromSymbol(&v, g_check_site, sizeof v) != cudaSuccess) return 0; \
+    if (v) cudaMemcpyToSymbol(g_check_site, &z, sizeof z);                    \
+    return v;                                                                 \
+  }
+#else
+#define SB_CHECK(cond, site) true
+#define SB_CHECKS_UNIT(unit) \
+  uint32_t checks_##unit() { return 0; }
+#endif
+uint32_t checks_segment();
+uint32_t checks_morph();
+uint32_t checks_cca();
+uint32_t checks_sad();
+uint32_t checks_recon();
+uint32_t checks_blur();
+uint32_t checks_api();
+uint32_t checks_noalloc();
+
 // ---------------------------------------------------------------- lightness
 struct LightJob {
   const uint8_t* rgb;  // n_px * 3

@@ -116,6 +116,7 @@ __global__ void k_static_setup(StaticPlan P, uint8_t* desc) {
   }
   SadItem* items = reinterpret_cast<SadItem*>(desc + kItemsOff);
   for (int i = tid; i < P.n_box + P.n_tail; i += gridDim.x * blockDim.x) {
+    if (!SB_CHECK(i < kMaxItems, 701u)) break;   // the host rejects larger plans
     SadItem it;
     it.job = 0;
     if (i < P.n_box) {
@@ -290,3 +291,7 @@ extern "C" sb_status sb_boundary_sad_static(const uint8_t* L_left, const uint8_t
   }
   return SB_OK;
 }
+
+namespace sb {
+SB_CHECKS_UNIT(noalloc)
+}  // namespace sb

@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -14,14 +16,27 @@ def _declared():
     return sorted(n for n in names if not n.startswith("sb_status"))
 
 
-def test_library_builds_and_exports_every_declared_symbol():
+@pytest.mark.parametrize("checks", [False, True], ids=["libsb", "libsb_checks"])
+def test_library_builds_and_exports_every_declared_symbol(checks):
     from paper_2001_07809_b300 import build
-    path = build.build()
+    path = build.build(checks=checks)
     lib = ctypes.CDLL(path)
     names = _declared()
     assert "sb_run" in names and "sb_boundary_sad" in names and len(names) >= 14
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, missing
+    assert lib.sb_checks_built() == (1 if checks else 0)   # host-only call
+
+
+def test_nvtx_recorder_compiles():
+    # the NVTX injection library the GPU tests load to observe the stage ranges
+    import subprocess, tempfile
+    with tempfile.TemporaryDirectory() as d:
+        out = os.path.join(d, "librec.so")
+        subprocess.check_call(["gcc", "-shared", "-fPIC", "-Wall", "-Werror", "-I", "/usr/local/cuda/include",
+                               os.path.join(ROOT, "tests", "nvtx_recorder.c"), "-o", out])
+        lib = ctypes.CDLL(out)
+        assert hasattr(lib, "InitializeInjectionNvtx2")
 
 
 def test_header_compiles_as_c():

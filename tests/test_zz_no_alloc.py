@@ -62,6 +62,30 @@ def test_static_entry_matches_context_entry_twice(variant):
         ctx.close()
 
 
+# disparity ranges around the chunk of 64 (a partial chunk, whole chunks, a
+# tail of 1..8 disparities, a remainder of 9 taken by the box sums), D = 0 and
+# block 1, widths with and without the 16-byte row phase, several row bands
+STATIC_CASES = [
+    (40, 160, 63, 9), (45, 171, 64, 9), (45, 176, 65, 9), (50, 272, 127, 11), (33, 301, 128, 7),
+    (64, 480, 200, 15), (48, 560, 256, 21), (31, 97, 0, 1), (26, 90, 7, 1), (200, 304, 72, 41),
+]
+
+
+@pytest.mark.parametrize("h,w,D,B", STATIC_CASES)
+def test_static_entry_equals_oracle(h, w, D, B):
+    import oracle
+    rng = np.random.default_rng(h * 7919 + w * 31 + D)
+    f = _static_fn()
+    Ll = rng.integers(0, 256, (h, w)).astype(np.uint8)
+    Lr = np.clip(np.roll(Ll, -(D // 3), axis=1).astype(int) + rng.integers(-6, 7, (h, w)), 0, 255).astype(np.uint8)
+    bmap = (rng.random((h, w)) < 0.25).astype(np.uint8)
+    want_d, want_c = oracle.boundary_sad(Ll, Lr, oracle.anchor_mask(bmap, D, B), D, B)
+    for variant in (sb.SB_SAD_BOXSUM, sb.SB_SAD_DIRECT):
+        got_d, got_c = _call_static(f, Ll, Lr, bmap, D, B, variant)
+        assert np.array_equal(got_d, want_d), variant
+        assert np.array_equal(got_c, want_c), variant
+
+
 def test_static_entry_rejects_images_above_the_limit():
     f = _static_fn()
     h, w = 2049, 2049                       # 4,198,401 pixels > 4,194,304
