@@ -86,12 +86,14 @@ namespace {
 // steps after the warm-up (n0 + K + 1), so Shi = H - n * 0x4000 and
 // Slo = T - (Shi << 16) - n * 0x40004000.  The lane's two keys
 // (S << 10 | d) are reduced in the lane, then over the warp (redux.sync) for
-// every anchor of the nibble first, then lane 0 keeps the minima with
-// atomicMin, so that the reductions' latencies overlap.  Disparities past D
-// carry all-ones low bits, which makes their key all ones (never the minimum).
+// every anchor of the nibble first, so that the reductions' latencies
+// overlap; the warp minimum of output o of the 32-output span goes to lane o
+// (`best`, lrel = lane - the block's first output in the span), which keeps
+// it with one atomicMin for the whole span.  Disparities past D carry
+// all-ones low bits, which makes their key all ones (never the minimum).
 template <unsigned NIB, int K0>
 __device__ __forceinline__ void emit_nibble(const uint32_t (&Tv)[8], const uint32_t (&Hv)[8], uint32_t n0,
-                                            uint32_t dlo, uint32_t dhi, uint32_t* kp, int lane) {
+                                            uint32_t dlo, uint32_t dhi, uint32_t& best, int lrel) {
   uint32_t m[4];
 #pragma unroll
   for (int b = 0; b < 4; ++b)
@@ -102,21 +104,19 @@ __device__ __forceinline__ void emit_nibble(const uint32_t (&Tv)[8], const uint3
       const uint32_t k = min((slo << SB_KEY_DBITS) | dlo, (shi << SB_KEY_DBITS) | dhi);
       m[b] = __reduce_min_sync(0xffffffffu, k);
     }
-  if (lane == 0) {
 #pragma unroll
-    for (int b = 0; b < 4; ++b)
-      if (NIB & (1u << b)) atomicMin(kp + K0 + b, m[b]);
-  }
+  for (int b = 0; b < 4; ++b)
+    if (NIB & (1u << b)) best = lrel == K0 + b ? m[b] : best;
 }
 
 // one case per non-empty nibble value: the bits are warp-uniform, so the
 // switch is a uniform jump and every case's code is straight-line
 template <int K0>
 __device__ __forceinline__ void emit_block_half(unsigned nib, const uint32_t (&Tv)[8], const uint32_t (&Hv)[8],
-                                                uint32_t n0, uint32_t dlo, uint32_t dhi, uint32_t* kp, int lane) {
+                                                uint32_t n0, uint32_t dlo, uint32_t dhi, uint32_t& best, int lrel) {
   switch (nib) {
 #define SB_EMIT_CASE(v) \
-  case v: emit_nibble<v, K0>(Tv, Hv, n0, dlo, dhi, kp, lane); break;
+  case v: emit_nibble<v, K0>(Tv, Hv, n0, dlo, dhi, best, lrel); break;
     SB_EMIT_CASE(1) SB_EMIT_CASE(2) SB_EMIT_CASE(3) SB_EMIT_CASE(4) SB_EMIT_CASE(5)
     SB_EMIT_CASE(6) SB_EMIT_CASE(7) SB_EMIT_CASE(8) SB_EMIT_CASE(9) SB_EMIT_CASE(10)
     SB_EMIT_CASE(11) SB_EMIT_CASE(12) SB_EMIT_CASE(13) SB_EMIT_CASE(14) SB_EMIT_CASE(15)
@@ -156,7 +156,7 @@ __device__ __forceinline__ void vertical_row(uint32_t (&Ve)[16], uint32_t (&Vo)[
 // multiple of 16, so the 16-byte phase of a strip column is the same in every
 // row and the vertical pass of the rows past the warm-up uses the item's
 // constant offsets.
-template <bool W16>
+template <bool W16, int RC>
 __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __restrict__ jobs,
                                                             const SadItem* __restrict__ items, int n_items,
                                                             unsigned* __restrict__ queue) {
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
     if (!SB_CHECK(it.y0 >= J.r && it.y0 <= it.y1 && it.y1 <= J.h - 1 - J.r && it.x0 >= J.D + J.r &&
                   it.x0 < J.w - J.r && it.d0 >= 0 && it.d0 <= J.D && it.d0 % kSadChunk == 0, 401u))
       continue;
-    const int r = J.r, D = J.D, w = J.w;
+    const int r = RC > 0 ? RC : J.r, D = J.D, w = J.w;     // RC: every job's radius, known at compile time
     const int64_t npx = (int64_t)w * J.h;
     const int ring = 2 * r + 1 + 2 * kG;                    // + one group staged ahead
     const int VC = box_vcols(r);
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
             uint32_t T1 = 0, T2 = 0, T3 = 0, H1 = 0, H2 = 0, H3 = 0;
             const uint32_t* p = vcol + xa * CW;
             int j = 0;
-#pragma unroll 1
+#pragma unroll(RC > 0 ? 16 : 1)
             for (; j + 4 <= 2 * r + 1; j += 4, p += 4 * CW) {
               const uint32_t v0 = p[0], v1 = p[CW], v2 = p[2 * CW], v3 = p[3 * CW];
               T += v0; H += v0 >> 16;
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
               T2 += v2; H2 += v2 >> 16;
               T3 += v3; H3 += v3 >> 16;
             }
-#pragma unroll 1
+#pragma unroll(RC > 0 ? 4 : 1)
             for (; j <= 2 * r; ++j, p += CW) {
               const uint32_t v = p[0];
               T += v;
@@ -367,6 +367,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
             const int n = min(32, xb - xbase);
             const uint32_t* pin = vcol + (xbase + 2 * r + 1) * CW;  // slot column of strip column x + 2r
             const uint32_t* pout = vcol + xbase * CW;             // slot column of x - 1
+            uint32_t best = 0xFFFFFFFFu;                          // lane o: the key of output xbase + o
 #pragma unroll 1
             for (int i = 0; i < n; i += 8) {
               uint32_t Tv[8], Hv[8];
@@ -379,10 +380,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
                 Hv[k] = H;
               }
               const unsigned bits = (mask >> i) & 0xFFu;
-              emit_block_half<0>(bits & 15u, Tv, Hv, n0, dlo, dhi, krow + xbase + i, lane);
-              emit_block_half<4>(bits >> 4, Tv, Hv, n0, dlo, dhi, krow + xbase + i, lane);
+              emit_block_half<0>(bits & 15u, Tv, Hv, n0, dlo, dhi, best, lane - i);
+              emit_block_half<4>(bits >> 4, Tv, Hv, n0, dlo, dhi, best, lane - i);
               n0 += 8;
             }
+            if ((mask >> lane) & 1u) atomicMin(krow + xbase + lane, best);   // one per anchor of the span
             bcur = bnext;
           }
         }
@@ -583,24 +585,38 @@ int sad_boxsum_smem_bytes(int r) {
   return (ring + 1) * kRowBytes + 2 * kG * kBBytes + kG * box_vcols(r) * kColBytes;
 }
 
-template <bool W16>
+template <bool W16, int RC>
 static void launch_box(const SadJob* jobs, const SadItem* items, int n_items, int smem, unsigned* queue,
                        cudaStream_t s) {
-  cudaFuncSetAttribute(k_sad_boxsum<W16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_sad_boxsum<W16, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   int dev = 0, sms = 148, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sad_boxsum<W16>, kThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sad_boxsum<W16, RC>, kThreads, smem);
   const int grid = std::min(n_items, sms * std::max(1, per_sm));
-  k_sad_boxsum<W16><<<grid, kThreads, smem, s>>>(jobs, items, n_items, queue);
+  k_sad_boxsum<W16, RC><<<grid, kThreads, smem, s>>>(jobs, items, n_items, queue);
 }
 
-void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, bool w16, unsigned* queue,
-                       cudaStream_t s) {
+template <bool W16>
+static void launch_box_r(const SadJob* jobs, const SadItem* items, int n_items, int smem, int uniform_r,
+                         unsigned* queue, cudaStream_t s) {
+  // instances with the radius of the benchmark blocks (15, 31 and 41) built in, so the
+  // horizontal warm-up over 2r + 1 columns is unrolled; any other radius, or a launch
+  // mixing radii, takes the radius from each job
+  switch (uniform_r) {
+    case 7: launch_box<W16, 7>(jobs, items, n_items, smem, queue, s); break;
+    case 15: launch_box<W16, 15>(jobs, items, n_items, smem, queue, s); break;
+    case 20: launch_box<W16, 20>(jobs, items, n_items, smem, queue, s); break;
+    default: launch_box<W16, 0>(jobs, items, n_items, smem, queue, s); break;
+  }
+}
+
+void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, int uniform_r, bool w16,
+                       unsigned* queue, cudaStream_t s) {
   if (n_items <= 0) return;
   const int smem = sad_boxsum_smem_bytes(max_r);
-  if (w16) launch_box<true>(jobs, items, n_items, smem, queue, s);
-  else launch_box<false>(jobs, items, n_items, smem, queue, s);
+  if (w16) launch_box_r<true>(jobs, items, n_items, smem, uniform_r, queue, s);
+  else launch_box_r<false>(jobs, items, n_items, smem, uniform_r, queue, s);
 }
 
 // ----------------------------------------------------------------- direct

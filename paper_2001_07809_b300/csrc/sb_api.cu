@@ -727,18 +727,19 @@ sb_status enqueue_pipeline(sb_context* ctx, std::vector<PairRun>& runs) {
       if (!di) return st;
       const SadItem* dt = tail.empty() ? nullptr : upload(ctx, tail, &st);
       if (!tail.empty() && !dt) return st;
-      int max_r = 0;
+      int max_r = 0, uniform_r = (box[0].second.p.block - 1) / 2;
       int max_rem = 1;
       bool w16 = true;   // every box-sum pair's width a multiple of 16
       for (auto& b : box) {
         max_r = std::max(max_r, (b.second.p.block - 1) / 2);
+        if ((b.second.p.block - 1) / 2 != uniform_r) uniform_r = -1;
         w16 = w16 && b.second.w % 16 == 0;
         if (sad_has_tail(b.second.p.max_disp))
           max_rem = std::max(max_rem, b.second.p.max_disp + 1 - sad_tail_first(b.second.p.max_disp));
       }
       SB_MEMSET(ctx, (ctx->sad_queue, 0, 8, s));
       if (!ctx->dry) {
-        launch_sad_boxsum(d, di, (int)items.size(), max_r, w16, ctx->sad_queue, s);
+        launch_sad_boxsum(d, di, (int)items.size(), max_r, uniform_r, w16, ctx->sad_queue, s);
         SB_LAUNCHED(ctx, 1);
       }
       SB_MARK(ctx, SB_STAGE_SAD_REST);
@@ -1131,7 +1132,7 @@ sb_status sb_boundary_sad(sb_context* ctx, const uint8_t* L_left, const uint8_t*
     const SadItem* dt = tail.empty() ? nullptr : upload(ctx, tail, &st);
     if (!tail.empty() && !dt) return st;
     SB_CUDA(ctx, cudaMemsetAsync(ctx->sad_queue, 0, 8, s));
-    launch_sad_boxsum(d, di, (int)items.size(), (block - 1) / 2, w % 16 == 0, ctx->sad_queue, s);
+    launch_sad_boxsum(d, di, (int)items.size(), (block - 1) / 2, (block - 1) / 2, w % 16 == 0, ctx->sad_queue, s);
     SB_LAUNCHED(ctx, 1);
     if (!tail.empty()) {
       launch_sad_tail(d, dt, (int)tail.size(), max_disp + 1 - sad_tail_first(max_disp), ctx->sad_queue + 1, s);

@@ -187,9 +187,11 @@ __host__ __device__ inline int sad_tail_strip(int r) { return (256 - 2 * r) & ~3
 void launch_sad_tail(const SadJob* jobs, const SadItem* items, int n_items, int max_rem, unsigned* queue,
                      cudaStream_t s);
 // max_r: the largest block radius among the items (sizes shared memory);
+// uniform_r: the radius every item's job has, or -1 when they differ;
 // w16: every job's image width is a multiple of 16 (constant row phases);
 // queue: one device counter, zero before the launch (the kernel's work-item cursor)
-void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, bool w16, unsigned* queue,
+void launch_sad_boxsum(const SadJob* jobs, const SadItem* items, int n_items, int max_r, int uniform_r, bool w16,
+                       unsigned* queue,
                        cudaStream_t s);
 // the direct kernel for the jobs whose window spans nw = sad_direct_words(block) words
 int sad_direct_words(int block);

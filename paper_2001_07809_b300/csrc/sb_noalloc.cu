@@ -279,7 +279,7 @@ extern "C" sb_status sb_boundary_sad_static(const uint8_t* L_left, const uint8_t
     launch_count_nonzero((const uint8_t* const*)(desc + kCountOff), (const int64_t*)(desc + kCountOff + 8),
                          (int64_t*)(desc + kCountOff + 16), 1, s);
   if (run_box) {
-    launch_sad_boxsum(djob, items, P.n_box, r, w % 16 == 0, queue, s);
+    launch_sad_boxsum(djob, items, P.n_box, r, r, w % 16 == 0, queue, s);
     if (P.n_tail > 0) launch_sad_tail(djob, items + P.n_box, P.n_tail, max_disp + 1 - P.dt0, queue + 1, s);
   }
   if (run_direct) launch_sad_direct(djob, 1, sad_direct_words(block), r, max_disp, s);
