@@ -53,14 +53,14 @@ INTEREST_C3 = [(120, 256)]
 # algorithmic integer operations of the box-sum SAD per (domain pixel, disparity):
 # one |L - R|, two vertical running-sum updates, two horizontal, one compare
 BOX_OPS_PER_PXD = 6
-# disparities the box-sum kernel covers at D=256: its chunks of 32 stop at 256, and the
+# disparities the box-sum kernel covers at D=256: its chunks of 64 stop at 256, and the
 # tail disparity d=256 runs in its own kernel (timed in the "sad_rest" stage)
 BOX_DISPARITIES_C3 = 256
 # DRAM bytes of k_sad_boxsum per 4096x2304 pair (D=256, block 41, d = 0..255): the ncu
-# capture of one 8-pair launch read 498.54 MB and wrote 191.32 MB (L maps and boundary map
+# capture of one 8-pair launch read 506.99 MB and wrote 197.64 MB (L maps and boundary map
 # in, argmin keys out); a launch over P pairs moves P times that, since each pair's data is
 # its own
-SAD_DRAM_BYTES_PER_PAIR = (498.537216e6 + 191.321344e6) / 8
+SAD_DRAM_BYTES_PER_PAIR = (506.99e6 + 197.64e6) / 8
 METRIC = "stereo pairs/s at 4096x2304 (batched vs per-pair), SAD Gcell/s, p99 latency"
 # --sad-variant: the library's per-pair choice (box sums at this workload's density), or either
 # SAD kernel forced (the roofline then describes that kernel)
