@@ -388,6 +388,10 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
   extern __shared__ __align__(16) float fsm[];
   __shared__ uint32_t s_mbits[kBandRows * BX / 32];   // 1 = blurred
   __shared__ int s_flag[kMaxSteps];
+  // bit q of s_vq[h]: output rows 16q .. 16q + 15 of the band hold a blurred pixel in
+  // columns 32h .. 32h + 31 (one vertical task block of a warp: OB rows x 32 columns)
+  __shared__ uint32_t s_vq[2];
+  static_assert(2 * kMaxSteps <= 32 && kSB == 2 * OB, "two task blocks per step, one bit each");
   __shared__ int s_lo[8], s_hi[8];
   __shared__ uint8_t s_off[2][kSB];
   const BlurJob J = jobs[blockIdx.z];
@@ -457,10 +461,18 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
     }
   }
   __syncthreads();
+  if (tid < 2) s_vq[tid] = 0u;
+  __syncthreads();
   for (int st = tid; st < nsteps; st += kStripThreads) {
     int any = 0;
     for (int q = st * kSB * (BX / 32); q < (st + 1) * kSB * (BX / 32); ++q) any |= s_mbits[q] != 0u;
     s_flag[st] = any;
+  }
+  if (tid < 2 * 2 * nsteps) {   // thread (q, half): task block q, columns 32 half ..
+    const int q = tid >> 1, hf = tid & 1;
+    uint32_t any = 0;
+    for (int i = 0; i < OB; ++i) any |= s_mbits[(OB * q + i) * (BX / 32) + hf];
+    if (any) atomicOr(&s_vq[hf], 1u << q);
   }
   __syncthreads();
   int any_step = 0;
@@ -488,15 +500,16 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
   const int nbatch = nfill + nsteps - 1;
   auto batch_row0 = [&](int k) { return k < nfill ? yb0 - R + kSB * k : yb0 + kSB * (k - nfill + 1) + R + 1; };
   auto batch_rows = [&](int k) { return k < nfill ? min(kSB, F - kSB * k) : kSB; };
-  // does any blurred step read rows a .. a + n - 1?  step t reads y_t - R .. y_t + kSB + R
-  auto batch_needed = [&](int k) {
-    if (k < nfill) return true;
-    const int a = batch_row0(k), b = a + batch_rows(k) - 1;
-    for (int t = 0; t < nsteps; ++t) {
-      const int yt = yb0 + kSB * t;
-      if (s_flag[t] && yt - R <= b && yt + kSB + R >= a) return true;
-    }
-    return false;
+  // the column halves of batch k some running vertical task block reads: block q
+  // (output rows yb0 + 16q .. + 15) reads rows yb0 + 16q - R .. yb0 + 16q + 15 + R
+  auto batch_halves = [&](int k) -> unsigned {
+    const int a = batch_row0(k) - yb0, b = a + batch_rows(k) - 1;
+    // q0 = ceil((a - (OB - 1) - R) / OB), q1 = floor((b + R) / OB); a >= -R and R <= 96 keep the shifted
+    // numerators positive, so the divisions round down
+    const int q0 = max(0, (a - R + 16 * OB) / OB - 16), q1 = min(2 * nsteps - 1, (b + R + 16 * OB) / OB - 16);
+    if (q0 > q1) return 0u;
+    const uint32_t range = (q1 - q0 == 31 ? 0xffffffffu : ((2u << (q1 - q0)) - 1u)) << q0;
+    return ((s_vq[0] & range) ? 1u : 0u) | ((s_vq[1] & range) ? 2u : 0u);
   };
   auto stage = [&](int k, int buf) {
     const int a = batch_row0(k), n = batch_rows(k);
@@ -537,12 +550,18 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
     if (i < nrow) cp_async16(s_out + i * (BX * 3) + 16 * q, J.rgb + ((int64_t)(ys + i) * w + tx0) * 3 + 16 * q);
     asm volatile("cp.async.commit_group;\n" ::);
   };
+  // task = (column half, row, channel, block of OB outputs), half outermost so that
+  // a warp's tasks share a half; a half no running vertical block reads is skipped
   auto hpass = [&](int k, int buf) {
     const int a = batch_row0(k), n = batch_rows(k);
+    const unsigned halves = batch_halves(k);
     const uint8_t* base = s_in + buf * kSB * sr;
+    constexpr int kPerRow = 3 * (BX / 2 / OB);   // tasks of one row and half
     for (int task = tid; task < n * 3 * (BX / OB); task += kStripThreads) {
-      const int i = task / (3 * (BX / OB)), rest = task - i * (3 * (BX / OB));
-      const int ch = rest / (BX / OB), j0 = (rest - ch * (BX / OB)) * OB;
+      const int hf = task / (n * kPerRow), r2 = task - hf * (n * kPerRow);
+      if (!((halves >> hf) & 1u)) continue;
+      const int i = r2 / kPerRow, rest = r2 - i * kPerRow;
+      const int ch = rest / (BX / 2 / OB), j0 = hf * (BX / 2) + (rest - ch * (BX / 2 / OB)) * OB;
       const uint8_t* in = base + i * sr + s_off[buf][i] + j0 * 3 + ch;   // output j0+o uses in[3(o .. o+2R)]
       float acc[OB];
       conv16(acc, s_tap, nt, [in](int j) { return u8f(in[j * 3]); });
@@ -569,9 +588,13 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
       const int col = tid % BX, rest = tid / BX, ch = rest % 3, blk = rest / 3;
       const int i0 = blk * OB;
       const int b0 = slot(ys + i0 - R);
+      // a warp's tasks are 32 columns (one word of a mask row) x OB rows of one
+      // channel; in the staged-output form a warp none of whose pixels is
+      // blurred has nothing to write and skips its convolution
+      const bool need = (s_vq[col >> 5] >> (2 * st + blk)) & 1u;
       float acc[OB];
-      conv16_ring(acc, s_tap, nt, s_h + ch * (M * HS + kChPad) + col, b0, M);
-      if (vout) {
+      if (need) conv16_ring(acc, s_tap, nt, s_h + ch * (M * HS + kChPad) + col, b0, M);
+      if (vout && need) {
 #pragma unroll
         for (int o = 0; o < OB; ++o) {
           const int i = i0 + o;
@@ -618,7 +641,7 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
       if (vout) prefetch(st + 1);   // s_out was stored before the barrier
       if (k + 1 < nbatch) stage(k + 1, (k + 1) & 1);
       else if (vout) asm volatile("cp.async.commit_group;\n" ::);   // (an empty group)
-      if (batch_needed(k)) hpass(k, k & 1);
+      if (batch_halves(k)) hpass(k, k & 1);
     }
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
