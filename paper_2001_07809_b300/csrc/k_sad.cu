@@ -5,24 +5,26 @@
 //
 // Box-sum variant (dense over the domain, O(|Omega| d) with a few integer
 // operations per pixel and disparity): a CTA owns a strip of TX output
-// columns, a band of rows and a chunk of 32 disparities.
-//   Stage A: thread t owns column c = x0 - r + t and keeps the 32 vertical
+// columns, a band of rows and a chunk of 64 disparities.
+//   Stage A: thread t owns column c = x0 - r + t and keeps the 64 vertical
 //     window sums V_d(y, c) = sum_{|i|<=r} |L(y+i, c) - R(y+i, c-d)| in
-//     registers as 16 packed u16 pairs, sliding down one row per step.  Four
+//     registers as 32 packed u16 pairs, sliding down one row per step.  Four
 //     disparities at a time: one packed |L - R| of four bytes for the
 //     entering row and one for the leaving row (vabsdiff4), split into even
 //     and odd bytes (lop3 / prmt), and lane-wise u16 add-subtract (iadd3).
 //     Rows are staged with cp.async into a shared-memory ring one group of
 //     rows ahead, so every byte is read from HBM once per CTA and the copy
 //     overlaps the arithmetic.
-//   Stage B: lanes = disparities; a warp slides the horizontal sum
-//     S = sum_{|j|<=r} V(c+j) along its row segment in blocks of 8 outputs
-//     (a zero column before each row of column sums lets every output use
-//     the same add-entering / drop-leaving update) and, at anchor pixels
-//     (warp-uniform bits, one uniform jump per four outputs), reduces
-//     (S << 10 | d) over the 32 lanes with redux.sync and atomically keeps
-//     the minimum in the per-pixel key.
-// Tail kernel: the 1..8 disparities past the last whole chunk of 32 (one
+//   Stage B: lanes = disparity pairs (one 32-bit word of a column slot holds
+//     a lane's two u16 column sums); a warp slides the horizontal sums along
+//     its row segment in blocks of 8 outputs with two running words (the
+//     packed pair and its upper half, recovered exactly at anchors; a zero
+//     column before each row of column sums lets every output use the same
+//     add-entering / drop-leaving update).  At anchor pixels (warp-uniform
+//     bits, one uniform jump per four outputs) it reduces (S << 10 | d) over
+//     the warp with redux.sync; lane o keeps the minimum of output o of the
+//     32-output span, and one atomicMin per span keeps it in the per-pixel key.
+// Tail kernel: the 1..8 disparities past the last whole chunk of 64 (one
 // disparity at D = 2^n), a thread per column with the vertical sums and a
 // warp prefix sum per row for the horizontal ones, so the box-sum work list
 // need not spend a mostly idle chunk on them.
