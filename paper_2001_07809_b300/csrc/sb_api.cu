@@ -464,8 +464,23 @@ void sad_items(const std::vector<std::pair<int, Geo>>& pairs, int64_t target, in
     const int xo0 = D + r, xo1 = g.w - 1 - r, yo0 = r, yo1 = g.h - 1 - r;
     const int rows = yo1 - yo0 + 1;
     const int dend = sad_has_tail(D) ? sad_tail_first(D) : D + 1;   // box-sum chunks cover d < dend
-    int bands = (int)std::max<int64_t>(1, (target + base - 1) / std::max<int64_t>(base, 1));
-    bands = std::min(bands, std::max(1, rows / std::max(8 * r, 64)));
+    // row bands: enough items for `target` (bands of at least max(8r, 64) rows, so the
+    // 2r warm-up rows stay a small share); where that still leaves CTA slots of the
+    // persistent grid (two per SM) idle — a single small pair — the count, with bands of
+    // at least 8 rows, that minimises (rounds of the grid) x (band rows + r), r weighing
+    // the warm-up rows, which run the vertical pass only: the pair's time is then the
+    // walk down one band
+    const int64_t box_slots = (int64_t)sms * 2;
+    const int64_t per_target = std::max<int64_t>(1, (target + base - 1) / std::max<int64_t>(base, 1));
+    int bands = (int)std::min<int64_t>(per_target, std::max(1, rows / std::max(8 * r, 64)));
+    if (base * bands < box_slots) {
+      const int cap = (int)std::min<int64_t>(per_target, std::max(1, rows / 8));
+      int64_t best_cost = -1;
+      for (int t = 1; t <= cap; ++t) {
+        const int64_t c = (base * t + box_slots - 1) / box_slots * ((rows + t - 1) / t + r);
+        if (best_cost < 0 || c < best_cost) { best_cost = c; bands = t; }
+      }
+    }
     for (int b = 0; b < bands; ++b) {
       const int ya = yo0 + (int)((int64_t)rows * b / bands), yb = yo0 + (int)((int64_t)rows * (b + 1) / bands) - 1;
       if (ya > yb) continue;

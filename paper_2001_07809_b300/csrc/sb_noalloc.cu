@@ -233,10 +233,20 @@ extern "C" sb_status sb_boundary_sad_static(const uint8_t* L_left, const uint8_t
   uint8_t* desc = base + kKeyBytes;
 
   if (run_box && P.n_box > 0) {
-    // row bands so that one pair fills three waves of the persistent grid (two CTAs per SM)
-    const int64_t target = (int64_t)sms * 2 * 3;
-    P.bands = (int)std::max<int64_t>(1, (target + P.n_box - 1) / P.n_box);
-    P.bands = std::min(P.bands, std::max(1, P.rows / std::max(8 * r, 64)));
+    // row bands as in the context path: enough items for three waves of the persistent
+    // grid (bands of at least max(8r, 64) rows); where that leaves CTA slots idle, the
+    // count (bands of at least 8 rows) that minimises (rounds) x (band rows + r)
+    const int64_t target = (int64_t)sms * 2 * 3, box_slots = (int64_t)sms * 2;
+    const int64_t per_target = std::max<int64_t>(1, (target + P.n_box - 1) / P.n_box);
+    P.bands = (int)std::min<int64_t>(per_target, std::max(1, P.rows / std::max(8 * r, 64)));
+    if ((int64_t)P.n_box * P.bands < box_slots) {
+      const int cap = (int)std::min<int64_t>(per_target, std::max(1, P.rows / 8));
+      int64_t best_cost = -1;
+      for (int t = 1; t <= cap; ++t) {
+        const int64_t c = ((int64_t)P.n_box * t + box_slots - 1) / box_slots * ((P.rows + t - 1) / t + r);
+        if (best_cost < 0 || c < best_cost) { best_cost = c; P.bands = t; }
+      }
+    }
     P.n_box *= P.bands;
   }
   if (run_box && tail) {
