@@ -413,8 +413,9 @@ def per_config_measure(sb, torch, steps=20, warmup=3):
     """The single-pair workloads c1 (320x240, D 32, block 15) and c2
     (1400x1100, D 128, block 31): the CPU oracle on the whole pair in one
     thread (timed once), and the plain per-pair GPU pipeline (sb_run per
-    call, `steps` timed calls after `warmup`), outputs checked against the
-    oracle's (disparity bit-exact, blur within one level)."""
+    call, `steps` timed calls after `warmup`) and the same pair as a one-pair
+    graph replay, outputs checked against the oracle's (disparity bit-exact,
+    blur within one level)."""
     import numpy as np
     import oracle
     import synth
@@ -440,13 +441,25 @@ def per_config_measure(sb, torch, steps=20, warmup=3):
         e1.record()
         torch.cuda.synchronize()
         gpu_ms = e0.elapsed_time(e1) / steps
+        # the same pair as a one-pair graph replay (no per-launch host work)
+        gflags = sb.SB_RUN_BATCHED | sb.SB_RUN_GRAPH
+        for _ in range(warmup):
+            sb.sb_run(ctx, pair, gflags)
+        ctx.synchronize()
+        e0.record()
+        for _ in range(steps):
+            sb.sb_run(ctx, pair, gflags)
+        e1.record()
+        torch.cuda.synchronize()
+        graph_ms = e0.elapsed_time(e1) / steps
         t0 = time.perf_counter()
         want = oracle.run(left, right, p)
         oracle_s = time.perf_counter() - t0
         got_d = d.cpu().numpy().view(np.uint16)
         got_rgb = o.cpu().numpy()
         res[name] = {"size": "%dx%d" % (w, h), "D": p.max_disp, "block": p.block, "K": p.k,
-                     "oracle_s": oracle_s, "oracle_threads": 1, "gpu_ms_per_pair": gpu_ms, "gpu_steps": steps,
+                     "oracle_s": oracle_s, "oracle_threads": 1, "gpu_ms_per_pair": gpu_ms,
+                     "gpu_ms_per_pair_graph": graph_ms, "gpu_steps": steps,
                      "gpu_over_oracle": oracle_s / (gpu_ms / 1000.0),
                      "disparity_equal": bool(np.array_equal(got_d, want.disp)),
                      "blur_max_diff": int(np.abs(got_rgb.astype(int) - want.out_rgb.astype(int)).max())}
