@@ -204,7 +204,7 @@ sb_status sb_set_blur_form(sb_context* ctx, int32_t form);
  * (left + right RGB) start near first_bytes at both ends of the batch and
  * double towards the middle up to max_bytes (at least one pair per chunk), so
  * the first upload and the last download, which nothing overlaps, stay short.
- * Defaults 256 MB and 3 GB; (0, 0) restores them; 0 < first_bytes <=
+ * Defaults 64 MB and 1 GB; (0, 0) restores them; 0 < first_bytes <=
  * max_bytes, else SB_ERR_INVALID_ARG.  Smaller chunks need less staging
  * memory (three times the largest chunk's inputs and outputs). */
 sb_status sb_set_host_chunk(sb_context* ctx, size_t first_bytes, size_t max_bytes);

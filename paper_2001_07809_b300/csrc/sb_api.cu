@@ -211,8 +211,8 @@ struct sb_context {
   int sad_target_override = 0;   // set while sb_autotune times a candidate
   int blur_by_override = 0;
   int union_limit = kUnionLimitDefault;   // connected components: parent links / union attempts
-  size_t host_first = (size_t)256 << 20;  // host-buffer streaming: first chunk's input bytes (ramp start)
-  size_t host_cap = (size_t)3072 << 20;   // and the largest chunk
+  size_t host_first = (size_t)64 << 20;   // host-buffer streaming: first chunk's input bytes (ramp start)
+  size_t host_cap = (size_t)1024 << 20;   // and the largest chunk
   int host_chunks = 0;                    // chunks of the last host-buffer run
   int sms = 148;
 };
@@ -1235,8 +1235,8 @@ sb_status sb_selective_blur(sb_context* ctx, const uint8_t* rgb, const uint16_t*
 sb_status sb_set_host_chunk(sb_context* ctx, size_t first_bytes, size_t max_bytes) {
   if (!ctx) return SB_ERR_INVALID_ARG;
   if (first_bytes == 0 && max_bytes == 0) {
-    ctx->host_first = (size_t)256 << 20;
-    ctx->host_cap = (size_t)3072 << 20;
+    ctx->host_first = (size_t)64 << 20;
+    ctx->host_cap = (size_t)1024 << 20;
     return SB_OK;
   }
   if (first_bytes == 0 || max_bytes < first_bytes)
@@ -1405,9 +1405,10 @@ sb_status run_graph(sb_context* ctx, const sb_pair* pairs, int n) {
 sb_status run_host_io(sb_context* ctx, const sb_pair* pairs, int n, bool batched) {
   if (!ctx->s_in) SB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking));
   if (!ctx->s_out) SB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking));
-  // chunking: up to 3 GB of inputs per chunk, at least one pair; the chunk
-  // size ramps up from 256 MB at the start and back down at the end, so the
-  // first upload (nothing to overlap it with yet) and the last download are short
+  // chunking: up to host_cap bytes of inputs per chunk (1 GB by default), at
+  // least one pair; the chunk size ramps up from host_first (64 MB) at the start
+  // and back down at the end, so the first upload (nothing to overlap it with
+  // yet) and the last download are short
   std::vector<std::pair<int, int>> chunks;
   if (!batched) {
     for (int i = 0; i < n; ++i) chunks.push_back({i, i + 1});
