@@ -310,7 +310,7 @@ def uneven_measure(sb, torch, n_pairs=64, steps=3):
 SERVE_RATES = (10.0, 25.0, 50.0, 100.0, 150.0, 200.0, 300.0, 400.0)
 
 
-def serve_measure(sb, torch, rates=SERVE_RATES, per_rate=250, pool=64, seed=7, saturate=2.0):
+def serve_measure(sb, torch, rates=SERVE_RATES, per_rate=250, pool=64, seed=7, saturate=2.0, n_streams=3):
     """Served form, workload c5: a stream of len(rates) * per_rate requests
     (2000 by default; seed 7) in segments of per_rate Poisson arrivals at each
     swept rate, into one continuous-batching server (40 GB admission budget),
@@ -369,7 +369,7 @@ def serve_measure(sb, torch, rates=SERVE_RATES, per_rate=250, pool=64, seed=7, s
     one_rate = len(lat) / sum(lat)
     out["one_by_one"] = {"requests": len(lat), "p50_ms": 1e3 * percentile(lat, 50),
                          "p99_ms": 1e3 * percentile(lat, 99), "pairs_s": one_rate}
-    srv = Server(0, mem_budget_bytes=40 << 30, max_batch=64)
+    srv = Server(0, mem_budget_bytes=40 << 30, max_batch=64, n_streams=n_streams)
     pending = threading.Semaphore(0)
 
     def done(f):

@@ -4,7 +4,8 @@ Requests (a stereo pair in pinned host memory plus its parameters) arrive at
 any time through ``Server.submit``.  A scheduler thread admits waiting
 requests in arrival order while their device-memory estimate fits the budget,
 batches everything admitted into one ``sb_run(SB_RUN_BATCHED)`` call on the
-first free stream (two streams, so a new batch overlaps the one on the GPU),
+first free stream (three by default, so new batches are copied in and
+launched while earlier ones compute),
 and resolves each request's future when its batch's completion event has
 fired.  Inputs, intermediate maps and results of admitted requests stay
 resident on the device until the batch completes; results are copied back to
@@ -57,7 +58,7 @@ class Request:
 
 
 class Server:
-    def __init__(self, device: int = 0, mem_budget_bytes: int = 40 << 30, max_batch: int = 64, n_streams: int = 2):
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 40 << 30, max_batch: int = 64, n_streams: int = 3):
         self.device = device
         self.budget = int(mem_budget_bytes)
         self.max_batch = max_batch
