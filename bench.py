@@ -377,10 +377,14 @@ def serve_measure(sb, torch, rates=SERVE_RATES, per_rate=250, pool=64, seed=7, s
             srv.recycle(f.result())
         pending.release()
 
-    # warm-up: every distinct pair twice, in one burst
+    # warm-up: every distinct pair twice, in one burst, then once alone (a lone
+    # request replays its shape's graph, captured on its first run)
     for i in range(2 * pool):
         srv.submit(*reqs[i % pool]).add_done_callback(done)
     for _ in range(2 * pool):
+        pending.acquire(timeout=300)
+    for i in range(pool):
+        srv.submit(*reqs[i]).add_done_callback(done)
         pending.acquire(timeout=300)
     segments = []
     plan = [(r, i * per_rate) for i, r in enumerate(rates)] + [(saturate * one_rate, n_total)]

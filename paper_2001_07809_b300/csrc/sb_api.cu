@@ -165,6 +165,10 @@ std::vector<float> gauss_taps(float sigma, int* R_out) {
 }  // namespace
 
 // ------------------------------------------------------------------ context
+// batch shapes whose graphs a context keeps instantiated (each holds only its
+// kernel nodes; the job blob and the workspace are the context's)
+constexpr size_t kGraphCacheMax = 64;
+
 struct sb_context {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -180,12 +184,19 @@ struct sb_context {
   bool ws_pooled = false;            // ws came from ws_pool
   Uploader up;
   cudaStream_t s_in = nullptr, s_out = nullptr;  // host-buffer streaming
-  // graph cache (batched form)
+  // graph cache (batched form): the instantiated graphs of the most recent
+  // batch shapes, least recently used first out
   struct GraphEntry {
-    std::string key;
     cudaGraphExec_t exec = nullptr;
+    uint64_t kernels = 0;   // kernel nodes (for sb_launch_count)
+    uint64_t used = 0;      // last use (a counter)
   };
-  GraphEntry graph;
+  std::map<std::string, GraphEntry> graphs;
+  uint64_t graph_clock = 0;
+  void drop_graphs() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.second.exec);
+    graphs.clear();
+  }
   // host-buffer staging
   uint8_t* stage = nullptr;
   size_t stage_bytes = 0;
@@ -203,7 +214,6 @@ struct sb_context {
   bool prof_recorded = false;
   bool nvtx_open = false;   // a stage's NVTX range is pushed
   bool capturing = false;
-  uint64_t graph_kernels = 0;
   // autotune cache: launch-group shape (each pair's w, h, D, block) -> the
   // box-sum SAD's work-item target chosen by sb_autotune
   std::map<std::string, int> tuned;
@@ -914,7 +924,7 @@ void sb_destroy(sb_context* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   ctx->up.release();
-  if (ctx->graph.exec) cudaGraphExecDestroy(ctx->graph.exec);
+  ctx->drop_graphs();
   if (ctx->blob_dev) cudaFree(ctx->blob_dev);
   if (ctx->blob_host) cudaFreeHost(ctx->blob_host);
   if (ctx->blob_ev) cudaEventDestroy(ctx->blob_ev);
@@ -954,10 +964,7 @@ sb_status sb_profile_enable(sb_context* ctx, int on) {
   if (!ctx) return SB_ERR_INVALID_ARG;
   if (on && !ctx->prof_ev[0])
     for (int i = 0; i <= SB_N_STAGES; ++i) SB_CUDA(ctx, cudaEventCreate(&ctx->prof_ev[i]));
-  if (ctx->prof_on != (on != 0) && ctx->graph.exec) {  // captured graphs hold (or lack) the marks
-    cudaGraphExecDestroy(ctx->graph.exec);
-    ctx->graph.exec = nullptr;
-  }
+  if (ctx->prof_on != (on != 0)) ctx->drop_graphs();  // captured graphs hold (or lack) the marks
   ctx->prof_on = on != 0;
   ctx->prof_recorded = false;
   return SB_OK;
@@ -1315,7 +1322,7 @@ sb_status record_and_upload_blob(sb_context* ctx, const std::function<sb_status(
     if (ctx->blob.size() <= ctx->blob_cap) break;
     // grow the blob (its address is baked into captured graphs: drop them)
     SB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (ctx->graph.exec) { cudaGraphExecDestroy(ctx->graph.exec); ctx->graph.exec = nullptr; }
+    ctx->drop_graphs();
     if (ctx->blob_dev) cudaFree(ctx->blob_dev);
     if (ctx->blob_host) cudaFreeHost(ctx->blob_host);
     ctx->blob_dev = ctx->blob_host = nullptr;
@@ -1362,8 +1369,15 @@ sb_status run_graph(sb_context* ctx, const sb_pair* pairs, int n) {
   // record-only pass: the blob for the current pointers, uploaded ahead of the replay
   st = record_and_upload_blob(ctx, [&]() { return run_device(ctx, pairs, n, true); });
   if (st != SB_OK) return st;
-  if (!ctx->graph.exec || ctx->graph.key != key) {
-    if (ctx->graph.exec) { cudaGraphExecDestroy(ctx->graph.exec); ctx->graph.exec = nullptr; }
+  auto found = ctx->graphs.find(key);
+  if (found == ctx->graphs.end()) {
+    if (ctx->graphs.size() >= kGraphCacheMax) {   // evict the least recently used graph
+      auto old = ctx->graphs.begin();
+      for (auto it = ctx->graphs.begin(); it != ctx->graphs.end(); ++it)
+        if (it->second.used < old->second.used) old = it;
+      cudaGraphExecDestroy(old->second.exec);
+      ctx->graphs.erase(old);
+    }
     cudaStream_t cap = ctx->stream;
     bool own = false;
     if (cap == nullptr) {  // the legacy default stream cannot be captured
@@ -1379,7 +1393,7 @@ sb_status run_graph(sb_context* ctx, const sb_pair* pairs, int n) {
     ctx->capturing = true;
     if (e == cudaSuccess) st = run_device(ctx, pairs, n, true);
     ctx->capturing = false;
-    ctx->graph_kernels = ctx->launches - before;
+    const uint64_t kernels = ctx->launches - before;
     ctx->launches = before;
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(cap, &graph) : e;
@@ -1389,14 +1403,16 @@ sb_status run_graph(sb_context* ctx, const sb_pair* pairs, int n) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
     if (st != SB_OK) { if (graph) cudaGraphDestroy(graph); return st; }
     if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&ctx->graph.exec, graph, 0);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
-    ctx->graph.key = key;
+    found = ctx->graphs.emplace(key, sb_context::GraphEntry{exec, kernels, 0}).first;
   }
-  cudaError_t e = cudaGraphLaunch(ctx->graph.exec, ctx->stream);
+  found->second.used = ++ctx->graph_clock;
+  cudaError_t e = cudaGraphLaunch(found->second.exec, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
-  ctx->launches += ctx->graph_kernels;
+  ctx->launches += found->second.kernels;
   return SB_OK;
 }
 

@@ -35,7 +35,7 @@ from typing import Dict, List, Tuple
 
 import torch
 
-from . import Context, Pair, SB_RUN_BATCHED, sb_params, sb_run
+from . import Context, Pair, SB_RUN_BATCHED, SB_RUN_GRAPH, sb_params, sb_run
 
 
 def request_bytes(h: int, w: int) -> int:
@@ -170,7 +170,10 @@ class Server:
                 dd = torch.empty((r.h, r.w), dtype=torch.int16, device=self.device)
                 keep += [dl, dr, do, dd]
                 pairs.append(Pair(dl, dr, r.params, do, dd))
-            sb_run(self.ctxs[i], pairs, SB_RUN_BATCHED)
+            # a lone request replays its shape's CUDA graph (one launch instead of
+            # one per kernel: the host side of a pair is most of its latency);
+            # a batch of several runs batched, since its composition rarely recurs
+            sb_run(self.ctxs[i], pairs, SB_RUN_BATCHED | (SB_RUN_GRAPH if len(pairs) == 1 else 0))
             for r, q in zip(reqs, pairs):
                 r.out_rgb.copy_(q.out_rgb, non_blocking=True)
                 r.out_disp.copy_(q.out_disp, non_blocking=True)

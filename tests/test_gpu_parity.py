@@ -575,6 +575,30 @@ def test_batched_and_graph_equal_plain_on_uneven_batch(ctx):
         _compare_full(o_rgb, o_disp, left, right, p)
 
 
+def test_graph_cache_keeps_several_shapes():
+    # one context alternating three one-pair shapes in the graph form: each
+    # shape keeps its own instantiated graph (a replay, not a re-capture, on
+    # the second round) and every replay equals the plain form
+    items = []
+    for i, (w, h, D, B, K) in enumerate([(200, 120, 24, 7, 3), (321, 203, 48, 13, 5), (150, 150, 16, 5, 4)]):
+        r = synth.Rng(700 + i)
+        layers = synth._c2_style_layers(r, w, h, D, contrast=60)
+        sc = synth.Scene(w, h, layers, noise_q8=256, noise_seed=r.u64())
+        left, right, _ = sc.render()
+        items.append((left, right, synth.Params(k=K, max_disp=D, block=B, sigma=2.0, ranges=[(D // 3, D)])))
+    with sb.Context(0) as c:
+        plain = [run_pairs(c, [it], sb.SB_RUN_PLAIN)[0] for it in items]
+        counts = []
+        for rnd in range(3):
+            for it, want in zip(items, plain):
+                l0 = c.launch_count()
+                got = run_pairs(c, [it], sb.SB_RUN_BATCHED | sb.SB_RUN_GRAPH)[0]
+                counts.append(c.launch_count() - l0)
+                assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+        # every replay of a shape counts the same kernels as its first run
+        assert counts[:3] == counts[3:6] == counts[6:9] and min(counts) > 0
+
+
 def test_host_io_equals_device(ctx):
     sc, p, _ = synth.workload("c1")
     left, right, _ = sc.render()
