@@ -5,7 +5,8 @@ any time through ``Server.submit``.  A scheduler thread admits waiting
 requests in arrival order while their device-memory estimate fits the budget,
 batches everything admitted into one ``sb_run(SB_RUN_BATCHED)`` call on the
 first free stream (three by default, so new batches are copied in and
-launched while earlier ones compute),
+launched while earlier ones compute; a batch of one request replays its
+shape's CUDA graph, which the stream's context keeps),
 and resolves each request's future when its batch's completion event has
 fired.  Inputs, intermediate maps and results of admitted requests stay
 resident on the device until the batch completes; results are copied back to
