@@ -254,7 +254,13 @@ enum {
 };
 
 /* The whole pipeline of Section III for n_pairs pairs (pairs: HOST array).
- * Results are identical for every flag combination. */
+ * Results are identical for every flag combination.  With SB_RUN_GRAPH the
+ * first call of a batch shape (every pair's size and parameters) captures
+ * and instantiates a CUDA graph; later calls of that shape replay it after
+ * rebuilding its job descriptors for the current pointers.  A context keeps
+ * the graphs of its 64 most recently used shapes (a graph holds no device
+ * memory beyond its kernel nodes); enabling or disabling stage profiling,
+ * or a growth of the descriptor blob, drops them. */
 sb_status sb_run(sb_context* ctx, const sb_pair* pairs, int32_t n_pairs, uint32_t flags);
 
 /* Boundary SAD for callers that cannot allocate device memory: a plug-in
