@@ -39,27 +39,35 @@ __device__ __forceinline__ bool in_focus(uint16_t d, const int* lo, const int* h
 // exact u8 -> float: 2^23 + b as a float, minus 2^23
 __device__ __forceinline__ float u8f(uint8_t b) { return __int_as_float(0x4B000000 | b) - 8388608.0f; }
 
+// tap x value + accumulator, one channel (float) or two (float2: a packed
+// FP32 FMA, two channels per instruction)
+__device__ __forceinline__ float fma_t(float tp, float w, float a) { return fmaf(tp, w, a); }
+__device__ __forceinline__ float2 fma_t(float tp, float2 w, float2 a) { return __ffma2_rn(make_float2(tp, tp), w, a); }
+template <class T> __device__ __forceinline__ T zero_t();
+template <> __device__ __forceinline__ float zero_t<float>() { return 0.f; }
+template <> __device__ __forceinline__ float2 zero_t<float2>() { return make_float2(0.f, 0.f); }
+
 // One tap of the register-window convolution at rotation offset OFF + u:
 // win[(OFF + u + o) % OB] holds x[t + u + o]; afterwards the freed slot takes
 // x[t + u + OB].
-template <int OFF, int U, class LOAD>
-__device__ __forceinline__ void conv_tap(float (&acc)[OB], float (&win)[OB], float tp, int t, LOAD x) {
+template <int OFF, int U, int N, class T, class LOAD>
+__device__ __forceinline__ void conv_tap(T (&acc)[N], T (&win)[N], float tp, int t, LOAD x) {
 #pragma unroll
-  for (int o = 0; o < OB; ++o) acc[o] = fmaf(tp, win[(OFF + U + o) % OB], acc[o]);
-  win[(OFF + U) % OB] = x(t + U + OB);
+  for (int o = 0; o < N; ++o) acc[o] = fma_t(tp, win[(OFF + U + o) % N], acc[o]);
+  win[(OFF + U) % N] = x(t + U + N);
 }
 
 // at most 7 single taps t .. t+rem-1 at rotation offset OFF
-template <int OFF, class LOAD>
-__device__ __forceinline__ void conv_tail(float (&acc)[OB], float (&win)[OB], const float* tap, int t, int rem,
+template <int OFF, int N, class T, class LOAD>
+__device__ __forceinline__ void conv_tail(T (&acc)[N], T (&win)[N], const float* tap, int t, int rem,
                                           LOAD x) {
-  if (rem > 0) conv_tap<OFF, 0>(acc, win, tap[t], t, x);
-  if (rem > 1) conv_tap<OFF, 1>(acc, win, tap[t + 1], t, x);
-  if (rem > 2) conv_tap<OFF, 2>(acc, win, tap[t + 2], t, x);
-  if (rem > 3) conv_tap<OFF, 3>(acc, win, tap[t + 3], t, x);
-  if (rem > 4) conv_tap<OFF, 4>(acc, win, tap[t + 4], t, x);
-  if (rem > 5) conv_tap<OFF, 5>(acc, win, tap[t + 5], t, x);
-  if (rem > 6) conv_tap<OFF, 6>(acc, win, tap[t + 6], t, x);
+  if (rem > 0) conv_tap<OFF, 0, N>(acc, win, tap[t], t, x);
+  if (rem > 1) conv_tap<OFF, 1, N>(acc, win, tap[t + 1], t, x);
+  if (rem > 2) conv_tap<OFF, 2, N>(acc, win, tap[t + 2], t, x);
+  if (rem > 3) conv_tap<OFF, 3, N>(acc, win, tap[t + 3], t, x);
+  if (rem > 4) conv_tap<OFF, 4, N>(acc, win, tap[t + 4], t, x);
+  if (rem > 5) conv_tap<OFF, 5, N>(acc, win, tap[t + 5], t, x);
+  if (rem > 6) conv_tap<OFF, 6, N>(acc, win, tap[t + 6], t, x);
 }
 
 // acc[o] = sum_{t < nt} tap[t] * x[o + t] for o < OB, where x(j) loads input
@@ -90,9 +98,9 @@ __device__ __forceinline__ void conv16(float (&acc)[OB], const float* tap, int n
       for (int o = 0; o < OB; ++o) acc[o] = fmaf(tp, win[(u + o) % OB], acc[o]);
       win[u] = x(t + u + OB);
     }
-    conv_tail<8>(acc, win, tap, t + 8, rem - 8, x);
+    conv_tail<8, OB>(acc, win, tap, t + 8, rem - 8, x);
   } else {
-    conv_tail<0>(acc, win, tap, t, rem, x);
+    conv_tail<0, OB>(acc, win, tap, t, rem, x);
   }
 }
 
@@ -343,42 +351,44 @@ __host__ __device__ inline StripGeo strip_geo(int R) {
 // conv16 over ring rows b0 + j (mod M) of one column (hc: the column's row-0
 // entry, row stride HS); b0 and M are multiples of OB, so the wrap is taken
 // once per block of OB rows
-__device__ __forceinline__ void conv16_ring(float (&acc)[OB], const float* tap, int nt, const float* hc, int b0,
-                                            int M) {
-  auto block = [&](int j) {   // j: a multiple of OB
+// rd(k): the value (one channel, or two channels as a float2) at float
+// offset k of the channel plane(s) of the ring
+template <int N, class T, class RD>
+__device__ __forceinline__ void conv16_ring(T (&acc)[N], const float* tap, int nt, RD rd, int b0, int M) {
+  auto block = [&](int j) {   // j: a multiple of N
     int q = b0 + j;
     if (q >= M) q -= M;
-    return hc + q * HS;
+    return q * HS;
   };
-  float win[OB];
-  const float* p = block(0);
+  T win[N];
+  const int p = block(0);
 #pragma unroll
-  for (int o = 0; o < OB; ++o) { acc[o] = 0.f; win[o] = p[o * HS]; }
+  for (int o = 0; o < N; ++o) { acc[o] = zero_t<T>(); win[o] = rd(p + o * HS); }
   int t = 0;
-  for (; t + OB <= nt; t += OB) {
-    const float* pn = block(t + OB);
+  for (; t + N <= nt; t += N) {
+    const int pn = block(t + N);
 #pragma unroll
-    for (int u = 0; u < OB; ++u) {
+    for (int u = 0; u < N; ++u) {
       const float tp = tap[t + u];
 #pragma unroll
-      for (int o = 0; o < OB; ++o) acc[o] = fmaf(tp, win[(u + o) % OB], acc[o]);
-      win[u] = pn[u * HS];
+      for (int o = 0; o < N; ++o) acc[o] = fma_t(tp, win[(u + o) % N], acc[o]);
+      win[u] = rd(pn + u * HS);
     }
   }
   const int rem = nt - t;
-  const float* pn = block(t + OB);   // the refills of the remaining taps: rows t + OB .. t + OB + rem - 1
-  auto x = [pn, t](int j) { return pn[(j - t - OB) * HS]; };
-  if (rem >= 8) {
+  const int pn = block(t + N);   // the refills of the remaining taps: rows t + N .. t + N + rem - 1
+  auto x = [pn, t, rd](int j) { return rd(pn + (j - t - N) * HS); };
+  if (N == 16 && rem >= 8) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const float tp = tap[t + u];
 #pragma unroll
-      for (int o = 0; o < OB; ++o) acc[o] = fmaf(tp, win[(u + o) % OB], acc[o]);
-      win[u] = pn[u * HS];
+      for (int o = 0; o < N; ++o) acc[o] = fma_t(tp, win[(u + o) % N], acc[o]);
+      win[u] = rd(pn + u * HS);
     }
-    conv_tail<8>(acc, win, tap, t + 8, rem - 8, x);
+    conv_tail<8 % N, N>(acc, win, tap, t + 8, rem - 8, x);
   } else {
-    conv_tail<0>(acc, win, tap, t, rem, x);
+    conv_tail<0, N>(acc, win, tap, t, rem, x);
   }
 }
 
@@ -583,7 +593,49 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
     if (vout) asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // this step's original rows
     __syncthreads();   // the ring holds every row step st reads
     const int ys = yb0 + kSB * st, nrow = min(kSB, rows - kSB * st);
-    if (s_flag[st]) {
+    if (s_flag[st] && vout) {
+      // vertical pass, staged-output form: thread groups 0-3 take the R and G
+      // planes together (packed FP32 FMAs, float2) over blocks of 8 output
+      // rows, groups 4-5 the B plane over blocks of 16 (the same registers per
+      // thread), so every thread has a task
+      constexpr int kPair = OB / 2;   // output rows of an R+G task
+      const int col = tid % BX, rest = tid / BX;
+      if (rest < 4) {
+        const int i0 = rest * kPair;
+        const bool need = (s_vq[col >> 5] >> (2 * st + (i0 >= OB))) & 1u;
+        if (need) {
+          const float* hr = s_h + col;
+          const float* hg = s_h + (M * HS + kChPad) + col;
+          float2 acc[kPair];
+          conv16_ring(acc, s_tap, nt, [hr, hg](int k) { return make_float2(hr[k], hg[k]); }, slot(ys + i0 - R), M);
+#pragma unroll
+          for (int o = 0; o < kPair; ++o) {
+            const int i = i0 + o;
+            if (i < nrow && ((s_mbits[((kSB * st + i) * BX + col) >> 5] >> (col & 31)) & 1u)) {
+              const int q0 = __float2int_rd(acc[o].x + 0.5f), q1 = __float2int_rd(acc[o].y + 0.5f);
+              s_out[i * (BX * 3) + col * 3] = (uint8_t)min(max(q0, 0), 255);
+              s_out[i * (BX * 3) + col * 3 + 1] = (uint8_t)min(max(q1, 0), 255);
+            }
+          }
+        }
+      } else {
+        const int blk = rest - 4, i0 = blk * OB;
+        const bool need = (s_vq[col >> 5] >> (2 * st + blk)) & 1u;
+        if (need) {
+          const float* hb = s_h + 2 * (M * HS + kChPad) + col;
+          float acc[OB];
+          conv16_ring(acc, s_tap, nt, [hb](int k) { return hb[k]; }, slot(ys + i0 - R), M);
+#pragma unroll
+          for (int o = 0; o < OB; ++o) {
+            const int i = i0 + o;
+            if (i < nrow && ((s_mbits[((kSB * st + i) * BX + col) >> 5] >> (col & 31)) & 1u)) {
+              const int q = __float2int_rd(acc[o] + 0.5f);
+              s_out[i * (BX * 3) + col * 3 + 2] = (uint8_t)min(max(q, 0), 255);
+            }
+          }
+        }
+      }
+    } else if (s_flag[st]) {
       // vertical pass: task = (column, channel, block of OB output rows)
       const int col = tid % BX, rest = tid / BX, ch = rest % 3, blk = rest / 3;
       const int i0 = blk * OB;
@@ -593,7 +645,8 @@ __global__ void __launch_bounds__(kStripThreads, 2) k_blur_strip(const BlurJob* 
       // blurred has nothing to write and skips its convolution
       const bool need = (s_vq[col >> 5] >> (2 * st + blk)) & 1u;
       float acc[OB];
-      if (need) conv16_ring(acc, s_tap, nt, s_h + ch * (M * HS + kChPad) + col, b0, M);
+      const float* hc = s_h + ch * (M * HS + kChPad) + col;
+      if (need) conv16_ring(acc, s_tap, nt, [hc](int k) { return hc[k]; }, b0, M);
       if (vout && need) {
 #pragma unroll
         for (int o = 0; o < OB; ++o) {
