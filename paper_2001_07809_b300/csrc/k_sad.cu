@@ -469,20 +469,24 @@ __global__ void __launch_bounds__(256, 6) k_sad_tail(const SadJob* __restrict__ 
         G = min(kTailRows, it.y1 - yg + 1);
         nrows = 2 * G;
       }
-      for (int i = warp; i < nrows; i += 8) {
-        const int q = gi < nwarm ? i : (i < G ? i : kTailRows + i - G);
-        const int row = gi < nwarm ? row0 + i : (i < G ? yg + i + r : yg + (i - G) - r);
-        const int64_t rb = (int64_t)row * w;
-        if (lane == 0) s_ph[buf][q] = (uint16_t)(phase(row, cstart) | (phase(row, cr0) << 8));
-        for (int ch = lane; ch < nchL; ch += 32)
-          stage_chunk(B + q * kTailL, J.Ll, npx, (rb + cstart) & ~(int64_t)15, ch, fast);
-        for (int ch = lane; ch < nchR; ch += 32)
-          stage_chunk(B + kTailSlots * kTailL + q * kTailR, J.Lr, npx, (rb + cr0) & ~(int64_t)15, ch, fast);
-      }
-      for (int j = warp; j < G; j += 8)
-        for (int ch = lane; ch < nchB; ch += 32)
+      // one flat index over (row, chunk) so that every thread copies a chunk:
+      // the image rows' L and R chunks first, then the anchor-map rows'
+      const int per = nchL + nchR, nimg = nrows * per;
+      for (int idx = tid; idx < nimg + G * nchB; idx += 256) {
+        if (idx < nimg) {
+          const int i = idx / per, ch = idx - i * per;
+          const int q = gi < nwarm ? i : (i < G ? i : kTailRows + i - G);
+          const int row = gi < nwarm ? row0 + i : (i < G ? yg + i + r : yg + (i - G) - r);
+          const int64_t rb = (int64_t)row * w;
+          if (ch == 0) s_ph[buf][q] = (uint16_t)(phase(row, cstart) | (phase(row, cr0) << 8));
+          if (ch < nchL) stage_chunk(B + q * kTailL, J.Ll, npx, (rb + cstart) & ~(int64_t)15, ch, fast);
+          else stage_chunk(B + kTailSlots * kTailL + q * kTailR, J.Lr, npx, (rb + cr0) & ~(int64_t)15, ch - nchL, fast);
+        } else {
+          const int j = (idx - nimg) / nchB, ch = idx - nimg - j * nchB;
           stage_chunk(B + kTailSlots * (kTailL + kTailR) + j * kTailB, J.bmap, npx,
                       ((int64_t)(yg + j) * w + x0) & ~(int64_t)15, ch, fast);
+        }
+      }
       cp_async_commit();
     };
     uint32_t V[REM];
