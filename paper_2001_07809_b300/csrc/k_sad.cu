@@ -84,9 +84,9 @@ namespace {
 // Anchor emission for four consecutive outputs K0 .. K0+3 of a block whose
 // anchor bits are the compile-time nibble NIB.  Lane p holds the packed
 // running sums of its disparity pair (dlo, dhi) after output K: T = Slo +
-// 65536 Shi + n * 0x40004000 (mod 2^32) and H = Shi + n * 0x4000, n = K + 1
-// steps after the warm-up (n0 + K + 1), so Shi = H - n * 0x4000 and
-// Slo = T - (Shi << 16) - n * 0x40004000.  The lane's two keys
+// 65536 Shi (mod 2^32) and H = Shi + n * 0x4000, n = K + 1 steps after the
+// warm-up (n0 + K + 1), so Shi = H - n * 0x4000 and Slo = T - (Shi << 16).
+// The lane's two keys
 // (S << 10 | d) are reduced in the lane, then over the warp (redux.sync) for
 // every anchor of the nibble first, so that the reductions' latencies
 // overlap; the warp minimum of output o of the 32-output span goes to lane o
@@ -102,7 +102,7 @@ __device__ __forceinline__ void emit_nibble(const uint32_t (&Tv)[8], const uint3
     if (NIB & (1u << b)) {
       const uint32_t n = n0 + K0 + b + 1;
       const uint32_t shi = Hv[K0 + b] - n * 0x4000u;
-      const uint32_t slo = Tv[K0 + b] - (shi << 16) - n * 0x40004000u;
+      const uint32_t slo = Tv[K0 + b] - (shi << 16);
       const uint32_t k = min((slo << SB_KEY_DBITS) | dlo, (shi << SB_KEY_DBITS) | dhi);
       m[b] = __reduce_min_sync(0xffffffffu, k);
     }
@@ -316,11 +316,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
       // Stage B: warp -> (row g of the group, segment of TX / kSegs outputs);
       // lane -> disparity pair.  The column sums of a pair are one 32-bit word
       // (lo | hi << 16, each below 2^14), so one load serves two disparities.
-      // The horizontal window slides by delta = entering - leaving + 0x40004000:
-      // each u16 lane of delta is the lane's difference plus 0x4000, in
-      // [0x4000 - 16065, 0x4000 + 16065], so no borrow crosses lanes; T adds
-      // delta (mod 2^32) and H adds its upper lane, from which the emission
-      // recovers both window sums exactly.
+      // The horizontal window slides by entering - leaving: T adds it (mod 2^32;
+      // the packed pair of window sums, whose lanes are exact once the true sums
+      // are known to fit), and H adds the upper lane of delta = entering -
+      // leaving + 0x40004000, each of whose u16 lanes is the lane's difference
+      // plus 0x4000, in [0x4000 - 16065, 0x4000 + 16065], so no borrow crosses
+      // lanes; from T and H the emission recovers both window sums exactly.
       {
         const int g = warp / kSegs, seg = warp % kSegs;
         const int y = yg + g;
@@ -375,9 +376,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
               uint32_t Tv[8], Hv[8];
 #pragma unroll
               for (int k = 0; k < 8; ++k) {
-                const uint32_t delta = pin[(i + k) * CW] - pout[(i + k) * CW] + 0x40004000u;
-                T += delta;
-                H += delta >> 16;
+                const uint32_t e = pin[(i + k) * CW], l = pout[(i + k) * CW];
+                T += e - l;
+                H += (e - l + 0x40004000u) >> 16;
                 Tv[k] = T;
                 Hv[k] = H;
               }
