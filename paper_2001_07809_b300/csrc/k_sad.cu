@@ -89,13 +89,14 @@ namespace {
 // The lane's two keys
 // (S << 10 | d) are reduced in the lane, then over the warp (redux.sync) for
 // every anchor of the nibble first, so that the reductions' latencies
-// overlap; the warp minimum of output o of the 32-output span goes to lane o
-// (`best`, lrel = lane - the block's first output in the span), which keeps
-// it with one atomicMin for the whole span.  Disparities past D carry
+// overlap; the warp minimum of output o of the 32-output span goes to word o
+// of the warp's slot row `sbest` (one uniform store: every lane writes the
+// same value to the same word), from which lane o takes it for one atomicMin
+// per anchor at the end of the span.  Disparities past D carry
 // all-ones low bits, which makes their key all ones (never the minimum).
 template <unsigned NIB, int K0>
 __device__ __forceinline__ void emit_nibble(const uint32_t (&Tv)[8], const uint32_t (&Hv)[8], uint32_t n0,
-                                            uint32_t dlo, uint32_t dhi, uint32_t& best, int lrel) {
+                                            uint32_t dlo, uint32_t dhi, uint32_t* sbest) {
   uint32_t m[4];
 #pragma unroll
   for (int b = 0; b < 4; ++b)
@@ -108,17 +109,17 @@ __device__ __forceinline__ void emit_nibble(const uint32_t (&Tv)[8], const uint3
     }
 #pragma unroll
   for (int b = 0; b < 4; ++b)
-    if (NIB & (1u << b)) best = lrel == K0 + b ? m[b] : best;
+    if (NIB & (1u << b)) sbest[K0 + b] = m[b];
 }
 
 // one case per non-empty nibble value: the bits are warp-uniform, so the
 // switch is a uniform jump and every case's code is straight-line
 template <int K0>
 __device__ __forceinline__ void emit_block_half(unsigned nib, const uint32_t (&Tv)[8], const uint32_t (&Hv)[8],
-                                                uint32_t n0, uint32_t dlo, uint32_t dhi, uint32_t& best, int lrel) {
+                                                uint32_t n0, uint32_t dlo, uint32_t dhi, uint32_t* sbest) {
   switch (nib) {
 #define SB_EMIT_CASE(v) \
-  case v: emit_nibble<v, K0>(Tv, Hv, n0, dlo, dhi, best, lrel); break;
+  case v: emit_nibble<v, K0>(Tv, Hv, n0, dlo, dhi, sbest); break;
     SB_EMIT_CASE(1) SB_EMIT_CASE(2) SB_EMIT_CASE(3) SB_EMIT_CASE(4) SB_EMIT_CASE(5)
     SB_EMIT_CASE(6) SB_EMIT_CASE(7) SB_EMIT_CASE(8) SB_EMIT_CASE(9) SB_EMIT_CASE(10)
     SB_EMIT_CASE(11) SB_EMIT_CASE(12) SB_EMIT_CASE(13) SB_EMIT_CASE(14) SB_EMIT_CASE(15)
@@ -164,6 +165,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
                                                             unsigned* __restrict__ queue) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int s_item;
+  __shared__ uint32_t s_best[kThreads];   // per warp: the span's 32 anchor keys
   for (;;) {
     __syncthreads();  // every thread is done with the previous item (and has read s_item)
     if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);
@@ -370,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
             const int n = min(32, xb - xbase);
             const uint32_t* pin = vcol + (xbase + 2 * r + 1) * CW;  // slot column of strip column x + 2r
             const uint32_t* pout = vcol + xbase * CW;             // slot column of x - 1
-            uint32_t best = 0xFFFFFFFFu;                          // lane o: the key of output xbase + o
+            uint32_t* sbest = s_best + warp * 32;                 // word o: the key of output xbase + o
 #pragma unroll 1
             for (int i = 0; i < n; i += 8) {
               uint32_t Tv[8], Hv[8];
@@ -383,11 +385,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
                 Hv[k] = H;
               }
               const unsigned bits = (mask >> i) & 0xFFu;
-              emit_block_half<0>(bits & 15u, Tv, Hv, n0, dlo, dhi, best, lane - i);
-              emit_block_half<4>(bits >> 4, Tv, Hv, n0, dlo, dhi, best, lane - i);
+              emit_block_half<0>(bits & 15u, Tv, Hv, n0, dlo, dhi, sbest + i);
+              emit_block_half<4>(bits >> 4, Tv, Hv, n0, dlo, dhi, sbest + i);
               n0 += 8;
             }
-            if ((mask >> lane) & 1u) atomicMin(krow + xbase + lane, best);   // one per anchor of the span
+            __syncwarp();   // the span's uniform stores are visible to every lane
+            if ((mask >> lane) & 1u) atomicMin(krow + xbase + lane, sbest[lane]);   // one per anchor of the span
+            __syncwarp();   // read before the next span overwrites
             bcur = bnext;
           }
         }
