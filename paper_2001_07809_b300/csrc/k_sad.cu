@@ -84,10 +84,8 @@ namespace {
 // Anchor emission for four consecutive outputs K0 .. K0+3 of a block whose
 // anchor bits are the compile-time nibble NIB.  Lane p holds the packed
 // running sums of its disparity pair (dlo, dhi) after output K: T = Slo +
-// 65536 Shi (mod 2^32) and H = Shi + n * 0x4000, n = K + 1 steps after the
-// warm-up (n0 + K + 1), so Shi = H - n * 0x4000 and Slo = T - (Shi << 16).
-// The lane's two keys
-// (S << 10 | d) are reduced in the lane, then over the warp (redux.sync) for
+// 65536 Shi (mod 2^32) and H = Shi, so Slo = T - (Shi << 16).  The lane's
+// two keys (S << 10 | d) are reduced in the lane, then over the warp (redux.sync) for
 // every anchor of the nibble first, so that the reductions' latencies
 // overlap; the warp minimum of output o of the 32-output span goes to word o
 // of the warp's slot row `sbest` (one uniform store: every lane writes the
@@ -95,14 +93,13 @@ namespace {
 // per anchor at the end of the span.  Disparities past D carry
 // all-ones low bits, which makes their key all ones (never the minimum).
 template <unsigned NIB, int K0>
-__device__ __forceinline__ void emit_nibble(const uint32_t (&Tv)[8], const uint32_t (&Hv)[8], uint32_t n0,
-                                            uint32_t dlo, uint32_t dhi, uint32_t* sbest) {
+__device__ __forceinline__ void emit_nibble(const uint32_t (&Tv)[8], const uint32_t (&Hv)[8], uint32_t dlo,
+                                            uint32_t dhi, uint32_t* sbest) {
   uint32_t m[4];
 #pragma unroll
   for (int b = 0; b < 4; ++b)
     if (NIB & (1u << b)) {
-      const uint32_t n = n0 + K0 + b + 1;
-      const uint32_t shi = Hv[K0 + b] - n * 0x4000u;
+      const uint32_t shi = Hv[K0 + b];
       const uint32_t slo = Tv[K0 + b] - (shi << 16);
       const uint32_t k = min((slo << SB_KEY_DBITS) | dlo, (shi << SB_KEY_DBITS) | dhi);
       m[b] = __reduce_min_sync(0xffffffffu, k);
@@ -116,10 +113,10 @@ __device__ __forceinline__ void emit_nibble(const uint32_t (&Tv)[8], const uint3
 // switch is a uniform jump and every case's code is straight-line
 template <int K0>
 __device__ __forceinline__ void emit_block_half(unsigned nib, const uint32_t (&Tv)[8], const uint32_t (&Hv)[8],
-                                                uint32_t n0, uint32_t dlo, uint32_t dhi, uint32_t* sbest) {
+                                                uint32_t dlo, uint32_t dhi, uint32_t* sbest) {
   switch (nib) {
 #define SB_EMIT_CASE(v) \
-  case v: emit_nibble<v, K0>(Tv, Hv, n0, dlo, dhi, sbest); break;
+  case v: emit_nibble<v, K0>(Tv, Hv, dlo, dhi, sbest); break;
     SB_EMIT_CASE(1) SB_EMIT_CASE(2) SB_EMIT_CASE(3) SB_EMIT_CASE(4) SB_EMIT_CASE(5)
     SB_EMIT_CASE(6) SB_EMIT_CASE(7) SB_EMIT_CASE(8) SB_EMIT_CASE(9) SB_EMIT_CASE(10)
     SB_EMIT_CASE(11) SB_EMIT_CASE(12) SB_EMIT_CASE(13) SB_EMIT_CASE(14) SB_EMIT_CASE(15)
@@ -321,9 +318,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
       // The horizontal window slides by entering - leaving: T adds it (mod 2^32;
       // the packed pair of window sums, whose lanes are exact once the true sums
       // are known to fit), and H adds the upper lane of delta = entering -
-      // leaving + 0x40004000, each of whose u16 lanes is the lane's difference
-      // plus 0x4000, in [0x4000 - 16065, 0x4000 + 16065], so no borrow crosses
-      // lanes; from T and H the emission recovers both window sums exactly.
+      // leaving + 0x4000 taken as a signed number (arithmetic shift): the lower
+      // u16 lane of delta is the lower difference plus 0x4000, in
+      // [0x4000 - 16065, 0x4000 + 16065], so it never borrows from the upper
+      // lane, which is then exactly the upper difference; H is the upper window
+      // sum itself, and T and H give both window sums exactly.
       {
         const int g = warp / kSegs, seg = warp % kSegs;
         const int y = yg + g;
@@ -363,7 +362,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
             T += T1 + T2 + T3;
             H += H1 + H2 + H3;
           }
-          uint32_t n0 = 0;                                        // outputs done before the block
           // the map bytes of the next 32 outputs are read one chunk ahead
           uint8_t bcur = xa + lane < xb ? bm[xa + lane] : (uint8_t)0;
           for (int xbase = xa; xbase < xb; xbase += 32) {
@@ -380,14 +378,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_sad_boxsum(const SadJob* __rest
               for (int k = 0; k < 8; ++k) {
                 const uint32_t e = pin[(i + k) * CW], l = pout[(i + k) * CW];
                 T += e - l;
-                H += (e - l + 0x40004000u) >> 16;
+                H += (uint32_t)((int32_t)(e - l + 0x4000u) >> 16);
                 Tv[k] = T;
                 Hv[k] = H;
               }
               const unsigned bits = (mask >> i) & 0xFFu;
-              emit_block_half<0>(bits & 15u, Tv, Hv, n0, dlo, dhi, sbest + i);
-              emit_block_half<4>(bits >> 4, Tv, Hv, n0, dlo, dhi, sbest + i);
-              n0 += 8;
+              emit_block_half<0>(bits & 15u, Tv, Hv, dlo, dhi, sbest + i);
+              emit_block_half<4>(bits >> 4, Tv, Hv, dlo, dhi, sbest + i);
             }
             __syncwarp();   // the span's uniform stores are visible to every lane
             if ((mask >> lane) & 1u) atomicMin(krow + xbase + lane, sbest[lane]);   // one per anchor of the span
