@@ -60,7 +60,7 @@ BOX_DISPARITIES_C3 = 256
 # capture of one 8-pair launch read 506.99 MB and wrote 197.64 MB (L maps and boundary map
 # in, argmin keys out); a launch over P pairs moves P times that, since each pair's data is
 # its own
-SAD_DRAM_BYTES_PER_PAIR = (506.99e6 + 197.64e6) / 8
+SAD_DRAM_BYTES_PER_PAIR = (498.09e6 + 194.33e6) / 8
 METRIC = "stereo pairs/s at 4096x2304 (batched vs per-pair), SAD Gcell/s, p99 latency"
 # --sad-variant: the library's per-pair choice (box sums at this workload's density), or either
 # SAD kernel forced (the roofline then describes that kernel)
