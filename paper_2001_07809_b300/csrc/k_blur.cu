@@ -47,13 +47,6 @@ template <class T> __device__ __forceinline__ T zero_t();
 template <> __device__ __forceinline__ float zero_t<float>() { return 0.f; }
 template <> __device__ __forceinline__ float2 zero_t<float2>() { return make_float2(0.f, 0.f); }
 
-// tap u of a block of taps that starts 16-byte aligned: one 16-byte load per
-// four taps (q holds taps u & ~3 .. (u & ~3) + 3 once u % 4 == 0 has loaded it)
-__device__ __forceinline__ float tap4(float4& q, const float* tap, int u) {
-  if ((u & 3) == 0) q = *reinterpret_cast<const float4*>(tap + u);
-  return (u & 3) == 0 ? q.x : (u & 3) == 1 ? q.y : (u & 3) == 2 ? q.z : q.w;
-}
-
 // One tap of the register-window convolution at rotation offset OFF + u:
 // win[(OFF + u + o) % OB] holds x[t + u + o]; afterwards the freed slot takes
 // x[t + u + OB].
@@ -87,11 +80,10 @@ __device__ __forceinline__ void conv16(float (&acc)[OB], const float* tap, int n
 #pragma unroll
   for (int o = 0; o < OB; ++o) { acc[o] = 0.f; win[o] = x(o); }
   int t = 0;
-  float4 q;
   for (; t + OB <= nt; t += OB) {
 #pragma unroll
     for (int u = 0; u < OB; ++u) {
-      const float tp = tap4(q, tap + t, u);
+      const float tp = tap[t + u];
 #pragma unroll
       for (int o = 0; o < OB; ++o) acc[o] = fmaf(tp, win[(u + o) % OB], acc[o]);
       win[u] = x(t + u + OB);
@@ -101,7 +93,7 @@ __device__ __forceinline__ void conv16(float (&acc)[OB], const float* tap, int n
   if (rem >= 8) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const float tp = tap4(q, tap + t, u);
+      const float tp = tap[t + u];
 #pragma unroll
       for (int o = 0; o < OB; ++o) acc[o] = fmaf(tp, win[(u + o) % OB], acc[o]);
       win[u] = x(t + u + OB);
@@ -373,12 +365,11 @@ __device__ __forceinline__ void conv16_ring(T (&acc)[N], const float* tap, int n
 #pragma unroll
   for (int o = 0; o < N; ++o) { acc[o] = zero_t<T>(); win[o] = rd(p + o * HS); }
   int t = 0;
-  float4 q;
   for (; t + N <= nt; t += N) {
     const int pn = block(t + N);
 #pragma unroll
     for (int u = 0; u < N; ++u) {
-      const float tp = tap4(q, tap + t, u);
+      const float tp = tap[t + u];
 #pragma unroll
       for (int o = 0; o < N; ++o) acc[o] = fma_t(tp, win[(u + o) % N], acc[o]);
       win[u] = rd(pn + u * HS);
@@ -390,7 +381,7 @@ __device__ __forceinline__ void conv16_ring(T (&acc)[N], const float* tap, int n
   if (N == 16 && rem >= 8) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const float tp = tap4(q, tap + t, u);
+      const float tp = tap[t + u];
 #pragma unroll
       for (int o = 0; o < N; ++o) acc[o] = fma_t(tp, win[(u + o) % N], acc[o]);
       win[u] = rd(pn + u * HS);
