@@ -97,17 +97,16 @@ __device__ __forceinline__ uint32_t comp_size(const CcaJob& J, int64_t r) {
 }
 }  // namespace
 
-// Tile-local labelling, one warp per 32x32 tile, rows in order (the classic
-// raster two-pass scheme with a warp holding one row): lane x of the warp is
-// tile column x.  Lane y first holds the mask of tile row y; each horizontal
-// run of a row is one union-find node, named by its first pixel (tile-local
-// index y * 32 + start), which is the smallest index of the run.  A run of row
-// y touches the runs of row y - 1 that cross its columns widened by one on
-// each side (8-connectivity); the lane at its start hangs the new node under
-// the root of the first of them and unites that tree with the trees of the
-// others (rare: where two branches meet).  Every link goes from a larger index
-// to a smaller one, so a piece's root is its smallest index.  A last sweep,
-// again rows in order, finds every pixel's root, writes it as the pixel's
+// Tile-local labelling, one warp per 32x32 tile.  Lane y holds the mask of
+// tile row y; each horizontal run of a row is one union-find node, named by its
+// first pixel (tile-local index y * 32 + start), which is the smallest index of
+// the run.  A run of row y touches the runs of row y - 1 that cross its
+// columns widened by one on each side (8-connectivity); every lane unites each
+// run of its row with each run above it touches, all rows at once, with the
+// lock-free union of the image-level merge (shared-memory atomics).  Every
+// link goes from a larger index to a smaller one, so a piece's root is its
+// smallest index.  A last sweep, lane x of the warp on tile column x,
+// rows in order, finds every pixel's root, writes it as the pixel's
 // label and points each run's node straight at it (so the searches of later
 // rows take one or two links), and gives every local root its node in the
 // image-level table (parent itself, size 0).
@@ -151,37 +150,32 @@ __global__ void __launch_bounds__(kCcaWarps * 32) k_cca_local(const CcaJob* __re
     }
   }
   bool ok = true;
-  unsigned prev = 0;
-  for (int y = 0; y < CT; ++y) {
-    const unsigned cur = __shfl_sync(0xffffffffu, rowmask, y);
-    if (cur) {
-      // the lane at the start of each run links the run (a fresh node) to the
-      // root of the first run above it touches, and unites that tree with the
-      // tree of every further run above it touches
-      const unsigned starts = cur & ~(cur << 1);
-      if ((starts >> lane) & 1u) {
-        const int C = y * CT + lane;
-        const unsigned inv = ~(cur >> lane);
-        const int len = inv ? __ffs(inv) - 1 : CT - lane;
-        const unsigned run = (len == 32 ? 0xffffffffu : ((1u << len) - 1u)) << lane;
-        const unsigned T = prev & (run | (run << 1) | (run >> 1));   // columns above it touches
-        if (!T) {
-          P[C] = C;
-        } else {
-          const int s1 = run_start(prev, __ffs(T) - 1);
-          const int r1 = find_root<1>(P, (y - 1) * CT + s1, J.union_limit, ok);
-          P[C] = r1;   // r1 < C: the smaller index stays the root
-          unsigned others = T & (prev & ~(prev << 1)) & ~(1u << s1);   // starts of the other runs above
-          while (others) {
-            const int b = __ffs(others) - 1;
-            others &= others - 1u;
-            ok &= unite<1>(P, r1, (y - 1) * CT + b, J.union_limit, ok);
-          }
-        }
-      }
-      __syncwarp();
+  {
+    // every row at once: lane y makes a node of each run of its row, then links
+    // each run to every run of row y - 1 it touches
+    const unsigned cur = rowmask;
+    const unsigned above = __shfl_up_sync(0xffffffffu, rowmask, 1);
+    const unsigned prev = lane > 0 ? above : 0u;
+    const unsigned starts = cur & ~(cur << 1), pstarts = prev & ~(prev << 1);
+    for (unsigned m = starts; m; m &= m - 1u) {
+      const int c = __ffs(m) - 1;
+      P[lane * CT + c] = lane * CT + c;
     }
-    prev = cur;
+    __syncwarp();
+    for (unsigned m = starts; m; m &= m - 1u) {
+      const int c = __ffs(m) - 1;
+      const unsigned inv = ~(cur >> c);
+      const int len = inv ? __ffs(inv) - 1 : CT - c;
+      const unsigned run = (len == 32 ? 0xffffffffu : ((1u << len) - 1u)) << c;
+      const unsigned T = prev & (run | (run << 1) | (run >> 1));   // columns above it touches
+      if (!T) continue;
+      const int C = lane * CT + c;
+      const int s1 = run_start(prev, __ffs(T) - 1);   // the first run above, which may start left of T
+      ok &= unite<1>(P, C, (lane - 1) * CT + s1, J.union_limit, ok);
+      for (unsigned o = T & pstarts & ~(1u << s1); o; o &= o - 1u)   // the other runs above
+        ok &= unite<1>(P, C, (lane - 1) * CT + __ffs(o) - 1, J.union_limit, ok);
+    }
+    __syncwarp();
   }
   // labels, rows in order (a node another lane is re-pointing still leads to
   // the same root, whichever value a search reads)
