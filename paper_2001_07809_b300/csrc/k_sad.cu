@@ -18,12 +18,13 @@
 //   Stage B: lanes = disparity pairs (one 32-bit word of a column slot holds
 //     a lane's two u16 column sums); a warp slides the horizontal sums along
 //     its row segment in blocks of 8 outputs with two running words (the
-//     packed pair and its upper half, recovered exactly at anchors; a zero
-//     column before each row of column sums lets every output use the same
-//     add-entering / drop-leaving update).  At anchor pixels (warp-uniform
-//     bits, one uniform jump per four outputs) it reduces (S << 10 | d) over
-//     the warp with redux.sync; lane o keeps the minimum of output o of the
-//     32-output span, and one atomicMin per span keeps it in the per-pixel key.
+//     packed pair and the upper window sum, from which the lower one is
+//     recovered exactly at anchors; a zero column before each row of column
+//     sums lets every output use the same add-entering / drop-leaving
+//     update).  At anchor pixels (warp-uniform bits, one uniform jump per four
+//     outputs) it reduces (S << 10 | d) over the warp with redux.sync; the
+//     minimum of output o of the 32-output span goes to word o of a per-warp
+//     shared row, and lane o keeps it in the per-pixel key with one atomicMin.
 // Tail kernel: the 1..8 disparities past the last whole chunk of 64 (one
 // disparity at D = 2^n), a thread per column with the vertical sums and a
 // warp prefix sum per row for the horizontal ones, so the box-sum work list
