@@ -121,6 +121,33 @@ def test_cca_dense_noisy_maps(ctx, noise):
     assert np.array_equal(bnd, oracle.cc_filter(o_ref, o_lab, 0.04))
 
 
+def _merge_pattern(kind, h, w):
+    # label maps whose boundary maps hold about 40 runs per row that meet the
+    # runs of the rows around them at once: stripes three pixels wide crossed
+    # by bars of a third label, concentric rings, and combs (teeth joined by
+    # a bar)
+    y, x = np.mgrid[0:h, 0:w]
+    if kind == "stripes":
+        lab = np.where((y % 37) > 33, 2, (x // 3) % 2)
+    elif kind == "rings":
+        lab = (np.hypot(x - w // 2, y - h // 2) // 4).astype(np.int64) % 3
+    else:
+        lab = ((x % 4) < 2) | ((y % 37) > 33)
+    return lab.astype(np.uint8)
+
+
+@pytest.mark.parametrize("kind", ["stripes", "rings", "comb"])
+def test_cca_merging_patterns(ctx, kind):
+    # ragged size over several tiles in both directions
+    labels = _merge_pattern(kind, 97, 133)
+    o_ref = oracle.refine(oracle.boundary(labels), 0)
+    ref, lab, bnd = refine(ctx, labels, 0, 0.04)
+    o_lab, _ = oracle.cca(o_ref)
+    assert np.array_equal(ref, o_ref)
+    assert np.array_equal(lab, o_lab)
+    assert np.array_equal(bnd, oracle.cc_filter(o_ref, o_lab, 0.04))
+
+
 def test_refine_degenerate(ctx):
     # K = 1: no boundary at all; one label row; a single pixel image
     for labels in (np.zeros((40, 50), np.uint8), np.array([[0, 1, 1, 0, 2]], np.uint8), np.zeros((1, 1), np.uint8)):
