@@ -30,10 +30,32 @@ constexpr int kSegRows = 64;  // Algorithm 2 column segment height
 inline size_t al(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
 // ------------------------------------------------------------ job uploads
-// A pinned host ring and a device ring of the same size.  Device reuse is
-// ordered by the stream; host reuse waits for the copy that read it.
+// Small host-to-device transfers (job descriptors, the graph form's blob, the
+// error word) are moved by the SMs through the device mapping of pinned host
+// memory, not by cudaMemcpyAsync: a copy engine runs its queued copies in
+// order, so a few hundred bytes of descriptors would otherwise wait behind
+// the bulk image copies other streams (host-buffer streaming, the served
+// requests) have queued on the same engine.
+__global__ void k_gather16(const uint4* __restrict__ src, uint4* __restrict__ dst, size_t n16) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+// bytes (rounded up to 16) from src_mapped, the device address of pinned host
+// memory, to dst; both 16-byte aligned
+cudaError_t gather_h2d(void* dst, const void* src_mapped, size_t bytes, cudaStream_t s) {
+  const size_t n16 = (bytes + 15) / 16;
+  if (!n16) return cudaSuccess;
+  const unsigned blocks = (unsigned)std::min<size_t>((n16 + 255) / 256, 64);
+  k_gather16<<<blocks, 256, 0, s>>>(reinterpret_cast<const uint4*>(src_mapped), reinterpret_cast<uint4*>(dst), n16);
+  return cudaGetLastError();
+}
+__global__ void k_read_word(const uint32_t* __restrict__ src, volatile uint32_t* dst) { *dst = *src; }
+
+// A pinned (mapped) host ring and a device ring of the same size.  Device
+// reuse is ordered by the stream; host reuse waits for the copy that read it.
 struct Uploader {
   uint8_t* host = nullptr;
+  uint8_t* host_dev = nullptr;   // the device address of the host ring
   uint8_t* dev = nullptr;
   size_t cap = 0, head = 0;
   struct Flight { size_t a, b; cudaEvent_t ev; };
@@ -42,7 +64,9 @@ struct Uploader {
 
   cudaError_t init(size_t bytes) {
     cap = bytes;
-    cudaError_t e = cudaMallocHost(&host, cap);
+    cudaError_t e = cudaHostAlloc(&host, cap, cudaHostAllocMapped);
+    if (e != cudaSuccess) return e;
+    e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&host_dev), host, 0);
     if (e != cudaSuccess) return e;
     return cudaMalloc(&dev, cap);
   }
@@ -72,7 +96,7 @@ struct Uploader {
       }
     }
     if (bytes) memcpy(host + a, src, bytes);
-    *err = cudaMemcpyAsync(dev + a, host + a, n, cudaMemcpyHostToDevice, s);
+    *err = gather_h2d(dev + a, host_dev + a, n, s);
     cudaEvent_t ev;
     if (!pool.empty()) { ev = pool.back(); pool.pop_back(); }
     else cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -206,7 +230,10 @@ struct sb_context {
   std::vector<uint8_t> blob;
   uint8_t* blob_dev = nullptr;
   size_t blob_cap = 0;
-  uint8_t* blob_host = nullptr;  // pinned staging of the blob
+  uint8_t* blob_host = nullptr;  // pinned (mapped) staging of the blob
+  uint8_t* blob_host_dev = nullptr;   // its device address
+  uint32_t* err_host = nullptr;       // pinned (mapped) copy of the error word
+  uint32_t* err_host_dev = nullptr;
   cudaEvent_t blob_ev = nullptr;
   // stage profiling
   bool prof_on = false;
@@ -401,6 +428,7 @@ const T* upload(sb_context* ctx, const std::vector<T>& v, sb_status* st) {
   cudaError_t e = cudaSuccess;
   void* d = ctx->up.put(v.data(), v.size() * sizeof(T), ctx->stream, &e);
   if (e != cudaSuccess || !d) { *st = cuda_fail(ctx, e == cudaSuccess ? cudaErrorMemoryAllocation : e, "job upload"); return nullptr; }
+  ++ctx->launches;   // the gather kernel
   *st = SB_OK;
   return (const T*)d;
 }
@@ -911,6 +939,9 @@ sb_status sb_create(int device, size_t mem_budget_bytes, void* cuda_stream, sb_c
   if (cudaSetDevice(device) != cudaSuccess) return SB_ERR_CUDA;
   if (build_tables(ctx.get()) != SB_OK) return SB_ERR_CUDA;
   if (cudaMalloc(&ctx->dev_err, 4) != cudaSuccess || cudaMemset(ctx->dev_err, 0, 4) != cudaSuccess) return SB_ERR_CUDA;
+  if (cudaHostAlloc(&ctx->err_host, 16, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer(reinterpret_cast<void**>(&ctx->err_host_dev), ctx->err_host, 0) != cudaSuccess)
+    return SB_ERR_CUDA;
   if (cudaMalloc(&ctx->sad_queue, 8) != cudaSuccess) return SB_ERR_CUDA;   // box-sum and tail cursors
   if (cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) ctx->sms = 148;
   if (ctx->up.init(8 << 20) != cudaSuccess) return SB_ERR_OOM;
@@ -932,6 +963,7 @@ void sb_destroy(sb_context* ctx) {
     if (ctx->prof_ev[i]) cudaEventDestroy(ctx->prof_ev[i]);
   if (ctx->tables) cudaFree(ctx->tables);
   if (ctx->dev_err) cudaFree(ctx->dev_err);
+  if (ctx->err_host) cudaFreeHost(ctx->err_host);
   if (ctx->sad_queue) cudaFree(ctx->sad_queue);
   if (ctx->ws) {
     if (ctx->ws_pooled) {
@@ -984,9 +1016,12 @@ int32_t sb_profile_read(sb_context* ctx, float* ms, int32_t max_stages) {
 
 sb_status sb_synchronize(sb_context* ctx) {
   if (!ctx) return SB_ERR_INVALID_ARG;
+  // the error word comes back through mapped host memory (see gather_h2d)
+  k_read_word<<<1, 1, 0, ctx->stream>>>(ctx->dev_err, ctx->err_host_dev);
+  ++ctx->launches;
+  SB_CUDA(ctx, cudaGetLastError());
   SB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  uint32_t e = 0;
-  SB_CUDA(ctx, cudaMemcpy(&e, ctx->dev_err, 4, cudaMemcpyDeviceToHost));
+  const uint32_t e = *reinterpret_cast<volatile uint32_t*>(ctx->err_host);
   if (e) {
     cudaMemset(ctx->dev_err, 0, 4);
     if (e & DEV_ERR_CCA_ITER)
@@ -1325,17 +1360,19 @@ sb_status record_and_upload_blob(sb_context* ctx, const std::function<sb_status(
     ctx->drop_graphs();
     if (ctx->blob_dev) cudaFree(ctx->blob_dev);
     if (ctx->blob_host) cudaFreeHost(ctx->blob_host);
-    ctx->blob_dev = ctx->blob_host = nullptr;
+    ctx->blob_dev = ctx->blob_host = ctx->blob_host_dev = nullptr;
     ctx->blob_cap = 0;
-    const size_t cap = ctx->blob.size() * 2;
+    const size_t cap = al(ctx->blob.size() * 2);   // a multiple of 16: the gather copies whole 16-byte words
     SB_CUDA(ctx, cudaMalloc(&ctx->blob_dev, cap));
-    SB_CUDA(ctx, cudaMallocHost(&ctx->blob_host, cap));
+    SB_CUDA(ctx, cudaHostAlloc(&ctx->blob_host, cap, cudaHostAllocMapped));
+    SB_CUDA(ctx, cudaHostGetDevicePointer(reinterpret_cast<void**>(&ctx->blob_host_dev), ctx->blob_host, 0));
     ctx->blob_cap = cap;
   }
   if (!ctx->blob_ev) SB_CUDA(ctx, cudaEventCreateWithFlags(&ctx->blob_ev, cudaEventDisableTiming));
   SB_CUDA(ctx, cudaEventSynchronize(ctx->blob_ev));  // the previous blob copy has been read
   memcpy(ctx->blob_host, ctx->blob.data(), ctx->blob.size());
-  SB_CUDA(ctx, cudaMemcpyAsync(ctx->blob_dev, ctx->blob_host, ctx->blob.size(), cudaMemcpyHostToDevice, ctx->stream));
+  SB_CUDA(ctx, gather_h2d(ctx->blob_dev, ctx->blob_host_dev, ctx->blob.size(), ctx->stream));
+  ++ctx->launches;
   SB_CUDA(ctx, cudaEventRecord(ctx->blob_ev, ctx->stream));
   return SB_OK;
 }
