@@ -8,7 +8,7 @@ first free stream (three by default, so new batches are copied in and
 launched while earlier ones compute; a batch of one request replays its
 shape's CUDA graph, which the stream's context keeps),
 and resolves each request's future when its batch's completion event has
-fired.  Inputs, intermediate maps and results of admitted requests stay
+fired (in the stream's waiter thread, which then wakes the scheduler).  Inputs, intermediate maps and results of admitted requests stay
 resident on the device until the batch completes; results are copied back to
 pinned host memory in the same stream.
 
@@ -19,7 +19,7 @@ fresh pinned allocation costs milliseconds and holds the interpreter lock).
 
 The scheduler never polls: it sleeps on a condition variable that new
 requests and batch completions signal (one waiter thread per stream blocks
-on its batch's completion event).  ``Server.cancel`` drops a request that is
+on its batch's completion event, finishes the batch and frees the stream).  ``Server.cancel`` drops a request that is
 still waiting for admission.
 
 The pipeline is deterministic per pair, so a request's result does not depend
@@ -76,7 +76,6 @@ class Server:
         self.cancelled = 0
         self._free: Dict[Tuple[int, int], list] = collections.defaultdict(list)
         self._free_lock = threading.Lock()
-        self._ready: collections.deque = collections.deque()   # streams whose batch has completed
         self._events = [_queue.Queue() for _ in range(n_streams)]
         self.waiters = [threading.Thread(target=self._wait_loop, args=(i,), daemon=True) for i in range(n_streams)]
         for t in self.waiters:
@@ -141,17 +140,21 @@ class Server:
 
     # ---------------------------------------------------------- scheduler side
     def _finish(self, i: int):
+        # in stream i's waiter thread, once the batch's event has fired
         ev, reqs, _keep = self.busy[i]
         now = time.perf_counter()
-        self.busy[i] = None
         err = None
         try:
             self.ctxs[i].synchronize()
         except Exception as e:  # a failed batch fails its requests, the server keeps going
             err = e
+        with self.cv:
+            for r in reqs:
+                self.used -= r.bytes
+                self.completed.append((r.arrival, now))
+            self.busy[i] = None   # the stream is free (its device tensors go with the entry)
+            self.cv.notify()
         for r in reqs:
-            self.used -= r.bytes
-            self.completed.append((r.arrival, now))
             if err is None:
                 r.future.set_result((r.out_rgb, r.out_disp))
             else:
@@ -185,7 +188,9 @@ class Server:
         self._events[i].put(ev)
 
     def _wait_loop(self, i: int):
-        # blocks (without the interpreter lock) until stream i's batch is done
+        # blocks (without the interpreter lock) until stream i's batch is done,
+        # then finishes it here: one thread hand-off fewer than waking the
+        # scheduler to do it
         while True:
             ev = self._events[i].get()
             if ev is None:
@@ -194,9 +199,7 @@ class Server:
                 ev.synchronize()
             except Exception:   # a failed batch: _finish reports the error on its requests
                 pass
-            with self.cv:
-                self._ready.append(i)
-                self.cv.notify()
+            self._finish(i)
 
     def _admissible(self) -> bool:
         return bool(self.queue) and self.used + self.queue[0].bytes <= self.budget
@@ -206,15 +209,11 @@ class Server:
             with self.cv:
                 while True:
                     free = any(b is None for b in self.busy)
-                    if self._ready or (free and self._admissible()):
+                    if free and self._admissible():
                         break
                     if not self.running and not self.queue and all(b is None for b in self.busy):
                         return
                     self.cv.wait()
-                ready = list(self._ready)
-                self._ready.clear()
-            for i in ready:
-                self._finish(i)
             free = [i for i, b in enumerate(self.busy) if b is None]
             if free:
                 with self.cv:
