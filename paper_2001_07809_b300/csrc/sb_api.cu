@@ -631,11 +631,33 @@ std::string shape_key(const Geo* geos, int n) {
   return key;
 }
 
-// Blur tile height: the candidate being timed, else the tuned value, else 112.
+// A shape key whose pairs all have one geometry: that geometry's record, else
+// an empty string.
+std::string uniform_record(const std::string& key) {
+  constexpr size_t kRec = 5 * sizeof(int32_t);
+  if (key.size() < kRec || key.size() % kRec) return std::string();
+  for (size_t o = kRec; o < key.size(); o += kRec)
+    if (key.compare(o, kRec, key, 0, kRec) != 0) return std::string();
+  return key.substr(0, kRec);
+}
+
+// Blur tile height: the candidate being timed, else the tuned value, else the
+// value tuned for another batch of the same single geometry (host-buffer
+// streaming cuts a tuned batch into chunks of other sizes; every form gives
+// the same bytes, so only the speed of the choice is borrowed), else 112.
 int blur_rows(const sb_context* ctx, const std::string& key) {
   if (ctx->blur_by_override > 0) return ctx->blur_by_override;
   auto it = ctx->tuned_blur.find(key);
-  return it != ctx->tuned_blur.end() ? it->second : 112;
+  if (it != ctx->tuned_blur.end()) return it->second;
+  const std::string rec = uniform_record(key);
+  if (!rec.empty()) {
+    int best = 0;
+    size_t best_n = 0;
+    for (const auto& t : ctx->tuned_blur)   // the largest tuned batch of this geometry
+      if (t.first.size() > best_n && uniform_record(t.first) == rec) best = t.second, best_n = t.first.size();
+    if (best) return best;
+  }
+  return 112;
 }
 
 // Box-sum work items a launch aims for: the candidate being timed, else the
