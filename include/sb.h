@@ -194,7 +194,8 @@ sb_status sb_selective_blur(sb_context* ctx, const uint8_t* rgb, const uint16_t*
  * the horizontally filtered rows in a ring so no row is filtered twice; taken
  * where its shared memory fits the largest radius of the launch, else tiles
  * of 112 rows), or SB_BLUR_AUTO (the form sb_autotune chose for the launch
- * shape, else tiles of 112 rows).  Every form gives the same bytes.  Returns
+ * shape; else, when every pair of the launch has one geometry, the form tuned
+ * for the largest tuned batch of that geometry; else tiles of 112 rows).  Every form gives the same bytes.  Returns
  * SB_ERR_INVALID_ARG for any other value. */
 enum { SB_BLUR_AUTO = 0, SB_BLUR_STRIP = 32, SB_BLUR_TILES_64 = 64, SB_BLUR_TILES_112 = 112 };
 sb_status sb_set_blur_form(sb_context* ctx, int32_t form);
@@ -202,7 +203,8 @@ sb_status sb_set_blur_form(sb_context* ctx, int32_t form);
 /* Chunking of SB_RUN_HOST_IO | SB_RUN_BATCHED runs on this context: pairs
  * stream through three device staging slots in chunks whose input bytes
  * (left + right RGB) start near first_bytes at both ends of the batch and
- * double towards the middle up to max_bytes (at least one pair per chunk), so
+ * grow by half from one chunk to the next towards the middle, up to max_bytes
+ * (at least one pair per chunk), so
  * the first upload and the last download, which nothing overlaps, stay short.
  * Defaults 64 MB and 1 GB; (0, 0) restores them; 0 < first_bytes <=
  * max_bytes, else SB_ERR_INVALID_ARG.  Smaller chunks need less staging

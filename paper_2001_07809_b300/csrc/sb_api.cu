@@ -1481,9 +1481,11 @@ sb_status run_host_io(sb_context* ctx, const sb_pair* pairs, int n, bool batched
   if (!ctx->s_in) SB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking));
   if (!ctx->s_out) SB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking));
   // chunking: up to host_cap bytes of inputs per chunk (1 GB by default), at
-  // least one pair; the chunk size ramps up from host_first (64 MB) at the start
-  // and back down at the end, so the first upload (nothing to overlap it with
-  // yet) and the last download are short
+  // least one pair; the chunk size grows by half per chunk from host_first
+  // (64 MB) at the start and shrinks the same way at the end, so the first
+  // upload (nothing to overlap it with yet) and the last download are short,
+  // and each chunk's upload (about 1.0 ms per pair on a shared link) stays
+  // shorter than the compute of the chunk before it (about 1.6 ms per pair)
   std::vector<std::pair<int, int>> chunks;
   if (!batched) {
     for (int i = 0; i < n; ++i) chunks.push_back({i, i + 1});
@@ -1492,7 +1494,7 @@ sb_status run_host_io(sb_context* ctx, const sb_pair* pairs, int n, bool batched
     int lo = 0, hi = n;
     const size_t cap = ctx->host_cap;
     for (int k = 0; lo < hi; ++k) {
-      const size_t target = std::min(cap, ctx->host_first << std::min(k, 8));
+      const size_t target = std::min(cap, (size_t)((double)ctx->host_first * std::pow(1.5, std::min(k, 16))));
       size_t acc = 0;
       const int a = lo;
       while (lo < hi && (acc < target || lo == a)) acc += (size_t)pairs[lo].w * pairs[lo].h * 6, ++lo;
