@@ -644,8 +644,8 @@ def test_host_io_equals_device(ctx):
 
 def test_host_io_batched_across_chunks_and_slots(ctx):
     # twelve mixed pairs streamed from pinned host memory in chunks that ramp from
-    # 1 MB to 4 MB of inputs: six chunks, so every one of the three staging slots is
-    # used twice, with uploads, compute and downloads of different chunks in flight
+    # 1 MB to 4 MB of inputs: seven chunks, so every one of the three staging slots
+    # is used at least twice, with uploads, compute and downloads of different chunks in flight
     # together; every pair equals the device-resident batched run, and two are
     # checked against the oracle
     from gpu_helpers import params_of
@@ -670,7 +670,7 @@ def test_host_io_batched_across_chunks_and_slots(ctx):
             outs.append((ho, hd))
         sb.sb_run(ctx, pairs, sb.SB_RUN_HOST_IO | sb.SB_RUN_BATCHED)
         ctx.synchronize()
-        assert ctx.host_io_chunks() == 6
+        assert ctx.host_io_chunks() == 7
         for (ho, hd), (w_rgb, w_disp) in zip(outs, want):
             assert np.array_equal(ho.numpy(), w_rgb)
             assert np.array_equal(hd.numpy().view(np.uint16), w_disp)
