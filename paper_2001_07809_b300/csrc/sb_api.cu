@@ -565,6 +565,23 @@ void sad_items(const std::vector<std::pair<int, Geo>>& pairs, int64_t target, in
         tail_parts.push_back(SadItem{it.job, it.x0, it.d0, it.y0 + rows * b / 4, it.y0 + rows * (b + 1) / 4 - 1});
     }
     if (!tail_parts.empty()) keep = list.size() - slots;
+    // and the last grid's worth of those quarters into halves again (eighth
+    // items), where a half keeps at least max(8r, 64) rows: a launch of a
+    // few pairs (a host-streaming chunk) spends its last round on them
+    if (tail_parts.size() >= 2 * slots) {
+      std::vector<SadItem> halves;
+      for (size_t k = tail_parts.size() - slots; k < tail_parts.size(); ++k) {
+        const SadItem& it = tail_parts[k];
+        const int rows = it.y1 - it.y0 + 1;
+        if (rows < 2 * std::max(8 * radius[it.job], 64)) { halves.clear(); break; }
+        halves.push_back(SadItem{it.job, it.x0, it.d0, it.y0, it.y0 + rows / 2 - 1});
+        halves.push_back(SadItem{it.job, it.x0, it.d0, it.y0 + rows / 2, it.y1});
+      }
+      if (!halves.empty()) {
+        tail_parts.resize(tail_parts.size() - slots);
+        tail_parts.insert(tail_parts.end(), halves.begin(), halves.end());
+      }
+    }
   }
   for (size_t k = 0; k < keep; ++k) items->push_back(list[k].second);
   for (auto& it : tail_parts) items->push_back(it);
